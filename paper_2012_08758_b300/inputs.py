@@ -1,0 +1,89 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the
+serving loop.  This module holds no arithmetic of the method itself: it only
+draws initial states and request streams from numpy generators.
+
+State arrays are float64 of shape (7, nz, ny, nx), x fastest, field order
+ln rho, u_x, u_y, u_z, A_x, A_y, A_z.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def seed_field_state(nx: int, ny: int | None = None, nz: int | None = None,
+                     seed: int = 0, amp: float = 1e-5) -> np.ndarray:
+    """Initial condition of Sec. 4: uniform density (ln rho = 0), u = 0 and a
+    weak delta-correlated Gaussian vector potential A ~ amp * N(0, 1)."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    rng = np.random.default_rng(seed)
+    q = np.zeros((7, nz, ny, nx))
+    q[4:7] = amp * rng.standard_normal((3, nz, ny, nx))
+    return q
+
+
+def uniform_state(nx: int, ny: int | None = None, nz: int | None = None,
+                  seed: int = 0, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+    """All seven fields uniform in [lo, hi): the benchmark state of App. A."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=(7, nz, ny, nx))
+
+
+def random_modes_state(nx: int, ny: int | None = None, nz: int | None = None,
+                       seed: int = 0, amp: float = 0.1, kmax: int = 3,
+                       nmodes: int = 6) -> np.ndarray:
+    """Smooth random state: each field is a sum of nmodes plane waves with
+    integer wave vectors |k_i| <= kmax, random amplitudes and phases."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    rng = np.random.default_rng(seed)
+    x = np.arange(nx) * (2 * math.pi / nx)
+    y = np.arange(ny) * (2 * math.pi / ny)
+    z = np.arange(nz) * (2 * math.pi / nz)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    q = np.zeros((7, nz, ny, nx))
+    for f in range(7):
+        for _ in range(nmodes):
+            k = rng.integers(-kmax, kmax + 1, size=3)
+            a = amp * rng.standard_normal() / math.sqrt(nmodes)
+            ph = rng.uniform(0, 2 * math.pi)
+            q[f] += a * np.cos(k[0] * X + k[1] * Y + k[2] * Z + ph)
+    return q
+
+
+def noise_state(nx: int, ny: int | None = None, nz: int | None = None,
+                seed: int = 0, amp: float = 0.05) -> np.ndarray:
+    """Delta-correlated Gaussian noise of amplitude amp in every field
+    (grid-scale structure that exercises every stencil point)."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    rng = np.random.default_rng(seed)
+    return amp * rng.standard_normal((7, nz, ny, nx))
+
+
+def serving_requests(n: int = 200, seed: int = 2025, rate: float = 1.0,
+                     grids=(64, 96, 128, 192, 256), rem=(10.0, 250.0),
+                     steps=(500, 5000)) -> list[dict]:
+    """Poisson stream of dynamo-run requests: exponential inter-arrival
+    times of mean 1/rate, grid uniform over `grids`, Re_M log-uniform over
+    `rem`, helicity sigma in {0, 1}, a uniform integer step budget, and a
+    per-request seed for the initial field and the forcing."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate)
+        out.append(dict(
+            id=i,
+            arrival=t,
+            n=int(rng.choice(grids)),
+            re_m=float(math.exp(rng.uniform(math.log(rem[0]), math.log(rem[1])))),
+            sigma=float(rng.integers(0, 2)),
+            steps=int(rng.integers(steps[0], steps[1] + 1)),
+            seed=int(rng.integers(0, 2**62)),
+        ))
+    return out

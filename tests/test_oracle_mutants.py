@@ -1,0 +1,60 @@
+"""Mutation check of the oracle's pins: each case plants one plausible
+mistake (a dropped factor, a wrong sign, a transposed operand, a wrong
+index) in a scratch copy of the oracle's C source, builds it with gcc in a
+temporary folder and runs the pin suite against it; every mutant must fail.
+CPU only; the committed oracle is never modified."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "mhd_oracle.c")
+
+MUTANTS = {
+    "lorentz_sign": ("JxB[a] / rho", "-JxB[a] / rho"),
+    "grad_div_third": ("gdu[a] / 3.0", "gdu[a] / 2.0"),
+    "strain_factor_two": ("2.0 * Sg", "1.0 * Sg"),
+    "strain_trace": ("divu / 3.0 : 0.0", "divu / 2.0 : 0.0"),
+    "u_cross_b_order": ("cross3(uu, B, uxB);", "cross3(B, uu, uxB);"),
+    "bz_sign": ("gA[1][0] - gA[0][1]};\n        /* Lap", "gA[0][1] - gA[1][0]};\n        /* Lap"),
+    "bx_sign": ("/* B = curl A */\n        double B[3] = {gA[2][1] - gA[1][2],",
+                "/* B = curl A */\n        double B[3] = {gA[1][2] - gA[2][1],"),
+    "d1_weight": ("- 9.0 * (f[2] - f[-2])", "- 8.0 * (f[2] - f[-2])"),
+    "d2_weight": ("- 27.0 * (f[2] + f[-2])", "- 26.0 * (f[2] + f[-2])"),
+    "dmix_weight": ("- 27.0 * S[2]", "- 26.0 * S[2]"),
+    "dmix_pattern": ("P(s, s) + P(-s, -s) - P(s, -s) - P(-s, s)",
+                     "P(s, s) - P(-s, -s) + P(s, -s) - P(-s, s)"),
+    "dmix_axis": ("offset(b, sb, &bi, &bj, &bk);", "offset(a, sb, &bi, &bj, &bk);"),
+    "rk_alpha": ("-153.0 / 128.0", "-150.0 / 128.0"),
+    "rk_beta": ("15.0 / 16.0, 8.0", "14.0 / 16.0, 8.0"),
+    "advection_transposed": ("uu[0] * G[a][0] + uu[1] * G[a][1]", "uu[0] * G[0][a] + uu[1] * G[1][a]"),
+    "pressure_cs_not_squared": ("- cs2 * g[a]", "- p->cs * g[a]"),
+    "continuity_div_sign": ("- divu;\n", "+ divu;\n"),
+    "eta_vs_nu": ("p->eta * lapA[a]", "p->nu * lapA[a]"),
+    "helicity_sign": ("F->b[d] = -p->sigma", "F->b[d] = p->sigma"),
+    "forcing_norm_dt": ("sqrt(kk * p->cs / dt)", "sqrt(kk * p->cs * dt)"),
+    "forcing_phase_sign": ("+ F->phi;", "- F->phi;"),
+    "forcing_sin_sign": ("F->a[d] * c - F->b[d] * s", "F->a[d] * c + F->b[d] * s"),
+    "shell_exclusive": ("m >= kmin && m <= kmax", "m > kmin && m <= kmax"),
+    "dt_max_spacing": ("double dmin = fmin(spacing(p, 0),", "double dmin = fmax(spacing(p, 0),"),
+    "dt_alfven_rho": ("sqrt(cs2 + B2 / exp(q[c]))", "sqrt(cs2 + B2 * exp(q[c]))"),
+    "ekin_density": ("kadd(&sk, rho * u2);", "kadd(&sk, u2);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_reject_mutant(name, tmp_path):
+    before, after = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(before) == 1, f"mutation site not unique/found: {name}"
+    mut = tmp_path / "mutant.c"
+    mut.write_text(src.replace(before, after))
+    lib = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O1", "-fopenmp", "-fPIC", "-shared", "-o", str(lib), str(mut), "-lm"])
+    env = dict(os.environ, ORACLE_LIB_OVERRIDE=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} survived the pins"
