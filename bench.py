@@ -1,0 +1,301 @@
+#!/usr/bin/env python
+"""Benchmark of one forced isothermal MHD time step on a B300.
+
+Workload (N=1): 256^3 periodic box, FP32 fields and arithmetic, helical
+forcing (sigma = 1, shell 2.5 <= |k| <= 3.5, k_f ~ 3.13, f0 = 0.02),
+nu = eta = 1.6e-4 (Re_M ~ 100 for u_rms ~ 0.05), CFL time step (0.4).  A
+step = device time-step reduction + forcing draw + three fused RHS/RK3-2N
+substeps, all of it inside the timed region.  Inputs are synthetic (seeded
+weak-field initial condition of Sec. 4) and larger than L2 (1.5 GB of
+state), so no L2 flush is needed between steps.
+
+Prints ONE JSON line.  --impl reference times the FP64 CPU oracle on the
+host cores instead (a deliberately slow baseline, not a target)."""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s & %HBM roofline, FP32 vs FP64; batched p50/p99 job latency"
+UNIT = "cell-updates/s"
+BYTES_PER_CELL = {"f32": 70 * 4, "f64": 70 * 8}  # algorithmic: 70 values per cell-update
+WORKLOAD = dict(f0=0.02, sigma=1.0, kmin=2.5, kmax=3.5, nu=1.6e-4, eta=1.6e-4, cfl=0.4, seed=1)
+
+
+def workload_name(n, dtype):
+    return (f"{n}^3 forced isothermal MHD step ({dtype.upper()}): helical sigma=1, shell [2.5,3.5] "
+            f"(k_f~3.13), f0=0.02, nu=eta=1.6e-4 (Re_M~100), CFL 0.4, seed-field initial state")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy of 1 Gi bf16)"
+    except Exception:
+        return 6400.0, "fallback (6.4 TB/s, earlier B300 measurement)"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2012_08758_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(n, dtype):
+    """DRAM bytes per substep launch from the committed ncu summary, or None
+    when the kernels changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "substep_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    key = f"{n}_{dtype}"
+    ent = d.get("workloads", {}).get(key)
+    return None if ent is None else ent.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = str(gpu_index)
+        self.samples = []
+        self._stop = threading.Event()
+        self._th = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", self.gpu, f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([c.strip() for c in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._th = threading.Thread(target=self._run, daemon=True)
+        self._th.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        if self._th:
+            self._th.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 5 + i and s[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def cpu_baseline(seconds=12.0, n=64):
+    """The FP64 oracle, as it stands, on the host cores: cell-updates/s on
+    whole steps of an n^3 sample of the same workload."""
+    from oracle import oracle as O
+    from paper_2012_08758_b300 import inputs
+
+    cores = O.set_threads(os.cpu_count() or 1)
+    p = O.Params(nx=n, ny=n, nz=n, **WORKLOAD)
+    q = inputs.seed_field_state(n, seed=0)
+    O.run(p, q, 1)  # warm-up
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        O.run(p, q, 1, step0=1 + steps)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > seconds or steps >= 200:
+            break
+    return {"value": n ** 3 * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} full steps of the {n}^3 version of the workload (FP64 oracle, "
+                      f"OpenMP over z-planes), {el:.1f} s"}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    cb = cpu_baseline(seconds=max(5.0, 2.0 * args.steps), n=64)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * 64 ** 3 / cb["value"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(64, "f64") + " (CPU sample of the 256^3 workload)",
+                       "grid": 64},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2012_08758_b300 import binding as B
+    from paper_2012_08758_b300 import inputs
+    from paper_2012_08758_b300.run import Run
+
+    n, dtype = args.n, args.dtype
+    cells = n ** 3
+    run = Run(n=n, device=dev, dtype=B.MHD_F32 if dtype == "f32" else B.MHD_F64, **WORKLOAD)
+    q0 = inputs.seed_field_state(n, seed=rank)
+    run.set_state(q0)
+    run.step(args.warmup)
+    run.sync()
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+
+    # --- device-timed region: K steps, events on the context's stream ---
+    barrier()
+    with ClockSampler(local) as clk:
+        stage_ms, total_ms = B.mhd_step_timed(run.ctx, args.steps)
+    barrier()
+    t_local = total_ms / 1e3
+    if world > 1:
+        t = torch.tensor([t_local], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    run.sync()  # raises if the run blew up
+    value = world * cells * args.steps / t_max
+
+    # --- roofline of the dominant kernel (fused substep, 3 launches/step) ---
+    sub_ms = sum(stage_ms[1:4])
+    bpc = BYTES_PER_CELL[dtype]
+    achieved = bpc * cells * args.steps / (sub_ms / 1e3) / 1e9
+    peak, peak_src = measured_peaks()
+    traffic = ncu_traffic(n, dtype)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": "k_substep (fused RHS + RK3-2N), 3 launches per step",
+            "algorithmic_bytes_per_cell_update": bpc, "peak_source": peak_src,
+            "stage_ms_per_step": {"prologue": stage_ms[0] / args.steps,
+                                  "substep1": stage_ms[1] / args.steps,
+                                  "substep2": stage_ms[2] / args.steps,
+                                  "substep3": stage_ms[3] / args.steps}}
+
+    # --- end to end through the public API with host buffers ---
+    pinned = torch.empty(q0.shape, dtype=torch.float32 if dtype == "f32" else torch.float64).pin_memory()
+    host_in = pinned.numpy()
+    host_in[...] = q0
+    host_out = torch.empty_like(pinned).pin_memory().numpy()
+    e2e_steps = args.steps
+    barrier()
+    t0 = time.perf_counter()
+    B.mhd_set_state(run.ctx, host_in, 0.0, 0)
+    for _ in range(e2e_steps):
+        B.mhd_step(run.ctx, 1)
+        B.mhd_reduce(run.ctx, B.MHD_BRMS)  # one double back per step
+    B.mhd_get_state(run.ctx, host_out)
+    barrier()
+    e2e_t = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    state_bytes = host_in.nbytes
+    e2e = {"value": world * cells * e2e_steps / e2e_t, "unit": UNIT,
+           "h2d_bytes_per_step": state_bytes / e2e_steps,
+           "d2h_bytes_per_step": (state_bytes + 8 * e2e_steps) / e2e_steps,
+           "note": "per job: state upload from pinned host memory, K x (mhd_step(1) + mhd_reduce(B_rms)), "
+                   "state download"}
+
+    # --- FP64 beside FP32 on the same workload (few steps: ALU-bound) ---
+    fp64 = None
+    if dtype == "f32" and not args.skip_fp64:
+        run64 = Run(n=n, device=dev, dtype=B.MHD_F64, **WORKLOAD)
+        run64.set_state(q0)
+        run64.step(1)
+        run64.sync()
+        st64, tot64 = B.mhd_step_timed(run64.ctx, 3)
+        run64.close()
+        sub64 = sum(st64[1:4])
+        fp64 = {"value": cells * 3 / (tot64 / 1e3), "unit": UNIT, "steps": 3,
+                "ms_per_step": tot64 / 3,
+                "hbm_frac": BYTES_PER_CELL["f64"] * cells * 3 / (sub64 / 1e3) / 1e9 / peak}
+    run.close()
+
+    cb = cpu_baseline() if (rank == 0 and world == 1 and not args.skip_cpu) else None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+                "config": {"workload": workload_name(n, dtype), "grid": n, "replicas": world,
+                           "parallelism": f"replicas x{world} (independent runs, no collective)",
+                           "l2": "inputs larger than L2 (21 padded arrays, %.2f GB)" % (run.nbytes / 1e9)},
+                "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "fp64": fp64,
+                "gpu_launches": 4 * args.steps, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU-baseline leg")
+    ap.add_argument("--skip-fp64", action="store_true", help="omit the FP64 side measurement")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,203 @@
+/*
+ * mhd.h -- C ABI of the B300 (sm_103a) isothermal MHD stepper.
+ *
+ * One time step of compressible isothermal resistive MHD on a triply
+ * periodic box (Vaisala et al. 2020, arXiv:2012.08758): continuity
+ * (Sec. 4, Eq. 1), momentum (Eq. 2) and induction in the diffusive gauge
+ * (Eq. 3) with the random helical/non-helical forcing of Eqs. 4-6,
+ * discretised with 6th-order central finite differences and advanced by
+ * third-order 2N-storage Runge-Kutta (Sec. 2).  Periodic boundaries are
+ * wrapped ghost zones of radius 3 (Sec. 3.1).
+ *
+ * Conventions for every entry point:
+ *  - return 0 (MHD_OK) on success, a negative MHD_E* code on failure; the
+ *    message is then available from mhd_last_error(ctx) (ctx may be NULL
+ *    for failures that happen before a context exists).
+ *  - host pointers belong to the caller and are only read/written during
+ *    the call; device memory belongs to the context (or to the caller, when
+ *    the caller passes a workspace to mhd_create).
+ *  - a failed call leaves the context as it was (no half-built state).
+ *  - all device work of a context is ordered on the CUDA stream given to
+ *    mhd_create; calls documented as asynchronous return before the GPU
+ *    has finished, calls documented as synchronising wait for that stream.
+ *  - host state arrays are SoA: 7 fields of nx*ny*nz values each, x
+ *    fastest, in the order ln rho, u_x, u_y, u_z, A_x, A_y, A_z.
+ *
+ * Not thread-safe per context: one host thread at a time per mhd_ctx.
+ */
+#ifndef MHD_H
+#define MHD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mhd_ctx mhd_ctx;
+typedef struct mhd_batch mhd_batch;
+
+/* Working precision of fields and stencil arithmetic (Sec. 3.2: the
+ * precision of reals is a build-time choice in the paper; here both
+ * instantiations ship and the choice is per context). */
+typedef enum { MHD_F32 = 0, MHD_F64 = 1 } mhd_dtype;
+
+enum {
+  MHD_OK = 0,
+  MHD_EINVAL = -1,     /* bad argument or parameter                       */
+  MHD_ENOMEM = -2,     /* device or host allocation failed / too small    */
+  MHD_ECUDA = -3,      /* a CUDA runtime call failed                      */
+  MHD_ETIMEOUT = -4,   /* a bounded device-side wait gave up              */
+  MHD_ENONFINITE = -5, /* the time-step reduction saw NaN/Inf (run blew up)*/
+  MHD_ESTATE = -6      /* call not valid in the current state             */
+};
+
+/* Quantities of mhd_reduce / mhd_diagnostics (volume means over the
+ * nx*ny*nz interior points; B = curl A with the first-derivative stencil).
+ * Global averages of this kind are the run-time diagnostics of Sec. 4. */
+enum {
+  MHD_URMS = 0,     /* sqrt(<|u|^2>)                                     */
+  MHD_BRMS = 1,     /* sqrt(<|B|^2>)                                     */
+  MHD_UMAX = 2,     /* max |u|                                           */
+  MHD_BMAX = 3,     /* max |B|                                           */
+  MHD_EKIN = 4,     /* <rho |u|^2> / 2                                   */
+  MHD_EMAG = 5,     /* <|B|^2> / 2   (mu0 = 1, Sec. 4 units)             */
+  MHD_DIVB_MAX = 6, /* max |div B| (zero up to rounding)                 */
+  MHD_MASS = 7,     /* <rho>                                             */
+  MHD_VMAX = 8,     /* max(|u| + sqrt(cs^2 + |B|^2/rho)), the CFL speed  */
+  MHD_NREDUCE = 9
+};
+
+/* Kernel variants of the fused RHS + RK substep. */
+enum {
+  MHD_KERNEL_AUTO = 0,  /* fastest measured variant for this grid          */
+  MHD_KERNEL_SMEM = 1,  /* plane ring in shared memory, plain loads        */
+  MHD_KERNEL_TMA = 2    /* TMA-staged planes + register pencils along z    */
+};
+
+typedef struct {
+  int nx, ny, nz;           /* interior points per axis, each >= 1           */
+  double lx, ly, lz;        /* box size (default 2 pi, Sec. 4)               */
+  double cs;                /* isothermal sound speed                        */
+  double nu, eta;           /* viscosity and resistivity (>= 0)              */
+  double f0;                /* forcing scale factor of Eq. 5 (0: no forcing) */
+  double kmin, kmax;        /* forcing shell kmin <= |k| <= kmax (integer k) */
+  double sigma;             /* forcing helicity in [0, 1] (Eq. 6)            */
+  uint64_t seed;            /* forcing random stream of this run             */
+  double cfl;               /* advective Courant number (default 0.4)        */
+  double cfl_visc;          /* diffusive number (default 0.08)               */
+  double dt_fixed;          /* > 0: constant dt instead of the CFL rule      */
+  int forcing_mode;         /* 0: f in every substep; 1: dt*f once per step  */
+  int dtype;                /* mhd_dtype                                     */
+  int kernel;               /* MHD_KERNEL_*                                  */
+  int tile;                 /* 0: automatic tile choice, else a tile id      */
+} mhd_params;
+
+/* Fills p with the defaults: 32^3, L = 2 pi, cs = 1, nu = eta = 5e-3,
+ * no forcing (f0 = 0), shell [2.5, 3.5], sigma = 0, seed = 1, cfl = 0.4,
+ * cfl_visc = 0.08, CFL time step, forcing in every substep, FP32, automatic
+ * kernel and tile.  p must be non-NULL. */
+void mhd_default_params(mhd_params *p);
+
+/* Device bytes a context with parameters p needs when the caller supplies
+ * the workspace (mhd_create with workspace != NULL).  Returns MHD_EINVAL on
+ * invalid parameters. */
+int mhd_workspace_bytes(const mhd_params *p, size_t *bytes);
+
+/* Creates a context on the current CUDA device.
+ *   p          parameters (validated; copied).
+ *   stream     cudaStream_t to order all work on (NULL: legacy stream).
+ *   workspace  device buffer of >= mhd_workspace_bytes bytes, 256-byte
+ *              aligned, owned by the caller and kept alive until
+ *              mhd_destroy; or NULL, and the context allocates its own.
+ *   out        receives the context.
+ * The state is zero (ln rho = 0, u = A = 0) at t = 0, step 0.
+ * Synchronising.  Errors: MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA. */
+int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t workspace_bytes,
+               mhd_ctx **out);
+
+/* Releases the context and any device memory it allocated itself.
+ * Waits for the context's stream.  NULL is ignored. */
+void mhd_destroy(mhd_ctx *ctx);
+
+/* Uploads a state: host_soa holds 7*nx*ny*nz values of type host_dtype
+ * (converted to the working precision on the device), t is the time and
+ * step the step index (it selects the forcing draws that follow).  Fills the
+ * periodic ghost zones.  Synchronising. */
+int mhd_set_state(mhd_ctx *ctx, const void *host_soa, int host_dtype, double t, int64_t step);
+
+/* Downloads the state into host_soa (7*nx*ny*nz values of host_dtype) and
+ * the time and step index (either pointer may be NULL).  Synchronising;
+ * returns MHD_ENONFINITE if the run has produced a non-finite time step. */
+int mhd_get_state(mhd_ctx *ctx, void *host_soa, int host_dtype, double *t, int64_t *step);
+
+/* Enqueues nsteps time steps (nsteps >= 0) on the context's stream and
+ * returns without waiting.  Each step: time-step reduction (CFL rule, or
+ * dt_fixed) and forcing draw on the device, then three fused RHS + RK3-2N
+ * substeps (Sec. 2) with the ghost zones refilled by each substep.  No
+ * host<->device traffic.  Errors of the launches are reported here;
+ * numerical blow-up is reported by the next synchronising call. */
+int mhd_step(mhd_ctx *ctx, int nsteps);
+
+/* mhd_step with CUDA events recorded on the context's stream around every
+ * kernel stage; waits for the steps to finish and adds the device time of
+ * each stage, summed over the nsteps steps, to stage_ms[0..3] = step
+ * prologue (time-step reduction + forcing draw), substeps 1, 2 and 3; the
+ * total elapsed time (first to last event) is added to *total_ms.  The
+ * work done is exactly that of mhd_step.  Synchronising. */
+int mhd_step_timed(mhd_ctx *ctx, int nsteps, double *stage_ms, double *total_ms);
+
+/* Reads one quantity (MHD_URMS ... MHD_VMAX) of the current state into
+ * *out, accumulated in FP64 in a fixed order.  Synchronising. */
+int mhd_reduce(mhd_ctx *ctx, int kind, double *out);
+
+/* All MHD_NREDUCE quantities at once into out[MHD_NREDUCE].  Synchronising. */
+int mhd_diagnostics(mhd_ctx *ctx, double *out);
+
+/* Time, last time step and step index of the current state (any pointer
+ * may be NULL).  Synchronising; MHD_ENONFINITE after a blow-up. */
+int mhd_time(mhd_ctx *ctx, double *t, double *dt_last, int64_t *step);
+
+/* Waits for the context's stream; MHD_ENONFINITE after a blow-up. */
+int mhd_sync(mhd_ctx *ctx);
+
+/* The forcing draw of step index `step` (Sec. 4, Eqs. 4 and 6) as computed
+ * on the device: out[0..2] = integer k, out[3] = phi, out[4..6] = e,
+ * out[7..9] = Re f_k, out[10..12] = Im f_k.  Does not change the run.
+ * Synchronising.  MHD_EINVAL when the run has no forcing. */
+int mhd_forcing_draw(mhd_ctx *ctx, int64_t step, double *out);
+
+/* Right-hand side of Eqs. 1-3 for the current state, evaluated by the same
+ * fused kernel as a substep: host_rhs (7*nx*ny*nz values of host_dtype)
+ * receives dq/dt, including the forcing of step index `step` normalised
+ * with time step dt_forcing (dt_forcing <= 0: no forcing).  Does not
+ * change the state.  Synchronising. */
+int mhd_eval_rhs(mhd_ctx *ctx, int64_t step, double dt_forcing, void *host_rhs, int host_dtype);
+
+/* Message of the last failure on ctx (or of the calling thread when ctx is
+ * NULL); never NULL. */
+const char *mhd_last_error(const mhd_ctx *ctx);
+
+/* ---- batched stepping of independent runs ------------------------------
+ * A batch steps several contexts (same device, stream and dtype; any grid
+ * sizes) with one launch per kernel stage over a combined tile table, the
+ * k-step sequence captured once in a CUDA graph and replayed.  Every run
+ * gives bit-for-bit the result it gives when stepped alone (per-run
+ * reductions have a fixed order that does not depend on the batch). */
+
+/* Creates a batch over runs[0..nruns-1] (the contexts must outlive it).
+ * Synchronising.  Errors: MHD_EINVAL (mixed dtype/stream), MHD_ENOMEM,
+ * MHD_ECUDA. */
+int mhd_batch_create(mhd_ctx *const *runs, int nruns, mhd_batch **out);
+
+/* Enqueues nsteps steps of every run of the batch.  Asynchronous. */
+int mhd_batch_step(mhd_batch *b, int nsteps);
+
+/* Releases the batch (not the contexts).  NULL is ignored. */
+void mhd_batch_destroy(mhd_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHD_H */

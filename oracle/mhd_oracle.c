@@ -271,67 +271,78 @@ void orc_forcing_at(const orc_params *p, const orc_forcing *F, int i, int j, int
 /* Right-hand side (Sec. 4 Eqs. 1-3)                                    */
 /* ------------------------------------------------------------------ */
 
-/* rhs[7*n] = d q / dt for state q; F == NULL or F->amp == 0: no forcing. */
-void orc_rhs(const orc_params *p, const double *q, const orc_forcing *F, double *rhs) {
+/* d q / dt of Eqs. 1-3 at grid point (i, j, k): out[0..6].
+ * F == NULL or F->amp == 0: no forcing. */
+void orc_rhs_at(const orc_params *p, const double *q, const orc_forcing *F, int i, int j, int k,
+          double *out) {
   const long n = (long)p->nx * p->ny * p->nz;
   const double *lnrho = q;
   const double *u[3] = {q + n, q + 2 * n, q + 3 * n};
   const double *A[3] = {q + 4 * n, q + 5 * n, q + 6 * n};
   const double cs2 = p->cs * p->cs;
+  const long c = ((long)k * p->ny + j) * p->nx + i;
+  double g[3], G[3][3], gA[3][3], uu[3];
+  for (int a = 0; a < 3; ++a) {
+    g[a] = orc_d1(p, lnrho, i, j, k, a);          /* grad ln rho       */
+    uu[a] = u[a][c];
+    for (int b = 0; b < 3; ++b) {
+      G[a][b] = orc_d1(p, u[a], i, j, k, b);       /* d u_a / d x_b     */
+      gA[a][b] = orc_d1(p, A[a], i, j, k, b);      /* d A_a / d x_b     */
+    }
+  }
+  const double rho = exp(lnrho[c]);
+  const double divu = G[0][0] + G[1][1] + G[2][2];
+  /* B = curl A */
+  double B[3] = {gA[2][1] - gA[1][2], gA[0][2] - gA[2][0], gA[1][0] - gA[0][1]};
+  /* Laplacians, grad(div u), grad(div A) from second/mixed stencils */
+  double lapu[3], lapA[3], gdu[3], gdA[3];
+  for (int a = 0; a < 3; ++a) {
+    lapu[a] = lapA[a] = gdu[a] = gdA[a] = 0.0;
+    for (int b = 0; b < 3; ++b) {
+      lapu[a] += orc_d2(p, u[a], i, j, k, b);
+      lapA[a] += orc_d2(p, A[a], i, j, k, b);
+      gdu[a] += dd(p, u[b], i, j, k, a, b);        /* d_a d_b u_b       */
+      gdA[a] += dd(p, A[b], i, j, k, a, b);        /* d_a d_b A_b       */
+    }
+  }
+  /* R2: j = grad(div A) - lap A (mu0 = 1) */
+  double J[3] = {gdA[0] - lapA[0], gdA[1] - lapA[1], gdA[2] - lapA[2]};
+  double JxB[3], uxB[3];
+  cross3(J, B, JxB);
+  cross3(uu, B, uxB);
+  /* traceless rate of strain S_ab = (G_ab + G_ba)/2 - delta_ab div u / 3 */
+  double S[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      S[a][b] = 0.5 * (G[a][b] + G[b][a]) - (a == b ? divu / 3.0 : 0.0);
+  double f[3] = {0.0, 0.0, 0.0};
+  if (F && F->amp != 0.0 && p->forcing_mode == 0) orc_forcing_at(p, F, i, j, k, f);
+
+  /* Eq. 1: D ln rho / Dt = -div u */
+  out[0] = -(uu[0] * g[0] + uu[1] * g[1] + uu[2] * g[2]) - divu;
+  for (int a = 0; a < 3; ++a) {
+    /* Eq. 2: Du/Dt = -cs^2 grad ln rho + j x B / rho
+     *         + nu [lap u + grad(div u)/3 + 2 S.grad ln rho] + f */
+    double adv = uu[0] * G[a][0] + uu[1] * G[a][1] + uu[2] * G[a][2];
+    double Sg = S[a][0] * g[0] + S[a][1] * g[1] + S[a][2] * g[2];
+    out[1 + a] = -adv - cs2 * g[a] + JxB[a] / rho +
+                 p->nu * (lapu[a] + gdu[a] / 3.0 + 2.0 * Sg) + f[a];
+    /* Eq. 3: dA/dt = u x B + eta lap A (diffusive gauge) */
+    out[4 + a] = uxB[a] + p->eta * lapA[a];
+  }
+}
+
+/* rhs[7*n] = d q / dt for state q at every grid point. */
+void orc_rhs(const orc_params *p, const double *q, const orc_forcing *F, double *rhs) {
+  const long n = (long)p->nx * p->ny * p->nz;
 #pragma omp parallel for schedule(static)
   for (int k = 0; k < p->nz; ++k)
     for (int j = 0; j < p->ny; ++j)
       for (int i = 0; i < p->nx; ++i) {
         const long c = ((long)k * p->ny + j) * p->nx + i;
-        double g[3], G[3][3], gA[3][3], uu[3];
-        for (int a = 0; a < 3; ++a) {
-          g[a] = orc_d1(p, lnrho, i, j, k, a);          /* grad ln rho       */
-          uu[a] = u[a][c];
-          for (int b = 0; b < 3; ++b) {
-            G[a][b] = orc_d1(p, u[a], i, j, k, b);       /* d u_a / d x_b     */
-            gA[a][b] = orc_d1(p, A[a], i, j, k, b);      /* d A_a / d x_b     */
-          }
-        }
-        const double rho = exp(lnrho[c]);
-        const double divu = G[0][0] + G[1][1] + G[2][2];
-        /* B = curl A */
-        double B[3] = {gA[2][1] - gA[1][2], gA[0][2] - gA[2][0], gA[1][0] - gA[0][1]};
-        /* Laplacians, grad(div u), grad(div A) from second/mixed stencils */
-        double lapu[3], lapA[3], gdu[3], gdA[3];
-        for (int a = 0; a < 3; ++a) {
-          lapu[a] = lapA[a] = gdu[a] = gdA[a] = 0.0;
-          for (int b = 0; b < 3; ++b) {
-            lapu[a] += orc_d2(p, u[a], i, j, k, b);
-            lapA[a] += orc_d2(p, A[a], i, j, k, b);
-            gdu[a] += dd(p, u[b], i, j, k, a, b);        /* d_a d_b u_b       */
-            gdA[a] += dd(p, A[b], i, j, k, a, b);        /* d_a d_b A_b       */
-          }
-        }
-        /* R2: j = grad(div A) - lap A (mu0 = 1) */
-        double J[3] = {gdA[0] - lapA[0], gdA[1] - lapA[1], gdA[2] - lapA[2]};
-        double JxB[3], uxB[3];
-        cross3(J, B, JxB);
-        cross3(uu, B, uxB);
-        /* traceless rate of strain S_ab = (G_ab + G_ba)/2 - delta_ab div u / 3 */
-        double S[3][3];
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b)
-            S[a][b] = 0.5 * (G[a][b] + G[b][a]) - (a == b ? divu / 3.0 : 0.0);
-        double f[3] = {0.0, 0.0, 0.0};
-        if (F && F->amp != 0.0 && p->forcing_mode == 0) orc_forcing_at(p, F, i, j, k, f);
-
-        /* Eq. 1: D ln rho / Dt = -div u */
-        rhs[c] = -(uu[0] * g[0] + uu[1] * g[1] + uu[2] * g[2]) - divu;
-        for (int a = 0; a < 3; ++a) {
-          /* Eq. 2: Du/Dt = -cs^2 grad ln rho + j x B / rho
-           *         + nu [lap u + grad(div u)/3 + 2 S.grad ln rho] + f */
-          double adv = uu[0] * G[a][0] + uu[1] * G[a][1] + uu[2] * G[a][2];
-          double Sg = S[a][0] * g[0] + S[a][1] * g[1] + S[a][2] * g[2];
-          rhs[(1 + a) * n + c] = -adv - cs2 * g[a] + JxB[a] / rho +
-                                 p->nu * (lapu[a] + gdu[a] / 3.0 + 2.0 * Sg) + f[a];
-          /* Eq. 3: dA/dt = u x B + eta lap A (diffusive gauge) */
-          rhs[(4 + a) * n + c] = uxB[a] + p->eta * lapA[a];
-        }
+        double out[7];
+        orc_rhs_at(p, q, F, i, j, k, out);
+        for (int f = 0; f < 7; ++f) rhs[f * n + c] = out[f];
       }
 }
 

@@ -129,6 +129,8 @@ def lib():
         L.orc_forcing_amplitude.restype = None
         L.orc_forcing_at.argtypes = [pp, fp, C.c_int, C.c_int, C.c_int, dp]
         L.orc_forcing_at.restype = None
+        L.orc_rhs_at.argtypes = [pp, dp, fp, C.c_int, C.c_int, C.c_int, dp]
+        L.orc_rhs_at.restype = None
         L.orc_rhs.argtypes = [pp, dp, fp, dp]
         L.orc_rhs.restype = None
         L.orc_max_speed.argtypes = [pp, dp]
@@ -254,6 +256,20 @@ def rhs(p: Params, q: np.ndarray, F: Forcing | None = None) -> np.ndarray:
     out = np.empty_like(q)
     pc = p.c()
     lib().orc_rhs(C.byref(pc), _dp(q), C.byref(F._c) if F is not None else None, _dp(out))
+    return out
+
+
+def rhs_at(p: Params, q: np.ndarray, points, F: Forcing | None = None) -> np.ndarray:
+    """dq/dt at the listed (i, j, k) points only; returns (len(points), 7)."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    assert q.shape == p.shape
+    pc = p.c()
+    out = np.empty((len(points), 7))
+    v = (C.c_double * 7)()
+    Fc = C.byref(F._c) if F is not None else None
+    for n, (i, j, k) in enumerate(points):
+        lib().orc_rhs_at(C.byref(pc), _dp(q), Fc, int(i), int(j), int(k), v)
+        out[n] = v[:]
     return out
 
 

@@ -1,0 +1,684 @@
+// Host side of the C ABI declared in include/mhd.h: parameter validation,
+// device workspace layout, tile tables, step orchestration and batching.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mhd.h"
+#include "mhd_internal.h"
+
+using namespace mhd;
+
+namespace {
+
+thread_local std::string g_err;
+
+constexpr size_t ALIGN = 256;
+constexpr int TARGET_CTAS = 2 * 2 * 148;  // ~two waves of two CTAs per SM on 148 SMs
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Byte offsets of every region of a context's device workspace.
+struct Layout {
+  int px, py, pz;
+  long long fstride;
+  size_t esz;
+  size_t q[2], w, roots[3], kshell, clock, coeffs, partials, counter, diag, scratch, run, tiles;
+  size_t total;
+  int nk;
+  int tw, th;
+  std::vector<Tile> tiles_host;
+};
+
+int shell_vectors(double kmin, double kmax, std::vector<int> *out) {
+  // Integer wave vectors with kmin <= |k| <= kmax, kx varying slowest.
+  const int K = (int)std::floor(kmax);
+  int n = 0;
+  for (int a = -K; a <= K; ++a)
+    for (int b = -K; b <= K; ++b)
+      for (int c = -K; c <= K; ++c) {
+        const double m = std::sqrt((double)(a * a + b * b + c * c));
+        if (m >= kmin && m <= kmax) {
+          if (out) {
+            out->push_back(a);
+            out->push_back(b);
+            out->push_back(c);
+          }
+          ++n;
+        }
+      }
+  return n;
+}
+
+int num_sms() {
+  int dev = 0, n = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 148;
+}
+
+// Tiles of one run: TX x TY columns, z split into chunks so that the launch
+// covers the GPU with a couple of waves; chunks of at least 8 planes keep the
+// re-read z-halo (6 planes per chunk) small.
+std::vector<Tile> make_tiles(int nx, int ny, int nz, int tw, int th, int target_ctas) {
+  const int ntx = (nx + tw - 1) / tw, nty = (ny + th - 1) / th;
+  const int ncol = ntx * nty;
+  int nch = std::max(1, (target_ctas + ncol - 1) / ncol);
+  int chunk = std::max(8, (nz + nch - 1) / nch);
+  chunk = std::min(chunk, nz);
+  std::vector<Tile> t;
+  int slot = 0;
+  for (int z0 = 0; z0 < nz; z0 += chunk)
+    for (int j = 0; j < nty; ++j)
+      for (int i = 0; i < ntx; ++i) t.push_back(Tile{0, i * tw, j * th, z0, std::min(nz, z0 + chunk), slot++});
+  return t;
+}
+
+int validate(const mhd_params *p, std::string *why) {
+  auto bad = [&](const char *m) {
+    *why = m;
+    return MHD_EINVAL;
+  };
+  if (!p) return bad("params is NULL");
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return bad("nx, ny, nz must be >= 1");
+  if (p->nx > 4096 || p->ny > 4096 || p->nz > 4096) return bad("nx, ny, nz must be <= 4096");
+  if (!(p->lx > 0 && p->ly > 0 && p->lz > 0)) return bad("box sizes must be > 0");
+  if (!(p->cs > 0)) return bad("cs must be > 0");
+  if (!(p->nu >= 0 && p->eta >= 0)) return bad("nu and eta must be >= 0");
+  if (!(p->f0 >= 0)) return bad("f0 must be >= 0");
+  if (p->f0 > 0) {
+    if (!(p->kmin > 0 && p->kmax >= p->kmin)) return bad("forcing shell needs 0 < kmin <= kmax");
+    if (p->kmax > 64) return bad("kmax must be <= 64");
+    if (shell_vectors(p->kmin, p->kmax, nullptr) == 0) return bad("forcing shell holds no integer wave vector");
+    if (!(p->sigma >= 0 && p->sigma <= 1)) return bad("sigma must be in [0, 1]");
+  }
+  if (!(p->dt_fixed >= 0)) return bad("dt_fixed must be >= 0");
+  if (p->dt_fixed == 0 && !(p->cfl > 0 && p->cfl_visc > 0)) return bad("cfl and cfl_visc must be > 0");
+  if (p->forcing_mode != 0 && p->forcing_mode != 1) return bad("forcing_mode must be 0 or 1");
+  if (p->dtype != MHD_F32 && p->dtype != MHD_F64) return bad("dtype must be MHD_F32 or MHD_F64");
+  if (p->kernel != MHD_KERNEL_AUTO && p->kernel != MHD_KERNEL_SMEM)
+    return bad("kernel variant not available in this build");
+  return MHD_OK;
+}
+
+Layout make_layout(const mhd_params *p) {
+  Layout L;
+  L.esz = p->dtype == MHD_F32 ? 4 : 8;
+  L.px = (int)align_up((size_t)p->nx + OX + RAD, 8);
+  L.py = p->ny + 2 * RAD;
+  L.pz = p->nz + 2 * RAD;
+  L.fstride = (long long)L.px * L.py * L.pz;
+  L.nk = p->f0 > 0 ? shell_vectors(p->kmin, p->kmax, nullptr) : 0;
+  substep_tile_shape(p->dtype, p->kernel, p->tile, &L.tw, &L.th);
+  // The tile table is a function of the parameters alone (not of the device
+  // it runs on), so per-tile reduction partials -- and hence every reduced
+  // value -- come out in the same order on every GPU and in every batch.
+  L.tiles_host = make_tiles(p->nx, p->ny, p->nz, L.tw, L.th, TARGET_CTAS);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes, ALIGN);
+    return at;
+  };
+  const size_t field_set = (size_t)NF * L.fstride * L.esz;
+  L.q[0] = take(field_set);
+  L.q[1] = take(field_set);
+  L.w = take(field_set);
+  const int n[3] = {p->nx, p->ny, p->nz};
+  for (int a = 0; a < 3; ++a) L.roots[a] = take((size_t)n[a] * 2 * L.esz);
+  L.kshell = take(sizeof(int) * 3 * std::max(L.nk, 1));
+  L.clock = take(sizeof(Clock));
+  L.coeffs = take(sizeof(StepCoeffs));
+  L.partials = take(sizeof(double) * NPART * L.tiles_host.size());
+  L.counter = take(sizeof(unsigned int) * 4);
+  L.diag = take(sizeof(double) * NDIAG);
+  L.scratch = take(sizeof(double) * 16);
+  L.run = take(sizeof(RunDesc));
+  L.tiles = take(sizeof(Tile) * L.tiles_host.size());
+  L.total = o;
+  return L;
+}
+
+}  // namespace
+
+struct mhd_ctx {
+  mhd_params p;
+  cudaStream_t stream;
+  Layout L;
+  char *ws;
+  bool owns_ws;
+  RunDesc h_run;
+  RunDesc *d_run;
+  Tile *d_tiles;
+  int ntiles;
+  int grid;  // substep launch grid (persistent CTAs)
+  std::string err;
+};
+
+struct mhd_batch {
+  std::vector<mhd_ctx *> runs;
+  cudaStream_t stream;
+  int dtype, kernel, tile, tw, th;
+  RunDesc *d_runs;
+  Tile *d_tiles;
+  int ntiles, grid;
+  cudaGraphExec_t exec;
+  int graph_steps;
+};
+
+namespace {
+
+int fail(mhd_ctx *ctx, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(mhd_ctx *ctx, int e, const char *what) {
+  return fail(ctx, MHD_ECUDA, "%s: %s", what, cudaGetErrorString((cudaError_t)e));
+}
+
+#define CK(ctx, call)                                            \
+  do {                                                           \
+    int e__ = (int)(call);                                       \
+    if (e__ != 0) return cuda_fail((ctx), e__, #call);           \
+  } while (0)
+
+int read_clock(mhd_ctx *ctx, Clock *c) {
+  CK(ctx, cudaMemcpyAsync(c, ctx->h_run.clock, sizeof(Clock), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return MHD_OK;
+}
+
+int check_status(mhd_ctx *ctx, const Clock &c) {
+  if (c.status & 1)
+    return fail(ctx, MHD_ENONFINITE, "non-finite time step at step %lld (run blew up)", c.step);
+  return MHD_OK;
+}
+
+int enqueue_step(cudaStream_t s, int dtype, int kernel, int tile, int tw, int th,
+                 const RunDesc *runs, const Tile *tiles, int ntiles, int grid) {
+  int e = launch_prologue(dtype, runs, tiles, ntiles, tw, th, s);
+  for (int sub = 0; sub < 3 && e == 0; ++sub)
+    e = launch_substep(dtype, kernel, tile, runs, tiles, ntiles, sub, grid, s);
+  return e;
+}
+
+size_t host_esz(int host_dtype) { return host_dtype == MHD_F32 ? 4 : 8; }
+
+}  // namespace
+
+extern "C" {
+
+void mhd_default_params(mhd_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->nx = p->ny = p->nz = 32;
+  p->lx = p->ly = p->lz = 2.0 * M_PI;
+  p->cs = 1.0;
+  p->nu = p->eta = 5e-3;
+  p->f0 = 0.0;
+  p->kmin = 2.5;
+  p->kmax = 3.5;
+  p->sigma = 0.0;
+  p->seed = 1;
+  p->cfl = 0.4;
+  p->cfl_visc = 0.08;
+  p->dt_fixed = 0.0;
+  p->forcing_mode = 0;
+  p->dtype = MHD_F32;
+  p->kernel = MHD_KERNEL_AUTO;
+  p->tile = 0;
+}
+
+int mhd_workspace_bytes(const mhd_params *p, size_t *bytes) {
+  std::string why;
+  if (validate(p, &why)) return fail(nullptr, MHD_EINVAL, "%s", why.c_str());
+  if (!bytes) return fail(nullptr, MHD_EINVAL, "bytes is NULL");
+  *bytes = make_layout(p).total;
+  return MHD_OK;
+}
+
+int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t workspace_bytes,
+               mhd_ctx **out) {
+  std::string why;
+  if (!out) return fail(nullptr, MHD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (validate(p, &why)) return fail(nullptr, MHD_EINVAL, "%s", why.c_str());
+  mhd_ctx *ctx = new mhd_ctx();
+  ctx->p = *p;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  ctx->L = make_layout(p);
+  const Layout &L = ctx->L;
+  if (workspace) {
+    if (workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) % ALIGN) != 0) {
+      delete ctx;
+      return fail(nullptr, MHD_ENOMEM, "workspace must be >= %zu bytes and 256-byte aligned", L.total);
+    }
+    ctx->ws = static_cast<char *>(workspace);
+    ctx->owns_ws = false;
+  } else {
+    cudaError_t e = cudaMalloc(&ctx->ws, L.total);
+    if (e != cudaSuccess) {
+      delete ctx;
+      return fail(nullptr, MHD_ENOMEM, "cudaMalloc(%zu): %s", L.total, cudaGetErrorString(e));
+    }
+    ctx->owns_ws = true;
+  }
+  auto cleanup = [&](int code) {
+    if (ctx->owns_ws) cudaFree(ctx->ws);
+    g_err = ctx->err;
+    delete ctx;
+    return code;
+  };
+  char *ws = ctx->ws;
+  RunDesc &R = ctx->h_run;
+  std::memset(&R, 0, sizeof(R));
+  R.nx = p->nx;
+  R.ny = p->ny;
+  R.nz = p->nz;
+  R.px = L.px;
+  R.py = L.py;
+  R.pz = L.pz;
+  R.fstride = L.fstride;
+  R.q[0] = ws + L.q[0];
+  R.q[1] = ws + L.q[1];
+  R.w = ws + L.w;
+  for (int a = 0; a < 3; ++a) R.roots[a] = ws + L.roots[a];
+  R.kshell = reinterpret_cast<const int *>(ws + L.kshell);
+  R.nk = L.nk;
+  R.forcing_mode = p->forcing_mode;
+  R.clock = reinterpret_cast<Clock *>(ws + L.clock);
+  R.coeffs = reinterpret_cast<StepCoeffs *>(ws + L.coeffs);
+  R.partials = reinterpret_cast<double *>(ws + L.partials);
+  R.counter = reinterpret_cast<unsigned int *>(ws + L.counter);
+  R.diag = reinterpret_cast<double *>(ws + L.diag);
+  R.cs = p->cs;
+  R.cs2 = p->cs * p->cs;
+  R.nu = p->nu;
+  R.eta = p->eta;
+  R.f0 = p->f0;
+  R.sigma = p->sigma;
+  const double Lb[3] = {p->lx, p->ly, p->lz};
+  const int n[3] = {p->nx, p->ny, p->nz};
+  R.dmin = 1e300;
+  for (int a = 0; a < 3; ++a) {
+    const double h = Lb[a] / n[a];
+    R.inv_h[a] = 1.0 / h;
+    R.kscale[a] = 2.0 * M_PI / Lb[a];
+    R.dmin = std::min(R.dmin, h);
+  }
+  R.cfl = p->cfl;
+  R.cfl_visc = p->cfl_visc;
+  R.dt_fixed = p->dt_fixed;
+  R.seed = p->seed;
+  R.ntiles = (int)L.tiles_host.size();
+  ctx->ntiles = R.ntiles;
+  ctx->d_run = reinterpret_cast<RunDesc *>(ws + L.run);
+  ctx->d_tiles = reinterpret_cast<Tile *>(ws + L.tiles);
+  int bps = 1;
+  if (substep_max_grid(p->dtype, p->kernel, p->tile, &bps) != 0 || bps < 1) bps = 1;
+  ctx->grid = std::min(ctx->ntiles, bps * num_sms());
+
+  // host tables: roots of unity (FP64 cos/sin, rounded to the working
+  // precision), shell list, tiles
+  std::vector<char> roots[3];
+  for (int a = 0; a < 3; ++a) {
+    roots[a].resize((size_t)n[a] * 2 * L.esz);
+    for (int m = 0; m < n[a]; ++m) {
+      const double ang = 2.0 * M_PI * (double)m / n[a];
+      const double c = std::cos(ang), s = std::sin(ang);
+      if (L.esz == 4) {
+        float *r = reinterpret_cast<float *>(roots[a].data());
+        r[2 * m] = (float)c;
+        r[2 * m + 1] = (float)s;
+      } else {
+        double *r = reinterpret_cast<double *>(roots[a].data());
+        r[2 * m] = c;
+        r[2 * m + 1] = s;
+      }
+    }
+  }
+  std::vector<int> shell;
+  if (L.nk) shell_vectors(p->kmin, p->kmax, &shell);
+  cudaStream_t s = ctx->stream;
+  int e = prepare_substep(p->dtype, p->kernel, p->tile);
+  if (!e) e = (int)cudaMemsetAsync(ws, 0, L.total, s);
+  for (int a = 0; a < 3 && !e; ++a)
+    e = (int)cudaMemcpyAsync(ws + L.roots[a], roots[a].data(), roots[a].size(), cudaMemcpyHostToDevice, s);
+  if (!e && L.nk)
+    e = (int)cudaMemcpyAsync(ws + L.kshell, shell.data(), shell.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (!e) e = (int)cudaMemcpyAsync(ctx->d_run, &R, sizeof(R), cudaMemcpyHostToDevice, s);
+  if (!e)
+    e = (int)cudaMemcpyAsync(ctx->d_tiles, L.tiles_host.data(), sizeof(Tile) * L.tiles_host.size(),
+                             cudaMemcpyHostToDevice, s);
+  if (!e) e = (int)cudaStreamSynchronize(s);
+  if (e) {
+    cuda_fail(ctx, e, "mhd_create upload");
+    return cleanup(MHD_ECUDA);
+  }
+  *out = ctx;
+  return MHD_OK;
+}
+
+void mhd_destroy(mhd_ctx *ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->owns_ws) cudaFree(ctx->ws);
+  delete ctx;
+}
+
+int mhd_set_state(mhd_ctx *ctx, const void *host_soa, int host_dtype, double t, int64_t step) {
+  if (!ctx) return fail(nullptr, MHD_EINVAL, "ctx is NULL");
+  if (!host_soa) return fail(ctx, MHD_EINVAL, "host_soa is NULL");
+  if (host_dtype != MHD_F32 && host_dtype != MHD_F64) return fail(ctx, MHD_EINVAL, "bad host_dtype");
+  if (step < 0) return fail(ctx, MHD_EINVAL, "step must be >= 0");
+  const RunDesc &R = ctx->h_run;
+  const size_t npts = (size_t)R.nx * R.ny * R.nz, hb = npts * host_esz(host_dtype);
+  const int dt = ctx->p.dtype;
+  char *dst = static_cast<char *>(R.q[step & 1]);
+  void *staging = R.w;  // dead between steps; holds one host-typed field
+  cudaStream_t s = ctx->stream;
+  for (int f = 0; f < NF; ++f) {
+    CK(ctx, cudaMemcpyAsync(staging, static_cast<const char *>(host_soa) + f * hb, hb,
+                            cudaMemcpyHostToDevice, s));
+    CK(ctx, launch_set_field(dt, host_dtype, staging, dst + (size_t)f * R.fstride * ctx->L.esz, R.nx,
+                             R.ny, R.nz, R.px, R.py, s));
+  }
+  CK(ctx, launch_halo(dt, dst, NF, R.fstride, R.nx, R.ny, R.nz, R.px, R.py, s));
+  Clock c;
+  std::memset(&c, 0, sizeof c);
+  c.t = t;
+  c.step = step;
+  CK(ctx, cudaMemcpyAsync(R.clock, &c, sizeof c, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  return MHD_OK;
+}
+
+int mhd_get_state(mhd_ctx *ctx, void *host_soa, int host_dtype, double *t, int64_t *step) {
+  if (!ctx) return fail(nullptr, MHD_EINVAL, "ctx is NULL");
+  if (host_dtype != MHD_F32 && host_dtype != MHD_F64) return fail(ctx, MHD_EINVAL, "bad host_dtype");
+  Clock c;
+  int rc = read_clock(ctx, &c);
+  if (rc) return rc;
+  if (host_soa) {
+    const RunDesc &R = ctx->h_run;
+    const size_t npts = (size_t)R.nx * R.ny * R.nz, hb = npts * host_esz(host_dtype);
+    const char *src = static_cast<const char *>(R.q[c.step & 1]);
+    void *staging = R.w;
+    cudaStream_t s = ctx->stream;
+    for (int f = 0; f < NF; ++f) {
+      CK(ctx, launch_get_field(ctx->p.dtype, host_dtype, src + (size_t)f * R.fstride * ctx->L.esz,
+                               staging, R.nx, R.ny, R.nz, R.px, R.py, s));
+      CK(ctx, cudaMemcpyAsync(static_cast<char *>(host_soa) + f * hb, staging, hb,
+                              cudaMemcpyDeviceToHost, s));
+    }
+    CK(ctx, cudaStreamSynchronize(s));
+  }
+  if (t) *t = c.t;
+  if (step) *step = c.step;
+  return check_status(ctx, c);
+}
+
+int mhd_step(mhd_ctx *ctx, int nsteps) {
+  if (!ctx) return fail(nullptr, MHD_EINVAL, "ctx is NULL");
+  if (nsteps < 0) return fail(ctx, MHD_EINVAL, "nsteps must be >= 0");
+  for (int i = 0; i < nsteps; ++i) {
+    int e = enqueue_step(ctx->stream, ctx->p.dtype, ctx->p.kernel, ctx->p.tile, ctx->L.tw, ctx->L.th,
+                         ctx->d_run, ctx->d_tiles, ctx->ntiles, ctx->grid);
+    if (e) return cuda_fail(ctx, e, "mhd_step launch");
+  }
+  return MHD_OK;
+}
+
+int mhd_step_timed(mhd_ctx *ctx, int nsteps, double *stage_ms, double *total_ms) {
+  if (!ctx) return fail(nullptr, MHD_EINVAL, "ctx is NULL");
+  if (nsteps < 0) return fail(ctx, MHD_EINVAL, "nsteps must be >= 0");
+  if (!stage_ms || !total_ms) return fail(ctx, MHD_EINVAL, "stage_ms and total_ms must be non-NULL");
+  if (nsteps == 0) return MHD_OK;
+  std::vector<cudaEvent_t> ev((size_t)4 * nsteps + 1, nullptr);
+  int rc = MHD_OK;
+  for (auto &e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      rc = fail(ctx, MHD_ECUDA, "cudaEventCreate failed");
+      break;
+    }
+  cudaStream_t s = ctx->stream;
+  for (int i = 0; i < nsteps && rc == MHD_OK; ++i) {
+    int e = (int)cudaEventRecord(ev[4 * i], s);
+    if (!e) e = launch_prologue(ctx->p.dtype, ctx->d_run, ctx->d_tiles, ctx->ntiles, ctx->L.tw, ctx->L.th, s);
+    for (int sub = 0; sub < 3 && !e; ++sub) {
+      e = (int)cudaEventRecord(ev[4 * i + 1 + sub], s);
+      if (!e) e = launch_substep(ctx->p.dtype, ctx->p.kernel, ctx->p.tile, ctx->d_run, ctx->d_tiles,
+                                 ctx->ntiles, sub, ctx->grid, s);
+    }
+    if (e) rc = cuda_fail(ctx, e, "mhd_step_timed launch");
+  }
+  if (rc == MHD_OK) {
+    int e = (int)cudaEventRecord(ev[4 * nsteps], s);
+    if (!e) e = (int)cudaEventSynchronize(ev[4 * nsteps]);
+    if (e) rc = cuda_fail(ctx, e, "mhd_step_timed sync");
+  }
+  if (rc == MHD_OK) {
+    for (int i = 0; i < nsteps; ++i)
+      for (int st = 0; st < 4; ++st) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[4 * i + st], ev[4 * i + st + 1]);
+        stage_ms[st] += ms;
+      }
+    float tot = 0.f;
+    cudaEventElapsedTime(&tot, ev[0], ev[4 * nsteps]);
+    *total_ms += tot;
+  }
+  for (auto &e : ev)
+    if (e) cudaEventDestroy(e);
+  return rc;
+}
+
+int mhd_diagnostics(mhd_ctx *ctx, double *out) {
+  if (!ctx) return fail(nullptr, MHD_EINVAL, "ctx is NULL");
+  if (!out) return fail(ctx, MHD_EINVAL, "out is NULL");
+  CK(ctx, launch_diagnostics(ctx->p.dtype, ctx->d_run, ctx->h_run, ctx->d_tiles, ctx->ntiles,
+                             ctx->L.tw, ctx->L.th, ctx->stream));
+  CK(ctx, cudaMemcpyAsync(out, ctx->h_run.diag, sizeof(double) * NDIAG, cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  Clock c;
+  int rc = read_clock(ctx, &c);
+  if (rc) return rc;
+  return check_status(ctx, c);
+}
+
+int mhd_reduce(mhd_ctx *ctx, int kind, double *out) {
+  if (!ctx) return fail(nullptr, MHD_EINVAL, "ctx is NULL");
+  if (kind < 0 || kind >= MHD_NREDUCE) return fail(ctx, MHD_EINVAL, "unknown reduction kind %d", kind);
+  if (!out) return fail(ctx, MHD_EINVAL, "out is NULL");
+  double all[MHD_NREDUCE];
+  int rc = mhd_diagnostics(ctx, all);
+  if (rc) return rc;
+  *out = all[kind];
+  return MHD_OK;
+}
+
+int mhd_time(mhd_ctx *ctx, double *t, double *dt_last, int64_t *step) {
+  if (!ctx) return fail(nullptr, MHD_EINVAL, "ctx is NULL");
+  Clock c;
+  int rc = read_clock(ctx, &c);
+  if (rc) return rc;
+  if (t) *t = c.t;
+  if (dt_last) *dt_last = c.dt_last;
+  if (step) *step = c.step;
+  return check_status(ctx, c);
+}
+
+int mhd_sync(mhd_ctx *ctx) {
+  if (!ctx) return fail(nullptr, MHD_EINVAL, "ctx is NULL");
+  Clock c;
+  int rc = read_clock(ctx, &c);
+  if (rc) return rc;
+  return check_status(ctx, c);
+}
+
+int mhd_forcing_draw(mhd_ctx *ctx, int64_t step, double *out) {
+  if (!ctx) return fail(nullptr, MHD_EINVAL, "ctx is NULL");
+  if (!out) return fail(ctx, MHD_EINVAL, "out is NULL");
+  if (ctx->h_run.nk == 0) return fail(ctx, MHD_EINVAL, "run has no forcing (f0 = 0)");
+  if (step < 0) return fail(ctx, MHD_EINVAL, "step must be >= 0");
+  double *scratch = reinterpret_cast<double *>(ctx->ws + ctx->L.scratch);
+  CK(ctx, launch_forcing_draw(ctx->d_run, step, scratch, ctx->stream));
+  CK(ctx, cudaMemcpyAsync(out, scratch, sizeof(double) * 13, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return MHD_OK;
+}
+
+int mhd_eval_rhs(mhd_ctx *ctx, int64_t step, double dt_forcing, void *host_rhs, int host_dtype) {
+  if (!ctx) return fail(nullptr, MHD_EINVAL, "ctx is NULL");
+  if (!host_rhs) return fail(ctx, MHD_EINVAL, "host_rhs is NULL");
+  if (host_dtype != MHD_F32 && host_dtype != MHD_F64) return fail(ctx, MHD_EINVAL, "bad host_dtype");
+  if (step < 0) return fail(ctx, MHD_EINVAL, "step must be >= 0");
+  Clock c;
+  int rc = read_clock(ctx, &c);
+  if (rc) return rc;
+  const RunDesc &R = ctx->h_run;
+  const int par = (int)(c.step & 1);
+  cudaStream_t s = ctx->stream;
+  // substep 0 with dt = 1 leaves w = RHS; the other state buffer is
+  // overwritten (it is dead between steps) and serves as staging.
+  CK(ctx, launch_coeffs(ctx->p.dtype, ctx->d_run, step, 1.0, dt_forcing, par, s));
+  CK(ctx, launch_substep(ctx->p.dtype, ctx->p.kernel, ctx->p.tile, ctx->d_run, ctx->d_tiles,
+                         ctx->ntiles, 0, ctx->grid, s));
+  const size_t npts = (size_t)R.nx * R.ny * R.nz, hb = npts * host_esz(host_dtype);
+  void *staging = R.q[par ^ 1];
+  for (int f = 0; f < NF; ++f) {
+    CK(ctx, launch_get_field(ctx->p.dtype, host_dtype,
+                             static_cast<const char *>(R.w) + (size_t)f * R.fstride * ctx->L.esz,
+                             staging, R.nx, R.ny, R.nz, R.px, R.py, s));
+    CK(ctx, cudaMemcpyAsync(static_cast<char *>(host_rhs) + f * hb, staging, hb,
+                            cudaMemcpyDeviceToHost, s));
+  }
+  CK(ctx, cudaStreamSynchronize(s));
+  // the staging buffer held the other parity's state: rebuild nothing (it is
+  // dead), but the step constants were overwritten; the next prologue
+  // rewrites them.
+  return MHD_OK;
+}
+
+const char *mhd_last_error(const mhd_ctx *ctx) {
+  if (ctx) return ctx->err.c_str();
+  return g_err.c_str();
+}
+
+// ---- batches ----------------------------------------------------------------
+
+int mhd_batch_create(mhd_ctx *const *runs, int nruns, mhd_batch **out) {
+  if (!out) return fail(nullptr, MHD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!runs || nruns < 1) return fail(nullptr, MHD_EINVAL, "need at least one run");
+  mhd_ctx *r0 = runs[0];
+  if (!r0) return fail(nullptr, MHD_EINVAL, "runs[0] is NULL");
+  std::vector<RunDesc> descs;
+  std::vector<Tile> tiles;
+  for (int i = 0; i < nruns; ++i) {
+    mhd_ctx *r = runs[i];
+    if (!r) return fail(nullptr, MHD_EINVAL, "runs[%d] is NULL", i);
+    if (r->p.dtype != r0->p.dtype || r->stream != r0->stream || r->p.kernel != r0->p.kernel ||
+        r->p.tile != r0->p.tile)
+      return fail(nullptr, MHD_EINVAL, "runs of a batch must share dtype, stream, kernel and tile");
+    for (int j = 0; j < i; ++j)
+      if (runs[j] == r) return fail(nullptr, MHD_EINVAL, "run %d appears twice", i);
+    descs.push_back(r->h_run);
+    for (const Tile &t : r->L.tiles_host) {
+      Tile u = t;
+      u.run = i;
+      tiles.push_back(u);
+    }
+  }
+  mhd_batch *b = new mhd_batch();
+  b->runs.assign(runs, runs + nruns);
+  b->stream = r0->stream;
+  b->dtype = r0->p.dtype;
+  b->kernel = r0->p.kernel;
+  b->tile = r0->p.tile;
+  b->tw = r0->L.tw;
+  b->th = r0->L.th;
+  b->ntiles = (int)tiles.size();
+  b->exec = nullptr;
+  b->graph_steps = 0;
+  int bps = 1;
+  if (substep_max_grid(b->dtype, b->kernel, b->tile, &bps) != 0 || bps < 1) bps = 1;
+  b->grid = std::min(b->ntiles, bps * num_sms());
+  cudaError_t e = cudaMalloc(&b->d_runs, sizeof(RunDesc) * descs.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_tiles, sizeof(Tile) * tiles.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_runs, descs.data(), sizeof(RunDesc) * descs.size(), cudaMemcpyHostToDevice,
+                        b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(Tile) * tiles.size(), cudaMemcpyHostToDevice,
+                        b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    cudaFree(b->d_runs);
+    cudaFree(b->d_tiles);
+    delete b;
+    return fail(nullptr, MHD_ECUDA, "mhd_batch_create: %s", cudaGetErrorString(e));
+  }
+  *out = b;
+  return MHD_OK;
+}
+
+int mhd_batch_step(mhd_batch *b, int nsteps) {
+  if (!b) return fail(nullptr, MHD_EINVAL, "batch is NULL");
+  if (nsteps < 0) return fail(nullptr, MHD_EINVAL, "nsteps must be >= 0");
+  cudaStream_t s = b->stream;
+  // Steps are captured once into a graph of graph_steps steps and replayed;
+  // a remainder is launched directly.  The device clocks advance on replay,
+  // so the same graph serves every later call.
+  if (!b->exec && nsteps >= 2 && s != nullptr) {
+    const int g = std::min(nsteps, 16);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    int le = 0;
+    for (int i = 0; i < g && e == cudaSuccess && !le; ++i)
+      le = enqueue_step(s, b->dtype, b->kernel, b->tile, b->tw, b->th, b->d_runs, b->d_tiles,
+                        b->ntiles, b->grid);
+    cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+    if (e == cudaSuccess && !le && e2 == cudaSuccess) {
+      if (cudaGraphInstantiate(&b->exec, graph, 0) == cudaSuccess) b->graph_steps = g;
+      else b->exec = nullptr;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+  }
+  int done = 0;
+  if (b->exec) {
+    for (; done + b->graph_steps <= nsteps; done += b->graph_steps) {
+      cudaError_t e = cudaGraphLaunch(b->exec, s);
+      if (e != cudaSuccess) return fail(nullptr, MHD_ECUDA, "graph launch: %s", cudaGetErrorString(e));
+    }
+  }
+  for (; done < nsteps; ++done) {
+    int e = enqueue_step(s, b->dtype, b->kernel, b->tile, b->tw, b->th, b->d_runs, b->d_tiles,
+                         b->ntiles, b->grid);
+    if (e) return fail(nullptr, MHD_ECUDA, "batch step launch: %s", cudaGetErrorString((cudaError_t)e));
+  }
+  return MHD_OK;
+}
+
+void mhd_batch_destroy(mhd_batch *b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  cudaFree(b->d_runs);
+  cudaFree(b->d_tiles);
+  delete b;
+}
+
+}  // extern "C"

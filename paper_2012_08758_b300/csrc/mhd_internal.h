@@ -1,0 +1,93 @@
+// Internal structures shared by the host side of the C ABI and the kernels.
+// Not part of the public interface (include/mhd.h is).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mhd {
+
+constexpr int NF = 7;            // ln rho, u_x, u_y, u_z, A_x, A_y, A_z
+constexpr int RAD = 3;           // stencil radius r of the 6th-order scheme (Sec. 3.1)
+constexpr int OX = 4;            // padded x index of interior point 0 (one spare column
+                                 // keeps interior rows 16-byte aligned)
+constexpr int OY = 3, OZ = 3;    // padded y / z index of interior point 0
+constexpr int NDIAG = 9;         // quantities of mhd_diagnostics
+constexpr int NPART = 8;         // doubles per reduction tile
+
+// Device-resident clock of one run: time, last dt and index of the state
+// currently held in q[step & 1].  Advanced on the device by the step
+// prologue, so a captured sequence of steps can be replayed.
+struct Clock {
+  double t;
+  double dt_last;
+  long long step;
+  int status;   // bit 0: the time-step reduction saw a non-finite value
+  int pad;
+};
+
+// Per-step constants written by the prologue and read by every substep of
+// that step: dt and the forcing realisation of Eqs. 4-6 (amplitude already
+// folded in: fa = N a, fb = N b).
+struct StepCoeffs {
+  double dt;
+  double fa[3], fb[3];
+  double cphi, sphi;   // e^{i phi}
+  int kmod[3];         // k mod N per axis, in [0, N)
+  int forcing;         // 1: apply the forcing this step
+  int parity;          // state of this step lives in q[parity] at substep 0
+  int pad;
+};
+
+// Everything a kernel needs to know about one run, resident in device memory.
+struct RunDesc {
+  int nx, ny, nz;
+  int px, py, pz;           // padded extents; px is the row pitch
+  long long fstride;        // elements per field (px * py * pz)
+  void *q[2];               // state buffers, NF fields each
+  void *w;                  // RK3-2N register, NF fields
+  const void *roots[3];     // e^{2 pi i m / N_a}, m < N_a, working precision
+  const int *kshell;        // forcing shell, 3 ints per vector
+  int nk;
+  int forcing_mode;
+  Clock *clock;
+  StepCoeffs *coeffs;
+  double *partials;         // NPART doubles per reduction tile of this run
+  unsigned int *counter;    // last-tile-done counters [0]: dt, [1]: diagnostics
+  double *diag;             // NDIAG doubles
+  double cs, cs2, nu, eta, f0, sigma;
+  double inv_h[3];          // 1 / grid spacing per axis
+  double kscale[3];         // 2 pi / L per axis (physical wave vector)
+  double cfl, cfl_visc, dt_fixed, dmin;
+  unsigned long long seed;
+  int ntiles;               // reduction tiles of this run
+  int pad;
+};
+
+// A unit of work: an x-y tile of one run and a range [z0, z1) of interior
+// planes.  slot = index of this tile among the run's tiles.
+struct Tile {
+  int run, x0, y0, z0, z1, slot;
+};
+
+// ---- launchers (kernels.cu / reduce.cu) -------------------------------------
+// dtype: 0 = float, 1 = double.  All return a cudaError_t as int.
+int launch_prologue(int dtype, const RunDesc *runs, const Tile *tiles, int ntiles, int tw, int th,
+                    cudaStream_t s);
+int launch_substep(int dtype, int kernel, int tile, const RunDesc *runs, const Tile *tiles,
+                   int ntiles, int substep, int grid, cudaStream_t s);
+int prepare_substep(int dtype, int kernel, int tile);
+int substep_tile_shape(int dtype, int kernel, int tile, int *tx, int *ty);
+int substep_max_grid(int dtype, int kernel, int tile, int *blocks_per_sm);
+int launch_halo(int dtype, void *fields, int nfields, long long fstride, int nx, int ny, int nz,
+                int px, int py, cudaStream_t s);
+int launch_set_field(int dtype, int host_dtype, const void *src, void *dst_field, int nx, int ny,
+                     int nz, int px, int py, cudaStream_t s);
+int launch_get_field(int dtype, int host_dtype, const void *src_field, void *dst, int nx, int ny,
+                     int nz, int px, int py, cudaStream_t s);
+int launch_diagnostics(int dtype, const RunDesc *run_dev, const RunDesc &run_host,
+                       const Tile *tiles, int ntiles, int tw, int th, cudaStream_t s);
+int launch_coeffs(int dtype, const RunDesc *run, int64_t draw_step, double dt_update,
+                  double dt_forcing, int parity, cudaStream_t s);
+int launch_forcing_draw(const RunDesc *run, int64_t step, double *out13, cudaStream_t s);
+
+}  // namespace mhd

@@ -1,0 +1,122 @@
+// Stencil weights and the right-hand side of the isothermal MHD equations
+// (arXiv:2012.08758, Sec. 4 Eqs. 1-3), shared by every substep kernel.
+#pragma once
+#include "mhd_internal.h"
+
+namespace mhd {
+
+// 6th-order central weights (Sec. 2).  First derivative:
+//   f' = [45 (f1 - f-1) - 9 (f2 - f-2) + (f3 - f-3)] / (60 h)
+// second derivative:
+//   f'' = [-490 f0 + 270 (f1 + f-1) - 27 (f2 + f-2) + 2 (f3 + f-3)] / (180 h^2)
+// mixed derivative on the two diagonals of the a-b plane (the diagonal
+// points of the stencil figure of Sec. 3.1):
+//   f_ab = [270 S1 - 27 S2 + 2 S3] / (720 h_a h_b),
+//   S_s = f(+s,+s) + f(-s,-s) - f(+s,-s) - f(-s,+s).
+__host__ __device__ constexpr double W1(int s) {
+  return s == 1 ? 45.0 / 60.0 : s == 2 ? -9.0 / 60.0 : s == 3 ? 1.0 / 60.0 : 0.0;
+}
+__host__ __device__ constexpr double W2(int s) {
+  return s == 0 ? -490.0 / 180.0 : s == 1 ? 270.0 / 180.0 : s == 2 ? -27.0 / 180.0 : 2.0 / 180.0;
+}
+__host__ __device__ constexpr double WM(int s) {
+  return s == 1 ? 270.0 / 720.0 : s == 2 ? -27.0 / 720.0 : s == 3 ? 2.0 / 720.0 : 0.0;
+}
+
+// Williamson (1980) low-storage RK3: w <- alpha_s w + dt RHS, q <- q + beta_s w.
+__host__ __device__ constexpr double RK_ALPHA(int s) {
+  return s == 0 ? 0.0 : s == 1 ? -5.0 / 9.0 : -153.0 / 128.0;
+}
+__host__ __device__ constexpr double RK_BETA(int s) {
+  return s == 0 ? 1.0 / 3.0 : s == 1 ? 15.0 / 16.0 : 8.0 / 15.0;
+}
+
+// Per-run stencil and physics constants in the working precision.
+template <typename T>
+struct Coefs {
+  T c1[3][4];   // first-derivative weights / h, per axis
+  T c2[3][4];   // second-derivative weights / h^2, per axis
+  T cm[3][4];   // mixed weights / (h_a h_b), index by the pair (xy=0, xz=1, yz=2)
+  T cs2, nu, eta;
+  __device__ void load(const RunDesc &R) {
+    for (int a = 0; a < 3; ++a)
+      for (int s = 0; s < 4; ++s) {
+        c1[a][s] = T(W1(s) * R.inv_h[a]);
+        c2[a][s] = T(W2(s) * R.inv_h[a] * R.inv_h[a]);
+      }
+    const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+    for (int p = 0; p < 3; ++p)
+      for (int s = 0; s < 4; ++s) cm[p][s] = T(WM(s) * R.inv_h[pa[p]] * R.inv_h[pb[p]]);
+    cs2 = T(R.cs2);
+    nu = T(R.nu);
+    eta = T(R.eta);
+  }
+};
+
+// Derivatives at one point, as delivered by a kernel variant.
+template <typename T>
+struct Derivs {
+  T lnr, u[3], A[3];   // centre values
+  T g[3];              // grad ln rho
+  T G[3][3];           // G[a][b] = d u_a / d x_b
+  T gA[3][3];          // gA[a][b] = d A_a / d x_b
+  T lapu[3];           // Laplacian of u_a
+  T gdu[3];            // (grad div u)_a = sum_b d_a d_b u_b
+  T lapA[3];           // Laplacian of A_a
+  T jc[3];             // j = grad div A - lap A with the d_a d_a A_a terms
+                       // cancelled analytically (mu0 = 1)
+};
+
+// dq/dt of Eqs. 1-3 at one point; f = forcing (already evaluated).
+template <typename T>
+__device__ __forceinline__ void rhs_point(const Derivs<T> &d, const Coefs<T> &c, const T f[3],
+                                          T out[NF]) {
+  const T rho_inv = exp(-d.lnr);
+  const T divu = d.G[0][0] + d.G[1][1] + d.G[2][2];
+  const T B[3] = {d.gA[2][1] - d.gA[1][2], d.gA[0][2] - d.gA[2][0], d.gA[1][0] - d.gA[0][1]};
+  // Eq. 1: D ln rho / Dt = -div u
+  out[0] = -(d.u[0] * d.g[0] + d.u[1] * d.g[1] + d.u[2] * d.g[2]) - divu;
+  const T third = T(1.0 / 3.0);
+  const T jxB[3] = {d.jc[1] * B[2] - d.jc[2] * B[1], d.jc[2] * B[0] - d.jc[0] * B[2],
+                    d.jc[0] * B[1] - d.jc[1] * B[0]};
+  const T uxB[3] = {d.u[1] * B[2] - d.u[2] * B[1], d.u[2] * B[0] - d.u[0] * B[2],
+                    d.u[0] * B[1] - d.u[1] * B[0]};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    // traceless rate of strain times grad ln rho
+    T Sg = T(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      T S = T(0.5) * (d.G[a][b] + d.G[b][a]);
+      if (a == b) S -= third * divu;
+      Sg += S * d.g[b];
+    }
+    const T adv = d.u[0] * d.G[a][0] + d.u[1] * d.G[a][1] + d.u[2] * d.G[a][2];
+    // Eq. 2
+    out[1 + a] = -adv - c.cs2 * d.g[a] + jxB[a] * rho_inv +
+                 c.nu * (d.lapu[a] + third * d.gdu[a] + T(2) * Sg) + f[a];
+    // Eq. 3 (diffusive gauge)
+    out[4 + a] = uxB[a] + c.eta * d.lapA[a];
+  }
+}
+
+// Complex product helpers for the forcing phase.
+template <typename T>
+struct Cplx {
+  T re, im;
+};
+template <typename T>
+__device__ __forceinline__ Cplx<T> cmul(Cplx<T> a, Cplx<T> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+
+// Periodic images of interior index i along an axis of n points: all
+// j = i + m n with -RAD <= j < n + RAD.  Returns the count (<= 7).
+__device__ __forceinline__ int periodic_images(int i, int n, int *out) {
+  int j = -RAD + (i + RAD) % n;
+  int c = 0;
+  for (; j < n + RAD; j += n) out[c++] = j;
+  return c;
+}
+
+}  // namespace mhd

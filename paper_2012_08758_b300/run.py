@@ -1,0 +1,129 @@
+"""Convenience wrappers over the C ABI: a ``Run`` owns one context whose
+device workspace is a PyTorch CUDA tensor and whose stream is a PyTorch
+stream; a ``Batch`` steps several runs together (one launch per kernel stage,
+CUDA-graph replay)."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import binding as B
+
+
+_STREAMS = {}
+
+
+def default_stream(device):
+    """One non-legacy PyTorch stream per device, shared by all runs on it
+    (runs of a batch must share a stream; graph capture needs a non-legacy
+    stream)."""
+    import torch
+
+    key = str(device)
+    if key not in _STREAMS:
+        _STREAMS[key] = torch.cuda.Stream(device=device)
+    return _STREAMS[key]
+
+
+class Run:
+    """One simulation on one GPU.
+
+    Keyword arguments are fields of ``mhd_params`` (nx, ny, nz, nu, eta, f0,
+    sigma, seed, dtype, ...).  ``n`` sets nx = ny = nz."""
+
+    def __init__(self, n: int | None = None, device=None, stream=None, **params):
+        import torch
+
+        if n is not None:
+            params.setdefault("nx", n)
+            params.setdefault("ny", n)
+            params.setdefault("nz", n)
+        self.params = B.mhd_default_params(**params)
+        self.device = torch.device(device if device is not None else "cuda")
+        self.stream = stream if stream is not None else default_stream(self.device)
+        self.nbytes = B.mhd_workspace_bytes(self.params)
+        # allocate on the run's stream so the caching allocator never hands
+        # this block to another stream while the library still uses it
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            self._ws = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=self.device)
+            ptr = self._ws.data_ptr()
+            ptr = (ptr + 255) // 256 * 256
+            self.ctx = B.mhd_create(self.params, self.stream.cuda_stream, ptr, self.nbytes)
+
+    @property
+    def shape(self):
+        p = self.params
+        return (7, p.nz, p.ny, p.nx)
+
+    @property
+    def cells(self) -> int:
+        p = self.params
+        return p.nx * p.ny * p.nz
+
+    def set_state(self, q: np.ndarray, t: float = 0.0, step: int = 0) -> None:
+        assert q.shape == self.shape, (q.shape, self.shape)
+        B.mhd_set_state(self.ctx, q, t, step)
+
+    def get_state(self, dtype=np.float64):
+        return B.mhd_get_state(self.ctx, shape=self.shape, dtype=dtype)
+
+    def step(self, n: int = 1) -> None:
+        B.mhd_step(self.ctx, n)
+
+    def diagnostics(self) -> dict:
+        return B.mhd_diagnostics(self.ctx)
+
+    def reduce(self, kind: int) -> float:
+        return B.mhd_reduce(self.ctx, kind)
+
+    def time(self):
+        return B.mhd_time(self.ctx)
+
+    def sync(self) -> None:
+        B.mhd_sync(self.ctx)
+
+    def forcing_draw(self, step: int) -> dict:
+        return B.mhd_forcing_draw(self.ctx, step)
+
+    def eval_rhs(self, step: int = 0, dt_forcing: float = 0.0, dtype=np.float64):
+        return B.mhd_eval_rhs(self.ctx, self.shape, step, dt_forcing, dtype)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            B.mhd_destroy(self.ctx)
+            self.ctx = None
+            self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Independent runs stepped together; each run's result is the one it
+    gives alone."""
+
+    def __init__(self, runs):
+        self.runs = list(runs)
+        self.handle = B.mhd_batch_create([r.ctx for r in self.runs])
+
+    def step(self, n: int = 1) -> None:
+        B.mhd_batch_step(self.handle, n)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            B.mhd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,295 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.  Tolerances (relative L-infinity per field, scale =
+max |oracle field|): FP64 1e-12, FP32 2e-5 for states; FP32 RHS 1e-5."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2012_08758_b300 import inputs
+from tests.gpu_util import gpu_params, oracle_params, rel_linf
+from tests.states import coords, k2sq_mod, rk3_gain
+
+pytestmark = pytest.mark.gpu
+
+C1 = dict(nx=32, ny=32, nz=32, nu=5e-3, eta=5e-3, f0=0.02, sigma=0.0, kmin=2.5, kmax=3.5, seed=1,
+          cfl=0.4)
+
+
+def make_run(**kw):
+    from paper_2012_08758_b300.run import Run
+    return Run(**gpu_params(**kw))
+
+
+# --------------------------------------------------------------------------
+# Forcing draw: integer k bit-exact, the rest to FP64 rounding
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("seed,sigma,shell", [(1, 0.0, (2.5, 3.5)), (123456789, 1.0, (4.5, 5.5)),
+                                              (2**62 + 7, 0.3, (1.0, 2.0))])
+def test_forcing_draw_matches_oracle(seed, sigma, shell):
+    kw = dict(nx=16, ny=16, nz=16, f0=0.02, sigma=sigma, kmin=shell[0], kmax=shell[1], seed=seed)
+    run = make_run(**kw)
+    p = oracle_params(**kw)
+    for step in (0, 1, 2, 17, 1000, 123456):
+        g = run.forcing_draw(step)
+        o = O.forcing_draw(p, step)
+        assert g["k"] == o.k
+        assert abs(g["phi"] - o.phi) < 1e-14
+        for key in ("e", "a", "b"):
+            np.testing.assert_allclose(g[key], getattr(o, key), atol=1e-14)
+    run.close()
+
+
+# --------------------------------------------------------------------------
+# Right-hand side through the fused substep kernel
+# --------------------------------------------------------------------------
+SHAPES = [(32, 32, 32), (37, 23, 11), (40, 8, 20), (12, 9, 1), (16, 1, 1), (1, 1, 1)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_rhs_matches_oracle(shape, dtype, tol):
+    nx, ny, nz = shape
+    kw = dict(nx=nx, ny=ny, nz=nz, nu=0.02, eta=0.03, cs=1.1, f0=0.05, sigma=0.7, kmin=1.0,
+              kmax=2.0, seed=5, dtype=dtype)
+    q = inputs.random_modes_state(nx, ny, nz, seed=3, amp=0.3) + inputs.noise_state(nx, ny, nz, seed=4,
+                                                                                    amp=0.02)
+    run = make_run(**kw)
+    run.set_state(q)
+    got = run.eval_rhs(step=9, dt_forcing=0.05)
+    p = oracle_params(**kw)
+    F = O.forcing_draw(p, 9, dt=0.05)
+    want = O.rhs(p, q, F)
+    err = rel_linf(got, want)
+    assert err.max() < tol, err
+    run.close()
+
+
+# --------------------------------------------------------------------------
+# Full steps (C1: 32^3, forcing, CFL dt, 20 steps)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_c1_step_parity(dtype, tol):
+    kw = dict(C1, dtype=dtype)
+    q0 = inputs.seed_field_state(32, seed=0)
+    run = make_run(**kw)
+    run.set_state(q0)
+    p = oracle_params(**kw)
+    q = q0.copy()
+    t_or = 0.0
+    done = 0
+    for target in (1, 20):
+        run.step(target - done)
+        t_o, dts = O.run(p, q, target - done, step0=done, t0=t_or)
+        t_or = t_o
+        done = target
+        got, t_gpu, step_gpu = run.get_state()
+        assert step_gpu == target
+        assert abs(t_gpu - t_or) <= (1e-13 if dtype == "f64" else 1e-6) * t_or
+        err = rel_linf(got, q)
+        assert err.max() < tol, (target, err)
+    run.close()
+
+
+@pytest.mark.parametrize("shape", [(37, 23, 11), (24, 24, 1), (1, 1, 1), (9, 40, 7)])
+def test_ragged_and_degenerate_step_parity(shape):
+    nx, ny, nz = shape
+    kw = dict(nx=nx, ny=ny, nz=nz, nu=0.01, eta=0.01, f0=0.05, sigma=1.0, kmin=1.0, kmax=2.0,
+              seed=11, dtype="f64")
+    q0 = inputs.random_modes_state(nx, ny, nz, seed=8, amp=0.2)
+    run = make_run(**kw)
+    run.set_state(q0)
+    run.step(4)
+    got, t, _ = run.get_state()
+    q = q0.copy()
+    O.run(oracle_params(**kw), q, 4)
+    err = rel_linf(got, q)
+    assert err.max() < 1e-12, err
+    run.close()
+
+
+def test_forcing_once_per_step_mode():
+    kw = dict(nx=20, ny=16, nz=12, nu=0.01, eta=0.01, f0=0.05, sigma=0.5, kmin=1.0, kmax=2.0,
+              seed=3, forcing_mode=1, dtype="f64")
+    q0 = inputs.random_modes_state(20, 16, 12, seed=2, amp=0.1)
+    run = make_run(**kw)
+    run.set_state(q0)
+    run.step(3)
+    got, _, _ = run.get_state()
+    q = q0.copy()
+    O.run(oracle_params(**kw), q, 3)
+    assert rel_linf(got, q).max() < 1e-12
+    run.close()
+
+
+def test_fixed_dt_and_clock():
+    kw = dict(nx=16, ny=16, nz=16, dt_fixed=1.19209e-3, dtype="f64")
+    q0 = inputs.uniform_state(16, seed=1, lo=0.0, hi=0.1)
+    run = make_run(**kw)
+    run.set_state(q0, t=2.0, step=7)
+    run.step(5)
+    got, t, step = run.get_state()
+    assert step == 12 and abs(t - (2.0 + 5 * 1.19209e-3)) < 1e-14
+    q = q0.copy()
+    O.run(oracle_params(**kw), q, 5, step0=7)
+    assert rel_linf(got, q).max() < 1e-12
+    tt, dtl, st = run.time()
+    assert dtl == 1.19209e-3 and st == 12
+    run.close()
+
+
+# --------------------------------------------------------------------------
+# Closed forms checked directly on the GPU (also at full size)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n,dtype,tol", [(24, "f64", 1e-13), (64, "f32", 2e-6)])
+def test_beltrami_decay_on_gpu(n, dtype, tol):
+    k, eta, dt, ns = 2, 0.05, 0.02, 6
+    run = make_run(nx=n, ny=n, nz=n, eta=eta, nu=0.01, dt_fixed=dt, dtype=dtype)
+    X, Y, Z = coords(n, n, n)
+    q = np.zeros((7, n, n, n))
+    q[4], q[5] = np.sin(k * Z), np.cos(k * Z)
+    run.set_state(q)
+    run.step(ns)
+    got, _, _ = run.get_state()
+    g = rk3_gain(-eta * k2sq_mod(k, 2 * math.pi / n) * dt) ** ns
+    assert np.abs(got[4] - g * np.sin(k * Z)).max() < tol
+    assert np.abs(got[5] - g * np.cos(k * Z)).max() < tol
+    assert np.abs(got[[0, 1, 2, 3, 6]]).max() < tol
+    run.close()
+
+
+@pytest.mark.slow
+def test_full_size_256_sampled_rhs_and_beltrami():
+    """The 256^3 FP32 launch configuration of the benchmark: RHS at sampled
+    points against the oracle point by point, and the Beltrami closed form
+    after full steps."""
+    n = 256
+    kw = dict(nx=n, ny=n, nz=n, nu=2e-4, eta=2e-4, f0=0.02, sigma=1.0, kmin=2.5, kmax=3.5,
+              seed=1, dtype="f32")
+    q = inputs.random_modes_state(n, seed=21, amp=0.2, kmax=4, nmodes=4)
+    q += inputs.noise_state(n, seed=22, amp=1e-3)
+    run = make_run(**kw)
+    run.set_state(q)
+    got = run.eval_rhs(step=4, dt_forcing=0.01)
+    rng = np.random.default_rng(0)
+    pts = [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(200)]
+    pts += [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n - 1, 3), (n - 3, 2, n - 1)]
+    p = oracle_params(**kw)
+    F = O.forcing_draw(p, 4, dt=0.01)
+    want = O.rhs_at(p, q, pts, F)
+    g = np.array([[got[f, k, j, i] for f in range(7)] for (i, j, k) in pts])
+    scale = np.abs(want).max(axis=0)
+    assert (np.abs(g - want).max(axis=0) / scale).max() < 1e-5
+    run.close()
+    del q, got
+    k, eta, dt, ns = 3, 2e-3, 5e-3, 3
+    run = make_run(nx=n, ny=n, nz=n, eta=eta, nu=2e-3, dt_fixed=dt, dtype="f32")
+    X, Y, Z = coords(n, n, n)
+    qb = np.zeros((7, n, n, n), dtype=np.float32)
+    qb[4], qb[5] = np.sin(k * Z), np.cos(k * Z)
+    run.set_state(qb)
+    run.step(ns)
+    out, _, _ = run.get_state(dtype=np.float32)
+    gk = rk3_gain(-eta * k2sq_mod(k, 2 * math.pi / n) * dt) ** ns
+    assert np.abs(out[4] - gk * np.sin(k * Z)).max() < 2e-6
+    assert np.abs(out[[0, 1, 2, 3, 6]]).max() < 2e-6
+    run.close()
+
+
+# --------------------------------------------------------------------------
+# Diagnostics, state transfer, batching, determinism, failure detection
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_diagnostics_match_oracle(dtype, tol):
+    kw = dict(nx=30, ny=20, nz=18, dtype=dtype)
+    q = inputs.random_modes_state(30, 20, 18, seed=6, amp=0.4)
+    run = make_run(**kw)
+    run.set_state(q)
+    d = run.diagnostics()
+    o = O.diagnostics(oracle_params(**kw), q)
+    for key in ("urms", "brms", "umax", "bmax", "ekin", "emag", "mass", "vmax"):
+        assert d[key] == pytest.approx(o[key], rel=tol), key
+    assert d["divb_max"] < (1e-12 if dtype == "f64" else 1e-4) * d["bmax"] * 30 / (2 * math.pi)
+    run.close()
+
+
+def test_state_roundtrip_is_exact():
+    q = inputs.noise_state(13, 7, 5, seed=1, amp=1.0)
+    run = make_run(nx=13, ny=7, nz=5, dtype="f64")
+    run.set_state(q, t=1.5, step=3)
+    back, t, step = run.get_state()
+    assert np.array_equal(back, q) and t == 1.5 and step == 3
+    run.close()
+    q32 = q.astype(np.float32)
+    run = make_run(nx=13, ny=7, nz=5, dtype="f32")
+    run.set_state(q32)
+    back, _, _ = run.get_state(dtype=np.float32)
+    assert np.array_equal(back, q32)
+    run.close()
+
+
+def test_batch_is_bitwise_identical_to_alone():
+    from paper_2012_08758_b300.run import Batch
+    cfgs = [dict(nx=32, ny=32, nz=32, f0=0.02, sigma=1.0, seed=1, nu=4e-3, eta=4e-3),
+            dict(nx=48, ny=40, nz=24, f0=0.02, sigma=0.0, seed=2, nu=2e-3, eta=2e-3),
+            dict(nx=17, ny=19, nz=23, f0=0.03, sigma=1.0, seed=3, nu=5e-3, eta=5e-3)]
+    states = [inputs.seed_field_state(c["nx"], c["ny"], c["nz"], seed=i, amp=1e-3)
+              for i, c in enumerate(cfgs)]
+    alone = []
+    for c, q in zip(cfgs, states):
+        r = make_run(**c)
+        r.set_state(q)
+        r.step(7)
+        alone.append(r.get_state(dtype=np.float32)[0])
+        r.close()
+    runs = [make_run(**c) for c in cfgs]
+    for r, q in zip(runs, states):
+        r.set_state(q)
+    b = Batch(runs)
+    b.step(5)  # graph of 5 steps
+    b.step(2)  # replay path / direct remainder
+    for r, ref in zip(runs, alone):
+        got, _, step = r.get_state(dtype=np.float32)
+        assert step == 7
+        assert np.array_equal(got, ref)
+    b.close()
+    for r in runs:
+        r.close()
+
+
+def test_runs_are_deterministic():
+    outs = []
+    for _ in range(2):
+        r = make_run(**dict(C1, dtype="f32"))
+        r.set_state(inputs.seed_field_state(32, seed=0))
+        r.step(6)
+        outs.append((r.get_state(dtype=np.float32)[0], r.diagnostics()))
+        r.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
+
+
+def test_zero_steps_is_a_noop():
+    q = inputs.noise_state(8, seed=2)
+    r = make_run(nx=8, ny=8, nz=8, dtype="f64")
+    r.set_state(q)
+    r.step(0)
+    back, t, st = r.get_state()
+    assert np.array_equal(back, q) and t == 0.0 and st == 0
+    r.close()
+
+
+def test_blow_up_is_reported_not_hidden():
+    """A NaN planted in the host-side upload makes the dt reduction
+    non-finite; the next synchronising call reports it."""
+    from paper_2012_08758_b300 import binding as B
+    q = inputs.seed_field_state(16, seed=0)
+    q[1, 3, 4, 5] = np.nan
+    r = make_run(nx=16, ny=16, nz=16, dtype="f32")
+    r.set_state(q)
+    r.step(2)
+    with pytest.raises(B.MhdError) as e:
+        r.sync()
+    assert e.value.code == B.MHD_ENONFINITE
+    r.close()

@@ -18,9 +18,9 @@ MUTANTS = {
     "strain_factor_two": ("2.0 * Sg", "1.0 * Sg"),
     "strain_trace": ("divu / 3.0 : 0.0", "divu / 2.0 : 0.0"),
     "u_cross_b_order": ("cross3(uu, B, uxB);", "cross3(B, uu, uxB);"),
-    "bz_sign": ("gA[1][0] - gA[0][1]};\n        /* Lap", "gA[0][1] - gA[1][0]};\n        /* Lap"),
-    "bx_sign": ("/* B = curl A */\n        double B[3] = {gA[2][1] - gA[1][2],",
-                "/* B = curl A */\n        double B[3] = {gA[1][2] - gA[2][1],"),
+    "bz_sign": ("gA[1][0] - gA[0][1]};\n  /* Lap", "gA[0][1] - gA[1][0]};\n  /* Lap"),
+    "bx_sign": ("/* B = curl A */\n  double B[3] = {gA[2][1] - gA[1][2],",
+                "/* B = curl A */\n  double B[3] = {gA[1][2] - gA[2][1],"),
     "d1_weight": ("- 9.0 * (f[2] - f[-2])", "- 8.0 * (f[2] - f[-2])"),
     "d2_weight": ("- 27.0 * (f[2] + f[-2])", "- 26.0 * (f[2] + f[-2])"),
     "dmix_weight": ("- 27.0 * S[2]", "- 26.0 * S[2]"),
