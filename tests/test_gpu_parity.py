@@ -1,6 +1,8 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
-the same seeded inputs.  Tolerances (relative L-infinity per field, scale =
-max |oracle field|): FP64 1e-12, FP32 2e-5 for states; FP32 RHS 1e-5."""
+the same seeded inputs.  Tolerances: states, relative L-infinity per field
+with the scale of its physical quantity (tests/gpu_util.rel_linf_state):
+FP64 1e-12, FP32 2e-5; right-hand sides, relative L-infinity per field:
+FP64 1e-12, FP32 1e-5."""
 import math
 
 import numpy as np
@@ -8,7 +10,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2012_08758_b300 import inputs
-from tests.gpu_util import gpu_params, oracle_params, rel_linf
+from tests.gpu_util import gpu_params, oracle_params, rel_linf, rel_linf_state
 from tests.states import coords, k2sq_mod, rk3_gain
 
 pytestmark = pytest.mark.gpu
@@ -61,7 +63,9 @@ def test_rhs_matches_oracle(shape, dtype, tol):
     p = oracle_params(**kw)
     F = O.forcing_draw(p, 9, dt=0.05)
     want = O.rhs(p, q, F)
-    err = rel_linf(got, want)
+    # RHS fields here are O(0.1-10); a field that is zero up to rounding
+    # (e.g. on a 1-point grid) is compared absolutely at tol * 1e-3
+    err = rel_linf(got, want, floor=1e-3)
     assert err.max() < tol, err
     run.close()
 
@@ -87,8 +91,8 @@ def test_c1_step_parity(dtype, tol):
         got, t_gpu, step_gpu = run.get_state()
         assert step_gpu == target
         assert abs(t_gpu - t_or) <= (1e-13 if dtype == "f64" else 1e-6) * t_or
-        err = rel_linf(got, q)
-        assert err.max() < tol, (target, err)
+        err = rel_linf_state(got, q, cs=1.0)
+        assert err.max() < tol, (target, err, rel_linf(got, q))
     run.close()
 
 
@@ -104,7 +108,7 @@ def test_ragged_and_degenerate_step_parity(shape):
     got, t, _ = run.get_state()
     q = q0.copy()
     O.run(oracle_params(**kw), q, 4)
-    err = rel_linf(got, q)
+    err = rel_linf_state(got, q)
     assert err.max() < 1e-12, err
     run.close()
 
@@ -119,7 +123,7 @@ def test_forcing_once_per_step_mode():
     got, _, _ = run.get_state()
     q = q0.copy()
     O.run(oracle_params(**kw), q, 3)
-    assert rel_linf(got, q).max() < 1e-12
+    assert rel_linf_state(got, q).max() < 1e-12
     run.close()
 
 
@@ -133,7 +137,7 @@ def test_fixed_dt_and_clock():
     assert step == 12 and abs(t - (2.0 + 5 * 1.19209e-3)) < 1e-14
     q = q0.copy()
     O.run(oracle_params(**kw), q, 5, step0=7)
-    assert rel_linf(got, q).max() < 1e-12
+    assert rel_linf_state(got, q).max() < 1e-12
     tt, dtl, st = run.time()
     assert dtl == 1.19209e-3 and st == 12
     run.close()
