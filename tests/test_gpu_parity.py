@@ -197,7 +197,14 @@ def test_full_size_256_sampled_rhs_and_beltrami():
     out, _, _ = run.get_state(dtype=np.float32)
     gk = rk3_gain(-eta * k2sq_mod(k, 2 * math.pi / n) * dt) ** ns
     assert np.abs(out[4] - gk * np.sin(k * Z)).max() < 2e-6
-    assert np.abs(out[[0, 1, 2, 3, 6]]).max() < 2e-6
+    # FP32 rounding of the second-derivative stencils grows like eps/h^2
+    # (the weights sum to 18.1/h^2 over three axes while the result is
+    # ~k^2): j carries ~eps * 18.1 |A| / h^2, so j x B, and from it u, ln rho
+    # and A_z, stay below t |B| eps 18.1 |A| / h^2 (~8e-5 here; exactly 0 in
+    # exact arithmetic).
+    h = 2 * math.pi / n
+    bound = ns * dt * 3.0 * 6e-8 * 18.1 / h ** 2
+    assert np.abs(out[[0, 1, 2, 3, 6]]).max() < bound
     run.close()
 
 
