@@ -197,6 +197,41 @@ int mhd_batch_step(mhd_batch *b, int nsteps);
 /* Releases the batch (not the contexts).  NULL is ignored. */
 void mhd_batch_destroy(mhd_batch *b);
 
+/* ---- diagnostics without device allocation ---------------------------------
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory: a plugin inside an application whose own
+ * memory pool already owns every byte of the GPU, code that must run within a
+ * memory budget fixed before it starts, and code on a latency-critical path,
+ * where cudaMalloc is unwelcome because it can synchronise the whole device
+ * and can fail once another allocator has reserved the memory.
+ *
+ * Computes the MHD_NREDUCE quantities of mhd_diagnostics (same order, same
+ * definitions) for a state the caller already holds on the device; no
+ * context is involved.
+ *   state_dev  device pointer, read only: 7*nx*ny*nz values of `dtype`
+ *              (MHD_F32 or MHD_F64), dense SoA without ghost zones, x fastest,
+ *              fields ln rho, u_x, u_y, u_z, A_x, A_y, A_z (periodic box).
+ *   nx..cs     grid, box lengths and sound speed, as in mhd_params.
+ *   out_dev    device pointer to MHD_NREDUCE doubles, written by the kernel.
+ *   stream     cudaStream_t the work is ordered on (NULL: legacy stream).
+ * Asynchronous: out_dev holds the result once the stream reaches this work.
+ * Allocates nothing.  Its scratch -- per-block partial sums and a counter --
+ * is one static device array of 256 KiB inside this library, which every GPU
+ * that loads the library keeps until the process exits.  That bounds the grid
+ * to MHD_NOALLOC_MAX_POINTS points (2^24, e.g. 256^3); larger grids are
+ * rejected with MHD_EINVAL and a message saying so.  The first call on a
+ * device looks up the device address of the array with that device current;
+ * make that first call before any stream capture.  All calls share the one
+ * array, which keeps the last call's partials: the counter is cleared at the
+ * start of every call, but calls whose work overlaps on the GPU (different
+ * streams or threads without ordering) race and give wrong results -- order
+ * them on one stream or synchronise in between.
+ * Errors: MHD_EINVAL (NULL pointer, bad size, grid above the limit),
+ * MHD_ECUDA; the message is returned by mhd_last_error(NULL). */
+enum { MHD_NOALLOC_MAX_POINTS = 1 << 24 };
+int mhd_diagnostics_noalloc(const void *state_dev, int dtype, int nx, int ny, int nz, double lx,
+                            double ly, double lz, double cs, double *out_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,8 @@ def lib():
             "mhd_batch_create": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(vp)]),
             "mhd_batch_step": (C.c_int, [vp, C.c_int]),
             "mhd_batch_destroy": (None, [vp]),
+            "mhd_diagnostics_noalloc": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                                                  C.c_double, C.c_double, C.c_double, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -214,6 +216,18 @@ def mhd_batch_step(batch: int, nsteps: int) -> None:
 
 def mhd_batch_destroy(batch: int) -> None:
     lib().mhd_batch_destroy(C.c_void_p(batch))
+
+
+MHD_NOALLOC_MAX_POINTS = 1 << 24
+
+
+def mhd_diagnostics_noalloc(state_dev: int, dtype: int, nx: int, ny: int, nz: int, lx: float,
+                            ly: float, lz: float, cs: float, out_dev: int, stream: int = 0) -> None:
+    """Diagnostics of a dense device state into out_dev (9 device doubles)
+    without any device allocation; pointers and stream are ints."""
+    _check(lib().mhd_diagnostics_noalloc(C.c_void_p(state_dev), int(dtype), int(nx), int(ny), int(nz),
+                                         float(lx), float(ly), float(lz), float(cs),
+                                         C.c_void_p(out_dev), C.c_void_p(stream or None)))
 
 
 def default_box() -> float:

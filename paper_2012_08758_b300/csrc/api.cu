@@ -16,8 +16,12 @@
 using namespace mhd;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+void mhd::set_last_error(const char *msg) { g_err = msg; }
+
+namespace {
 
 constexpr size_t ALIGN = 256;
 constexpr int TARGET_CTAS = 2 * 2 * 148;  // ~two waves of two CTAs per SM on 148 SMs

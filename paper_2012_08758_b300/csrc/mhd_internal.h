@@ -69,6 +69,9 @@ struct Tile {
   int run, x0, y0, z0, z1, slot;
 };
 
+// Records msg as the calling thread's last error (mhd_last_error(NULL)).
+void set_last_error(const char *msg);
+
 // ---- launchers (kernels.cu / reduce.cu) -------------------------------------
 // dtype: 0 = float, 1 = double.  All return a cudaError_t as int.
 int launch_prologue(int dtype, const RunDesc *runs, const Tile *tiles, int ntiles, int tw, int th,
