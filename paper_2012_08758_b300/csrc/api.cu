@@ -1,5 +1,6 @@
 // Host side of the C ABI declared in include/mhd.h: parameter validation,
 // device workspace layout, tile tables, step orchestration and batching.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -104,12 +105,66 @@ int validate(const mhd_params *p, std::string *why) {
   if (p->dt_fixed == 0 && !(p->cfl > 0 && p->cfl_visc > 0)) return bad("cfl and cfl_visc must be > 0");
   if (p->forcing_mode != 0 && p->forcing_mode != 1) return bad("forcing_mode must be 0 or 1");
   if (p->dtype != MHD_F32 && p->dtype != MHD_F64) return bad("dtype must be MHD_F32 or MHD_F64");
-  if (p->kernel != MHD_KERNEL_AUTO && p->kernel != MHD_KERNEL_SMEM)
-    return bad("kernel variant not available in this build");
+  if (p->kernel != MHD_KERNEL_AUTO && p->kernel != MHD_KERNEL_SMEM && p->kernel != MHD_KERNEL_TMA)
+    return bad("kernel must be MHD_KERNEL_AUTO, MHD_KERNEL_SMEM or MHD_KERNEL_TMA");
+  if (p->kernel == MHD_KERNEL_SMEM && p->tile != 0) return bad("the plane-ring kernel has one tile (tile = 0)");
+  if (p->tile < 0 || p->tile > tma_num_tiles(p->dtype)) return bad("tile id out of range");
   return MHD_OK;
 }
 
-Layout make_layout(const mhd_params *p) {
+// AUTO resolves to the TMA kernel; tile 0 to the default tile of the kernel.
+mhd_params resolved(const mhd_params *p) {
+  mhd_params r = *p;
+  if (r.kernel == MHD_KERNEL_AUTO) r.kernel = MHD_KERNEL_TMA;
+  if (r.kernel == MHD_KERNEL_TMA && r.tile == 0) r.tile = 1;
+  return r;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  }
+  return fn;
+}
+
+// 4-D map of one state buffer: (x: px, y: py, z: pz, field: 7), box = one
+// z-plane of a (tw+8) x (th+6) tile of all seven fields.
+int encode_state_map(CUtensorMap *m, void *base, size_t esz, int px, int py, int pz, int tw, int th,
+                     std::string *why) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) {
+    *why = "cuTensorMapEncodeTiled is not available from the driver";
+    return MHD_ECUDA;
+  }
+  const cuuint64_t dims[4] = {(cuuint64_t)px, (cuuint64_t)py, (cuuint64_t)pz, (cuuint64_t)NF};
+  const cuuint64_t strides[3] = {(cuuint64_t)px * esz, (cuuint64_t)px * py * esz,
+                                 (cuuint64_t)px * py * pz * esz};
+  const cuuint32_t box[4] = {(cuuint32_t)(tw + 8), (cuuint32_t)(th + 2 * RAD), 1u, (cuuint32_t)NF};
+  const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+  CUresult r = fn(m, esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, base,
+                  dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    *why = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
+    return MHD_ECUDA;
+  }
+  return MHD_OK;
+}
+
+Layout make_layout(const mhd_params *p_in) {
+  const mhd_params rp = resolved(p_in);
+  const mhd_params *p = &rp;
   Layout L;
   L.esz = p->dtype == MHD_F32 ? 4 : 8;
   L.px = (int)align_up((size_t)p->nx + OX + RAD, 8);
@@ -259,7 +314,8 @@ int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t worksp
   *out = nullptr;
   if (validate(p, &why)) return fail(nullptr, MHD_EINVAL, "%s", why.c_str());
   mhd_ctx *ctx = new mhd_ctx();
-  ctx->p = *p;
+  ctx->p = resolved(p);
+  p = &ctx->p;
   ctx->stream = static_cast<cudaStream_t>(stream);
   ctx->L = make_layout(p);
   const Layout &L = ctx->L;
@@ -327,6 +383,14 @@ int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t worksp
   R.seed = p->seed;
   R.ntiles = (int)L.tiles_host.size();
   ctx->ntiles = R.ntiles;
+  if (p->kernel == MHD_KERNEL_TMA) {
+    std::string why;
+    for (int b = 0; b < 2; ++b)
+      if (encode_state_map(&R.tmap[b], R.q[b], L.esz, L.px, L.py, L.pz, L.tw, L.th, &why)) {
+        fail(ctx, MHD_ECUDA, "%s", why.c_str());
+        return cleanup(MHD_ECUDA);
+      }
+  }
   ctx->d_run = reinterpret_cast<RunDesc *>(ws + L.run);
   ctx->d_tiles = reinterpret_cast<Tile *>(ws + L.tiles);
   int bps = 1;

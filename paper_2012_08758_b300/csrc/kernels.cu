@@ -251,16 +251,14 @@ static int launch_smem(const RunDesc *runs, const Tile *tiles, int ntiles, int s
 }
 
 int substep_tile_shape(int dtype, int kernel, int tile, int *tx, int *ty) {
-  (void)kernel;
-  (void)tile;
+  if (kernel == 2) return tma_tile_shape(dtype, tile, tx, ty);
   *tx = 32;
   *ty = dtype == 0 ? 8 : 4;
   return 0;
 }
 
 int substep_max_grid(int dtype, int kernel, int tile, int *blocks_per_sm) {
-  (void)kernel;
-  (void)tile;
+  if (kernel == 2) return tma_occupancy(dtype, tile, blocks_per_sm);
   int n = 0;
   cudaError_t e;
   if (dtype == 0)
@@ -275,16 +273,15 @@ int substep_max_grid(int dtype, int kernel, int tile, int *blocks_per_sm) {
 
 // Sets the kernel attributes (dynamic shared memory above 48 KB) on the
 // current device; called when a context is created, outside any capture.
+// kernel: 1 = shared-memory plane ring, 2 = TMA.
 int prepare_substep(int dtype, int kernel, int tile) {
-  (void)kernel;
-  (void)tile;
+  if (kernel == 2) return tma_prepare(dtype, tile);
   return dtype == 0 ? prepare_smem<float, 32, 8>() : prepare_smem<double, 32, 4>();
 }
 
 int launch_substep(int dtype, int kernel, int tile, const RunDesc *runs, const Tile *tiles,
                    int ntiles, int substep, int grid, cudaStream_t s) {
-  (void)kernel;
-  (void)tile;
+  if (kernel == 2) return tma_launch(dtype, tile, runs, tiles, ntiles, substep, grid, s);
   if (dtype == 0) return launch_smem<float, 32, 8>(runs, tiles, ntiles, substep, grid, s);
   return launch_smem<double, 32, 4>(runs, tiles, ntiles, substep, grid, s);
 }

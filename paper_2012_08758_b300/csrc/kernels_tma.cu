@@ -1,0 +1,443 @@
+// Substep kernel, TMA variant (the fast path).
+//
+// Same arithmetic as the plane-ring kernel (one stage of the 3rd-order
+// 2N-storage Runge-Kutta scheme of Sec. 2 on the right-hand side of
+// Eqs. 1-3 with the forcing of Eqs. 4-6), organised for sm_103a:
+//
+//  * a CTA owns a 32 x TY column and sweeps it along z;
+//  * every z-plane of all seven fields (with 3-point x/y halos) is brought
+//    into shared memory by one cp.async.bulk.tensor (TMA) copy, issued
+//    P = NS-4 planes ahead and completed on an mbarrier, so the memory
+//    system always has planes in flight while the SM computes;
+//  * each thread keeps its seven z-values of every field in registers (a
+//    pencil), so z-derivatives need no shared-memory traffic;
+//  * the mixed derivatives in the x-z and y-z planes are accumulated in
+//    registers: the diagonal sum S_s(z0) = dx_s(z0+s) - dx_s(z0-s) is built
+//    from the x-differences dx_s = f(x+s) - f(x-s) of each plane as it
+//    arrives, so only four planes (output plane to lead plane) must stay in
+//    shared memory;
+//  * x/y derivatives and the x-y mixed derivatives come from the output
+//    plane in shared memory.
+// Every wait on an mbarrier is bounded; on time-out the CTA records an
+// error in the run's clock (status bit 1), waits (bounded) for the copies it
+// issued and returns without writing further results.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mhd_internal.h"
+#include "physics.cuh"
+
+namespace mhd {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      "  .reg .pred p;\n"
+      "  mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "  selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after MAX_TRIES polls (each poll may suspend the
+// thread for a short, hardware-defined time), well under a few seconds.
+constexpr uint32_t MAX_TRIES = 1u << 20;
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (uint32_t i = 0; i < MAX_TRIES; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0,
+                                            int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+      : "memory");
+}
+
+template <typename T, int TY>
+struct TmaShape {
+  static constexpr int TX = 32;
+  static constexpr int SX = TX + 8;  // box width: x0-4 .. x0+TX+3 (16-byte multiple)
+  static constexpr int SY = TY + 2 * RAD;
+  static constexpr int FIELD = SX * SY;
+  static constexpr int STAGE_BYTES_RAW = NF * FIELD * (int)sizeof(T);
+  static constexpr int STAGE_BYTES = (STAGE_BYTES_RAW + 127) / 128 * 128;
+};
+
+}  // namespace
+
+template <typename T, int TY, int NS>
+__global__ void __launch_bounds__(32 * TY, 1)
+    k_substep_tma(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles, int ntiles,
+                  int substep) {
+  using SH = TmaShape<T, TY>;
+  constexpr int TX = SH::TX, SX = SH::SX, FIELD = SH::FIELD;
+  constexpr int P = NS - 4;  // prefetch distance in planes
+  static_assert(P >= 1, "need at least one plane of prefetch");
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * SH::STAGE_BYTES);
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * TX + tx;
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  unsigned long long G = 0;  // planes issued by this CTA before the current tile
+  bool failed = false;
+  int issued_hi = 0, consumed = 0;  // within the current tile (thread 0's view)
+  const Tile *cur_tile = nullptr;
+
+  for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+    const Tile tile = tiles[t];
+    cur_tile = &tiles[t];
+    const RunDesc &R = runs[tile.run];
+    const StepCoeffs &K = *R.coeffs;
+    Coefs<T> c;
+    c.load(R);
+    const int nx = R.nx, ny = R.ny, nz = R.nz, px = R.px, py = R.py;
+    const long long fs = R.fstride;
+    const int par = (K.parity + substep) & 1;
+    const CUtensorMap *map = &R.tmap[par];
+    T *__restrict__ qout = static_cast<T *>(R.q[par ^ 1]);
+    T *__restrict__ w = static_cast<T *>(R.w);
+    const T dt = T(K.dt);
+    const T alpha = T(RK_ALPHA(substep)), beta = T(RK_BETA(substep));
+    const int x = tile.x0 + tx, y = tile.y0 + ty;
+    const bool active = x < nx && y < ny;
+    const int npl = (tile.z1 - tile.z0) + 2 * RAD;  // lead planes z0-3 .. z1+2
+
+    const bool forcing = K.forcing != 0;
+    const bool force_in_rhs = forcing && R.forcing_mode == 0;
+    const bool force_at_end = forcing && R.forcing_mode == 1 && substep == 2;
+    Cplx<T> exy = {T(1), T(0)};
+    T fa[3] = {T(0), T(0), T(0)}, fb[3] = {T(0), T(0), T(0)};
+    if (forcing) {
+      const Cplx<T> *rx = static_cast<const Cplx<T> *>(R.roots[0]);
+      const Cplx<T> *ry = static_cast<const Cplx<T> *>(R.roots[1]);
+      if (active) exy = cmul(rx[(int)(((long long)K.kmod[0] * x) % nx)], ry[(int)(((long long)K.kmod[1] * y) % ny)]);
+      for (int a = 0; a < 3; ++a) {
+        fa[a] = T(K.fa[a]);
+        fb[a] = T(K.fb[a]);
+      }
+    }
+    const Cplx<T> ephi = {T(K.cphi), T(K.sphi)};
+    const Cplx<T> *rz = static_cast<const Cplx<T> *>(R.roots[2]);
+
+    // TMA issue of lead plane p (interior z = z0 - 3 + p, padded Z = z0 + p)
+    auto issue = [&](int p) {
+      const unsigned long long g = G + p;
+      const int slot = (int)(g % NS);
+      uint64_t *bar = &bars[slot];
+      mbar_arrive_expect_tx(bar, (uint32_t)(NF * FIELD * sizeof(T)));
+      tma_load_4d(smem + slot * SH::STAGE_BYTES, map, bar, tile.x0, tile.y0, tile.z0 + p, 0);
+    };
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      const int first = npl < P ? npl : P;
+      for (int p = 0; p < first; ++p) issue(p);
+      issued_hi = first;
+      consumed = 0;
+    }
+
+    // register pencils pen[f][k] = value at lead-plane index p-6+k, and
+    // accumulators of the x-z / y-z mixed sums for output planes p-3 .. p+3
+    T pen[NF][7];
+    T aX1[7], aY1[7], aZ1[7], aX2[7], aY2[7], aZ2[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) pen[f][k] = T(0);
+      aX1[k] = aY1[k] = aZ1[k] = aX2[k] = aY2[k] = aZ2[k] = T(0);
+    }
+    const int cxy = (ty + RAD) * SX + tx + 4;  // thread's point inside a field plane
+
+    for (int p = 0; p < npl; ++p) {
+      if (tid == 0) {
+        consumed = p;  // planes before p are finished
+        if (p + P < npl) {
+          fence_proxy_async_smem();
+          issue(p + P);
+          issued_hi = p + P + 1;
+        }
+      }
+      const unsigned long long g = G + p;
+      const int slot = (int)(g % NS);
+      const bool ok = mbar_wait(&bars[slot], (uint32_t)((g / NS) & 1ull));
+      const T *lead = reinterpret_cast<const T *>(smem + slot * SH::STAGE_BYTES) + cxy;
+
+      // pencils
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) pen[f][k] = pen[f][k + 1];
+        pen[f][6] = lead[f * FIELD];
+      }
+      // x / y differences at the lead plane feeding the x-z / y-z sums
+      auto dxs = [&](int f, int s) { return lead[f * FIELD + s] - lead[f * FIELD - s]; };
+      auto dys = [&](int f, int s) { return lead[f * FIELD + s * SX] - lead[f * FIELD - s * SX]; };
+#pragma unroll
+      for (int s = 1; s <= 3; ++s) {
+        const T mxz = c.cm[1][s], myz = c.cm[2][s];
+        const T tX1 = mxz * dxs(3, s);                       // d_x d_z u_z
+        const T tY1 = myz * dys(3, s);                       // d_y d_z u_z
+        const T tZ1 = mxz * dxs(1, s) + myz * dys(2, s);     // d_x d_z u_x + d_y d_z u_y
+        const T tX2 = mxz * dxs(6, s);                       // d_x d_z A_z
+        const T tY2 = myz * dys(6, s);                       // d_y d_z A_z
+        const T tZ2 = mxz * dxs(4, s) + myz * dys(5, s);     // d_x d_z A_x + d_y d_z A_y
+        aX1[3 - s] += tX1; aX1[3 + s] -= tX1;
+        aY1[3 - s] += tY1; aY1[3 + s] -= tY1;
+        aZ1[3 - s] += tZ1; aZ1[3 + s] -= tZ1;
+        aX2[3 - s] += tX2; aX2[3 + s] -= tX2;
+        aY2[3 - s] += tY2; aY2[3 + s] -= tY2;
+        aZ2[3 - s] += tZ2; aZ2[3 + s] -= tZ2;
+      }
+
+      if (p >= 2 * RAD && ok && active) {
+        const int z = tile.z0 + p - 2 * RAD;  // output plane (interior index)
+        const int oslot = (int)((g - RAD) % NS);
+        const T *o = reinterpret_cast<const T *>(smem + oslot * SH::STAGE_BYTES) + cxy;
+        auto X = [&](int f, int s) { return o[f * FIELD + s]; };
+        auto Y = [&](int f, int s) { return o[f * FIELD + s * SX]; };
+        auto D = [&](int f, int sa, int sb) { return o[f * FIELD + sa + sb * SX]; };
+        auto d1x = [&](int f) {
+          return c.c1[0][1] * (X(f, 1) - X(f, -1)) + c.c1[0][2] * (X(f, 2) - X(f, -2)) +
+                 c.c1[0][3] * (X(f, 3) - X(f, -3));
+        };
+        auto d1y = [&](int f) {
+          return c.c1[1][1] * (Y(f, 1) - Y(f, -1)) + c.c1[1][2] * (Y(f, 2) - Y(f, -2)) +
+                 c.c1[1][3] * (Y(f, 3) - Y(f, -3));
+        };
+        auto d1z = [&](int f) {
+          return c.c1[2][1] * (pen[f][4] - pen[f][2]) + c.c1[2][2] * (pen[f][5] - pen[f][1]) +
+                 c.c1[2][3] * (pen[f][6] - pen[f][0]);
+        };
+        auto d2x = [&](int f) {
+          return c.c2[0][0] * pen[f][3] + c.c2[0][1] * (X(f, 1) + X(f, -1)) +
+                 c.c2[0][2] * (X(f, 2) + X(f, -2)) + c.c2[0][3] * (X(f, 3) + X(f, -3));
+        };
+        auto d2y = [&](int f) {
+          return c.c2[1][0] * pen[f][3] + c.c2[1][1] * (Y(f, 1) + Y(f, -1)) +
+                 c.c2[1][2] * (Y(f, 2) + Y(f, -2)) + c.c2[1][3] * (Y(f, 3) + Y(f, -3));
+        };
+        auto d2z = [&](int f) {
+          return c.c2[2][0] * pen[f][3] + c.c2[2][1] * (pen[f][4] + pen[f][2]) +
+                 c.c2[2][2] * (pen[f][5] + pen[f][1]) + c.c2[2][3] * (pen[f][6] + pen[f][0]);
+        };
+        auto dxy = [&](int f) {
+          T r = T(0);
+#pragma unroll
+          for (int s = 1; s <= 3; ++s)
+            r += c.cm[0][s] * ((D(f, s, s) - D(f, -s, s)) - (D(f, s, -s) - D(f, -s, -s)));
+          return r;
+        };
+
+        Derivs<T> d;
+        d.lnr = pen[0][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          d.u[a] = pen[1 + a][3];
+          d.A[a] = pen[4 + a][3];
+        }
+        d.g[0] = d1x(0);
+        d.g[1] = d1y(0);
+        d.g[2] = d1z(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          d.G[a][0] = d1x(1 + a);
+          d.G[a][1] = d1y(1 + a);
+          d.G[a][2] = d1z(1 + a);
+        }
+        d.gA[0][0] = d.gA[1][1] = d.gA[2][2] = T(0);  // not used by B = curl A
+        d.gA[0][1] = d1y(4);
+        d.gA[0][2] = d1z(4);
+        d.gA[1][0] = d1x(5);
+        d.gA[1][2] = d1z(5);
+        d.gA[2][0] = d1x(6);
+        d.gA[2][1] = d1y(6);
+        const T uxx = d2x(1), uxy_ = d2y(1), uxz_ = d2z(1);
+        const T uyx = d2x(2), uyy = d2y(2), uyz_ = d2z(2);
+        const T uzx = d2x(3), uzy = d2y(3), uzz = d2z(3);
+        d.lapu[0] = uxx + uxy_ + uxz_;
+        d.lapu[1] = uyx + uyy + uyz_;
+        d.lapu[2] = uzx + uzy + uzz;
+        d.gdu[0] = uxx + dxy(2) + aX1[0];
+        d.gdu[1] = dxy(1) + uyy + aY1[0];
+        d.gdu[2] = aZ1[0] + uzz;
+        const T Axx = d2x(4), Axy_ = d2y(4), Axz_ = d2z(4);
+        const T Ayx = d2x(5), Ayy = d2y(5), Ayz_ = d2z(5);
+        const T Azx = d2x(6), Azy = d2y(6), Azz = d2z(6);
+        d.lapA[0] = Axx + Axy_ + Axz_;
+        d.lapA[1] = Ayx + Ayy + Ayz_;
+        d.lapA[2] = Azx + Azy + Azz;
+        d.jc[0] = dxy(5) + aX2[0] - Axy_ - Axz_;
+        d.jc[1] = dxy(4) + aY2[0] - Ayx - Ayz_;
+        d.jc[2] = aZ2[0] - Azx - Azy;
+
+        T f[3] = {T(0), T(0), T(0)};
+        if (forcing) {
+          const Cplx<T> e = cmul(exy, cmul(rz[(int)(((long long)K.kmod[2] * z) % nz)], ephi));
+#pragma unroll
+          for (int a = 0; a < 3; ++a) f[a] = fa[a] * e.re - fb[a] * e.im;
+        }
+        const T fr[3] = {force_in_rhs ? f[0] : T(0), force_in_rhs ? f[1] : T(0), force_in_rhs ? f[2] : T(0)};
+        T r[NF];
+        rhs_point(d, c, fr, r);
+        const long long cidx = ((long long)(z + OZ) * py + (y + OY)) * px + (x + OX);
+        T qn[NF];
+#pragma unroll
+        for (int fld = 0; fld < NF; ++fld) {
+          T wv = dt * r[fld];
+          if (substep > 0) wv += alpha * w[fld * fs + cidx];
+          if (substep < 2) w[fld * fs + cidx] = wv;
+          qn[fld] = pen[fld][3] + beta * wv;
+        }
+        if (force_at_end)
+          for (int a = 0; a < 3; ++a) qn[1 + a] += dt * f[a];
+        int ix[7], iy[7], iz[7];
+        const int cx = periodic_images(x, nx, ix);
+        const int cy = periodic_images(y, ny, iy);
+        const int cz = periodic_images(z, nz, iz);
+        for (int a = 0; a < cz; ++a)
+          for (int b = 0; b < cy; ++b)
+            for (int e = 0; e < cx; ++e) {
+              const long long oo = ((long long)(iz[a] + OZ) * py + (iy[b] + OY)) * px + (ix[e] + OX);
+#pragma unroll
+              for (int fld = 0; fld < NF; ++fld) qout[fld * fs + oo] = qn[fld];
+            }
+      }
+      // retire the accumulator of the output plane
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        aX1[k] = aX1[k + 1]; aY1[k] = aY1[k + 1]; aZ1[k] = aZ1[k + 1];
+        aX2[k] = aX2[k + 1]; aY2[k] = aY2[k + 1]; aZ2[k] = aZ2[k + 1];
+      }
+      aX1[6] = aY1[6] = aZ1[6] = aX2[6] = aY2[6] = aZ2[6] = T(0);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+    }
+    if (!failed) G += npl;
+  }
+
+  if (failed && tid == 0) {
+    // record the time-out, then wait (bounded) for the copies still in flight
+    if (cur_tile) atomicOr(&runs[cur_tile->run].clock->status, 2);
+    for (int p = consumed; p < issued_hi; ++p) {
+      const unsigned long long g = G + p;
+      mbar_wait(&bars[(int)(g % NS)], (uint32_t)((g / NS) & 1ull));
+    }
+  }
+}
+
+namespace {
+
+template <typename T, int TY, int NS>
+int tma_smem_bytes() {
+  return NS * TmaShape<T, TY>::STAGE_BYTES + NS * 8;
+}
+
+template <typename T, int TY, int NS>
+int prepare_tma() {
+  return (int)cudaFuncSetAttribute(k_substep_tma<T, TY, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   tma_smem_bytes<T, TY, NS>());
+}
+
+template <typename T, int TY, int NS>
+int launch_tma(const RunDesc *runs, const Tile *tiles, int ntiles, int substep, int grid, cudaStream_t s) {
+  if (grid <= 0 || grid > ntiles) grid = ntiles;
+  if (grid == 0) return 0;
+  k_substep_tma<T, TY, NS><<<grid, dim3(32, TY), tma_smem_bytes<T, TY, NS>(), s>>>(runs, tiles, ntiles, substep);
+  return (int)cudaGetLastError();
+}
+
+template <typename T, int TY, int NS>
+int occupancy_tma(int *bps) {
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_substep_tma<T, TY, NS>, 32 * TY,
+                                                            tma_smem_bytes<T, TY, NS>());
+}
+
+}  // namespace
+
+// Tile variants of the TMA kernel: id -> (dtype, TY, stages).
+//   FP32: 1 = 32x8, 6 stages; 2 = 32x4, 6 stages; 3 = 32x8, 8 stages; 4 = 32x16, 6 stages
+//   FP64: 1 = 32x4, 6 stages; 2 = 32x8, 5 stages
+#define MHD_TMA_VARIANTS(X)     \
+  X(0, 1, float, 8, 6)          \
+  X(0, 2, float, 4, 6)          \
+  X(0, 3, float, 8, 8)          \
+  X(0, 4, float, 16, 6)         \
+  X(1, 1, double, 4, 6)         \
+  X(1, 2, double, 8, 5)
+
+int tma_num_tiles(int dtype) { return dtype == 0 ? 4 : 2; }
+
+int tma_tile_shape(int dtype, int tile, int *tx, int *ty) {
+  *tx = 32;
+#define X(DT, ID, T, TY, NS) \
+  if (dtype == DT && tile == ID) { *ty = TY; return 0; }
+  MHD_TMA_VARIANTS(X)
+#undef X
+  return -1;
+}
+
+int tma_prepare(int dtype, int tile) {
+#define X(DT, ID, T, TY, NS) \
+  if (dtype == DT && tile == ID) return prepare_tma<T, TY, NS>();
+  MHD_TMA_VARIANTS(X)
+#undef X
+  return (int)cudaErrorInvalidValue;
+}
+
+int tma_occupancy(int dtype, int tile, int *bps) {
+#define X(DT, ID, T, TY, NS) \
+  if (dtype == DT && tile == ID) return occupancy_tma<T, TY, NS>(bps);
+  MHD_TMA_VARIANTS(X)
+#undef X
+  return (int)cudaErrorInvalidValue;
+}
+
+int tma_launch(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles, int substep, int grid,
+               cudaStream_t s) {
+#define X(DT, ID, T, TY, NS) \
+  if (dtype == DT && tile == ID) return launch_tma<T, TY, NS>(runs, tiles, ntiles, substep, grid, s);
+  MHD_TMA_VARIANTS(X)
+#undef X
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace mhd

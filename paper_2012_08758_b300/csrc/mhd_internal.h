@@ -1,6 +1,7 @@
 // Internal structures shared by the host side of the C ABI and the kernels.
 // Not part of the public interface (include/mhd.h is).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -39,7 +40,8 @@ struct StepCoeffs {
 };
 
 // Everything a kernel needs to know about one run, resident in device memory.
-struct RunDesc {
+struct alignas(64) RunDesc {
+  CUtensorMap tmap[2];      // TMA maps of q[0], q[1]: 4-D (x, y, z, field), box of one z-plane
   int nx, ny, nz;
   int px, py, pz;           // padded extents; px is the row pitch
   long long fstride;        // elements per field (px * py * pz)
@@ -79,6 +81,13 @@ int launch_prologue(int dtype, const RunDesc *runs, const Tile *tiles, int ntile
 int launch_substep(int dtype, int kernel, int tile, const RunDesc *runs, const Tile *tiles,
                    int ntiles, int substep, int grid, cudaStream_t s);
 int prepare_substep(int dtype, int kernel, int tile);
+// TMA variant (kernels_tma.cu); tile ids start at 1
+int tma_num_tiles(int dtype);
+int tma_tile_shape(int dtype, int tile, int *tx, int *ty);
+int tma_prepare(int dtype, int tile);
+int tma_occupancy(int dtype, int tile, int *bps);
+int tma_launch(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles, int substep,
+               int grid, cudaStream_t s);
 int substep_tile_shape(int dtype, int kernel, int tile, int *tx, int *ty);
 int substep_max_grid(int dtype, int kernel, int tile, int *blocks_per_sm);
 int launch_halo(int dtype, void *fields, int nfields, long long fstride, int nx, int ny, int nz,

@@ -49,12 +49,17 @@ def test_forcing_draw_matches_oracle(seed, sigma, shell):
 SHAPES = [(32, 32, 32), (37, 23, 11), (40, 8, 20), (12, 9, 1), (16, 1, 1), (1, 1, 1)]
 
 
+KERNELS = [(2, 0), (1, 0)]  # (kernel, tile): TMA default tile, plane ring
+TMA_TILES = [(2, 1), (2, 2), (2, 3), (2, 4)]
+
+
+@pytest.mark.parametrize("kernel,tile", KERNELS)
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-5)])
-def test_rhs_matches_oracle(shape, dtype, tol):
+def test_rhs_matches_oracle(shape, dtype, tol, kernel, tile):
     nx, ny, nz = shape
     kw = dict(nx=nx, ny=ny, nz=nz, nu=0.02, eta=0.03, cs=1.1, f0=0.05, sigma=0.7, kmin=1.0,
-              kmax=2.0, seed=5, dtype=dtype)
+              kmax=2.0, seed=5, dtype=dtype, kernel=kernel, tile=tile)
     q = inputs.random_modes_state(nx, ny, nz, seed=3, amp=0.3) + inputs.noise_state(nx, ny, nz, seed=4,
                                                                                     amp=0.02)
     run = make_run(**kw)
@@ -73,9 +78,10 @@ def test_rhs_matches_oracle(shape, dtype, tol):
 # --------------------------------------------------------------------------
 # Full steps (C1: 32^3, forcing, CFL dt, 20 steps)
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("kernel,tile", KERNELS)
 @pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 2e-5)])
-def test_c1_step_parity(dtype, tol):
-    kw = dict(C1, dtype=dtype)
+def test_c1_step_parity(dtype, tol, kernel, tile):
+    kw = dict(C1, dtype=dtype, kernel=kernel, tile=tile)
     q0 = inputs.seed_field_state(32, seed=0)
     run = make_run(**kw)
     run.set_state(q0)
@@ -96,11 +102,12 @@ def test_c1_step_parity(dtype, tol):
     run.close()
 
 
+@pytest.mark.parametrize("kernel,tile", KERNELS)
 @pytest.mark.parametrize("shape", [(37, 23, 11), (24, 24, 1), (1, 1, 1), (9, 40, 7)])
-def test_ragged_and_degenerate_step_parity(shape):
+def test_ragged_and_degenerate_step_parity(shape, kernel, tile):
     nx, ny, nz = shape
     kw = dict(nx=nx, ny=ny, nz=nz, nu=0.01, eta=0.01, f0=0.05, sigma=1.0, kmin=1.0, kmax=2.0,
-              seed=11, dtype="f64")
+              seed=11, dtype="f64", kernel=kernel, tile=tile)
     q0 = inputs.random_modes_state(nx, ny, nz, seed=8, amp=0.2)
     run = make_run(**kw)
     run.set_state(q0)
@@ -110,6 +117,22 @@ def test_ragged_and_degenerate_step_parity(shape):
     O.run(oracle_params(**kw), q, 4)
     err = rel_linf_state(got, q)
     assert err.max() < 1e-12, err
+    run.close()
+
+
+@pytest.mark.parametrize("kernel,tile", TMA_TILES)
+def test_every_tma_tile_fp32_step_parity(kernel, tile):
+    """Each FP32 tile variant of the TMA kernel: ragged grid, 5 forced steps."""
+    kw = dict(nx=45, ny=37, nz=29, nu=0.01, eta=0.01, f0=0.05, sigma=1.0, kmin=1.0, kmax=2.0,
+              seed=4, dtype="f32", kernel=kernel, tile=tile)
+    q0 = inputs.random_modes_state(45, 37, 29, seed=12, amp=0.2)
+    run = make_run(**kw)
+    run.set_state(q0)
+    run.step(5)
+    got, _, _ = run.get_state()
+    q = q0.copy()
+    O.run(oracle_params(**kw), q, 5)
+    assert rel_linf_state(got, q).max() < 2e-5
     run.close()
 
 
