@@ -40,7 +40,7 @@ struct StepCoeffs {
 };
 
 // Everything a kernel needs to know about one run, resident in device memory.
-struct alignas(64) RunDesc {
+struct RunDesc {
   CUtensorMap tmap[2];      // TMA maps of q[0], q[1]: 4-D (x, y, z, field), box of one z-plane
   int nx, ny, nz;
   int px, py, pz;           // padded extents; px is the row pitch
@@ -64,6 +64,9 @@ struct alignas(64) RunDesc {
   int ntiles;               // reduction tiles of this run
   int pad;
 };
+
+static_assert(alignof(RunDesc) >= 64 && sizeof(RunDesc) % 64 == 0,
+              "tensor maps inside RunDesc arrays must stay 64-byte aligned");
 
 // A unit of work: an x-y tile of one run and a range [z0, z1) of interior
 // planes.  slot = index of this tile among the run's tiles.
