@@ -182,7 +182,8 @@ def run_ours(args):
 
     n, dtype = args.n, args.dtype
     cells = n ** 3
-    run = Run(n=n, device=dev, dtype=B.MHD_F32 if dtype == "f32" else B.MHD_F64, **WORKLOAD)
+    run = Run(n=n, device=dev, dtype=B.MHD_F32 if dtype == "f32" else B.MHD_F64, kernel=args.kernel,
+              tile=args.tile, **WORKLOAD)
     q0 = inputs.seed_field_state(n, seed=rank)
     run.set_state(q0)
     run.step(args.warmup)
@@ -287,6 +288,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 plane ring, 2 TMA")
+    ap.add_argument("--tile", type=int, default=0, help="tile variant id (0: default)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU-baseline leg")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the FP64 side measurement")
     args = ap.parse_args()

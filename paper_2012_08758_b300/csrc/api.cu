@@ -112,11 +112,13 @@ int validate(const mhd_params *p, std::string *why) {
   return MHD_OK;
 }
 
-// AUTO resolves to the TMA kernel; tile 0 to the default tile of the kernel.
+// AUTO resolves to the TMA kernel; tile 0 to the default tile of the kernel
+// (the fastest measured at 256^3 on B300: FP32 32x8 with 8 stages, FP64
+// 32x4 with 6 stages).
 mhd_params resolved(const mhd_params *p) {
   mhd_params r = *p;
   if (r.kernel == MHD_KERNEL_AUTO) r.kernel = MHD_KERNEL_TMA;
-  if (r.kernel == MHD_KERNEL_TMA && r.tile == 0) r.tile = 1;
+  if (r.kernel == MHD_KERNEL_TMA && r.tile == 0) r.tile = r.dtype == MHD_F32 ? 3 : 1;
   return r;
 }
 

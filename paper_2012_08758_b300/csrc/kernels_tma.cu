@@ -98,7 +98,12 @@ struct TmaShape {
 
 }  // namespace
 
-template <typename T, int TY, int NS>
+template <int V>
+struct Phase {
+  static constexpr int value = V;
+};
+
+template <typename T, int TY, int NS, bool UNROLL7>
 __global__ void __launch_bounds__(32 * TY, 1)
     k_substep_tma(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles, int ntiles,
                   int substep) {
@@ -118,12 +123,10 @@ __global__ void __launch_bounds__(32 * TY, 1)
 
   unsigned long long G = 0;  // planes issued by this CTA before the current tile
   bool failed = false;
-  int issued_hi = 0, consumed = 0;  // within the current tile (thread 0's view)
-  const Tile *cur_tile = nullptr;
+  int fail_run = -1, fail_p = 0, issued_hi = 0;
 
   for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
     const Tile tile = tiles[t];
-    cur_tile = &tiles[t];
     const RunDesc &R = runs[tile.run];
     const StepCoeffs &K = *R.coeffs;
     Coefs<T> c;
@@ -138,6 +141,7 @@ __global__ void __launch_bounds__(32 * TY, 1)
     const T alpha = T(RK_ALPHA(substep)), beta = T(RK_BETA(substep));
     const int x = tile.x0 + tx, y = tile.y0 + ty;
     const bool active = x < nx && y < ny;
+    const bool edge_xy = x < RAD || x >= nx - RAD || y < RAD || y >= ny - RAD;
     const int npl = (tile.z1 - tile.z0) + 2 * RAD;  // lead planes z0-3 .. z1+2
 
     const bool forcing = K.forcing != 0;
@@ -145,36 +149,40 @@ __global__ void __launch_bounds__(32 * TY, 1)
     const bool force_at_end = forcing && R.forcing_mode == 1 && substep == 2;
     Cplx<T> exy = {T(1), T(0)};
     T fa[3] = {T(0), T(0), T(0)}, fb[3] = {T(0), T(0), T(0)};
+    int mz = 0;  // (k_z * z_out) mod nz, advanced plane by plane
     if (forcing) {
       const Cplx<T> *rx = static_cast<const Cplx<T> *>(R.roots[0]);
       const Cplx<T> *ry = static_cast<const Cplx<T> *>(R.roots[1]);
-      if (active) exy = cmul(rx[(int)(((long long)K.kmod[0] * x) % nx)], ry[(int)(((long long)K.kmod[1] * y) % ny)]);
+      if (active)
+        exy = cmul(rx[(int)(((long long)K.kmod[0] * x) % nx)], ry[(int)(((long long)K.kmod[1] * y) % ny)]);
       for (int a = 0; a < 3; ++a) {
         fa[a] = T(K.fa[a]);
         fb[a] = T(K.fb[a]);
       }
+      mz = (int)(((long long)K.kmod[2] * tile.z0) % nz);
     }
+    const int kz = K.kmod[2];
     const Cplx<T> ephi = {T(K.cphi), T(K.sphi)};
     const Cplx<T> *rz = static_cast<const Cplx<T> *>(R.roots[2]);
 
-    // TMA issue of lead plane p (interior z = z0 - 3 + p, padded Z = z0 + p)
-    auto issue = [&](int p) {
-      const unsigned long long g = G + p;
-      const int slot = (int)(g % NS);
-      uint64_t *bar = &bars[slot];
+    // ring position of the first plane of this tile, advanced incrementally
+    int slot = (int)(G % NS);
+    uint32_t phase = (uint32_t)((G / NS) & 1ull);
+    auto issue = [&](int p, int sl) {
+      uint64_t *bar = &bars[sl];
       mbar_arrive_expect_tx(bar, (uint32_t)(NF * FIELD * sizeof(T)));
-      tma_load_4d(smem + slot * SH::STAGE_BYTES, map, bar, tile.x0, tile.y0, tile.z0 + p, 0);
+      tma_load_4d(smem + sl * SH::STAGE_BYTES, map, bar, tile.x0, tile.y0, tile.z0 + p, 0);
     };
     if (tid == 0) {
       fence_proxy_async_smem();
       const int first = npl < P ? npl : P;
-      for (int p = 0; p < first; ++p) issue(p);
+      for (int p = 0; p < first; ++p) issue(p, (slot + p) % NS);
       issued_hi = first;
-      consumed = 0;
     }
 
-    // register pencils pen[f][k] = value at lead-plane index p-6+k, and
-    // accumulators of the x-z / y-z mixed sums for output planes p-3 .. p+3
+    // Register rings (physical index = (logical + phase) mod 7): pencils
+    // pen[f][.] hold lead planes p-6 .. p; the accumulators hold the x-z /
+    // y-z mixed sums of output planes p-3 .. p+3.
     T pen[NF][7];
     T aX1[7], aY1[7], aZ1[7], aX2[7], aY2[7], aZ2[7];
 #pragma unroll
@@ -184,55 +192,64 @@ __global__ void __launch_bounds__(32 * TY, 1)
       aX1[k] = aY1[k] = aZ1[k] = aX2[k] = aY2[k] = aZ2[k] = T(0);
     }
     const int cxy = (ty + RAD) * SX + tx + 4;  // thread's point inside a field plane
+    const bool need_w = substep > 0 && active;
+    const long long wplane = (long long)py * px;
+    // index of the output point of lead plane 6 (interior z = z0)
+    long long cidx = ((long long)(tile.z0 + OZ) * py + (y + OY)) * px + (x + OX);
+    T wn[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) wn[f] = T(0);
 
-    for (int p = 0; p < npl; ++p) {
-      if (tid == 0) {
-        consumed = p;  // planes before p are finished
-        if (p + P < npl) {
-          fence_proxy_async_smem();
-          issue(p + P);
-          issued_hi = p + P + 1;
-        }
+    auto plane = [&](auto PHc, int p) {
+      constexpr int PH = decltype(PHc)::value;
+      auto L = [](int k) { return (k + PH) % 7; };  // logical -> physical ring index
+      if (tid == 0 && p + P < npl) {
+        fence_proxy_async_smem();
+        int sl = slot + P;
+        if (sl >= NS) sl -= NS;
+        issue(p + P, sl);
+        issued_hi = p + P + 1;
       }
-      const unsigned long long g = G + p;
-      const int slot = (int)(g % NS);
-      const bool ok = mbar_wait(&bars[slot], (uint32_t)((g / NS) & 1ull));
+      T wc[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) wc[f] = wn[f];
+      if (need_w && p >= 2 * RAD - 1 && p + 1 < npl) {
+        const long long nidx = cidx + (p >= 2 * RAD ? wplane : 0);
+#pragma unroll
+        for (int f = 0; f < NF; ++f) wn[f] = __ldcs(w + f * fs + nidx);
+      }
+      const bool ok = mbar_wait(&bars[slot], phase);
       const T *lead = reinterpret_cast<const T *>(smem + slot * SH::STAGE_BYTES) + cxy;
-
-      // pencils
 #pragma unroll
-      for (int f = 0; f < NF; ++f) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) pen[f][k] = pen[f][k + 1];
-        pen[f][6] = lead[f * FIELD];
-      }
-      // x / y differences at the lead plane feeding the x-z / y-z sums
+      for (int f = 0; f < NF; ++f) pen[f][L(6)] = lead[f * FIELD];
       auto dxs = [&](int f, int s) { return lead[f * FIELD + s] - lead[f * FIELD - s]; };
       auto dys = [&](int f, int s) { return lead[f * FIELD + s * SX] - lead[f * FIELD - s * SX]; };
 #pragma unroll
       for (int s = 1; s <= 3; ++s) {
         const T mxz = c.cm[1][s], myz = c.cm[2][s];
-        const T tX1 = mxz * dxs(3, s);                       // d_x d_z u_z
-        const T tY1 = myz * dys(3, s);                       // d_y d_z u_z
-        const T tZ1 = mxz * dxs(1, s) + myz * dys(2, s);     // d_x d_z u_x + d_y d_z u_y
-        const T tX2 = mxz * dxs(6, s);                       // d_x d_z A_z
-        const T tY2 = myz * dys(6, s);                       // d_y d_z A_z
-        const T tZ2 = mxz * dxs(4, s) + myz * dys(5, s);     // d_x d_z A_x + d_y d_z A_y
-        aX1[3 - s] += tX1; aX1[3 + s] -= tX1;
-        aY1[3 - s] += tY1; aY1[3 + s] -= tY1;
-        aZ1[3 - s] += tZ1; aZ1[3 + s] -= tZ1;
-        aX2[3 - s] += tX2; aX2[3 + s] -= tX2;
-        aY2[3 - s] += tY2; aY2[3 + s] -= tY2;
-        aZ2[3 - s] += tZ2; aZ2[3 + s] -= tZ2;
+        const T tX1 = mxz * dxs(3, s);                    // d_x d_z u_z
+        const T tY1 = myz * dys(3, s);                    // d_y d_z u_z
+        const T tZ1 = mxz * dxs(1, s) + myz * dys(2, s);  // d_x d_z u_x + d_y d_z u_y
+        const T tX2 = mxz * dxs(6, s);                    // d_x d_z A_z
+        const T tY2 = myz * dys(6, s);                    // d_y d_z A_z
+        const T tZ2 = mxz * dxs(4, s) + myz * dys(5, s);  // d_x d_z A_x + d_y d_z A_y
+        aX1[L(3 - s)] += tX1; aX1[L(3 + s)] -= tX1;
+        aY1[L(3 - s)] += tY1; aY1[L(3 + s)] -= tY1;
+        aZ1[L(3 - s)] += tZ1; aZ1[L(3 + s)] -= tZ1;
+        aX2[L(3 - s)] += tX2; aX2[L(3 + s)] -= tX2;
+        aY2[L(3 - s)] += tY2; aY2[L(3 + s)] -= tY2;
+        aZ2[L(3 - s)] += tZ2; aZ2[L(3 + s)] -= tZ2;
       }
 
       if (p >= 2 * RAD && ok && active) {
         const int z = tile.z0 + p - 2 * RAD;  // output plane (interior index)
-        const int oslot = (int)((g - RAD) % NS);
+        int oslot = slot - RAD;
+        if (oslot < 0) oslot += NS;
         const T *o = reinterpret_cast<const T *>(smem + oslot * SH::STAGE_BYTES) + cxy;
         auto X = [&](int f, int s) { return o[f * FIELD + s]; };
         auto Y = [&](int f, int s) { return o[f * FIELD + s * SX]; };
         auto D = [&](int f, int sa, int sb) { return o[f * FIELD + sa + sb * SX]; };
+        auto Z = [&](int f, int k) { return pen[f][L(k + 3)]; };  // z offset k in -3..3
         auto d1x = [&](int f) {
           return c.c1[0][1] * (X(f, 1) - X(f, -1)) + c.c1[0][2] * (X(f, 2) - X(f, -2)) +
                  c.c1[0][3] * (X(f, 3) - X(f, -3));
@@ -242,20 +259,20 @@ __global__ void __launch_bounds__(32 * TY, 1)
                  c.c1[1][3] * (Y(f, 3) - Y(f, -3));
         };
         auto d1z = [&](int f) {
-          return c.c1[2][1] * (pen[f][4] - pen[f][2]) + c.c1[2][2] * (pen[f][5] - pen[f][1]) +
-                 c.c1[2][3] * (pen[f][6] - pen[f][0]);
+          return c.c1[2][1] * (Z(f, 1) - Z(f, -1)) + c.c1[2][2] * (Z(f, 2) - Z(f, -2)) +
+                 c.c1[2][3] * (Z(f, 3) - Z(f, -3));
         };
         auto d2x = [&](int f) {
-          return c.c2[0][0] * pen[f][3] + c.c2[0][1] * (X(f, 1) + X(f, -1)) +
+          return c.c2[0][0] * Z(f, 0) + c.c2[0][1] * (X(f, 1) + X(f, -1)) +
                  c.c2[0][2] * (X(f, 2) + X(f, -2)) + c.c2[0][3] * (X(f, 3) + X(f, -3));
         };
         auto d2y = [&](int f) {
-          return c.c2[1][0] * pen[f][3] + c.c2[1][1] * (Y(f, 1) + Y(f, -1)) +
+          return c.c2[1][0] * Z(f, 0) + c.c2[1][1] * (Y(f, 1) + Y(f, -1)) +
                  c.c2[1][2] * (Y(f, 2) + Y(f, -2)) + c.c2[1][3] * (Y(f, 3) + Y(f, -3));
         };
         auto d2z = [&](int f) {
-          return c.c2[2][0] * pen[f][3] + c.c2[2][1] * (pen[f][4] + pen[f][2]) +
-                 c.c2[2][2] * (pen[f][5] + pen[f][1]) + c.c2[2][3] * (pen[f][6] + pen[f][0]);
+          return c.c2[2][0] * Z(f, 0) + c.c2[2][1] * (Z(f, 1) + Z(f, -1)) +
+                 c.c2[2][2] * (Z(f, 2) + Z(f, -2)) + c.c2[2][3] * (Z(f, 3) + Z(f, -3));
         };
         auto dxy = [&](int f) {
           T r = T(0);
@@ -266,11 +283,11 @@ __global__ void __launch_bounds__(32 * TY, 1)
         };
 
         Derivs<T> d;
-        d.lnr = pen[0][3];
+        d.lnr = Z(0, 0);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          d.u[a] = pen[1 + a][3];
-          d.A[a] = pen[4 + a][3];
+          d.u[a] = Z(1 + a, 0);
+          d.A[a] = Z(4 + a, 0);
         }
         d.g[0] = d1x(0);
         d.g[1] = d1y(0);
@@ -294,61 +311,100 @@ __global__ void __launch_bounds__(32 * TY, 1)
         d.lapu[0] = uxx + uxy_ + uxz_;
         d.lapu[1] = uyx + uyy + uyz_;
         d.lapu[2] = uzx + uzy + uzz;
-        d.gdu[0] = uxx + dxy(2) + aX1[0];
-        d.gdu[1] = dxy(1) + uyy + aY1[0];
-        d.gdu[2] = aZ1[0] + uzz;
+        d.gdu[0] = uxx + dxy(2) + aX1[L(0)];
+        d.gdu[1] = dxy(1) + uyy + aY1[L(0)];
+        d.gdu[2] = aZ1[L(0)] + uzz;
         const T Axx = d2x(4), Axy_ = d2y(4), Axz_ = d2z(4);
         const T Ayx = d2x(5), Ayy = d2y(5), Ayz_ = d2z(5);
         const T Azx = d2x(6), Azy = d2y(6), Azz = d2z(6);
         d.lapA[0] = Axx + Axy_ + Axz_;
         d.lapA[1] = Ayx + Ayy + Ayz_;
         d.lapA[2] = Azx + Azy + Azz;
-        d.jc[0] = dxy(5) + aX2[0] - Axy_ - Axz_;
-        d.jc[1] = dxy(4) + aY2[0] - Ayx - Ayz_;
-        d.jc[2] = aZ2[0] - Azx - Azy;
+        d.jc[0] = dxy(5) + aX2[L(0)] - Axy_ - Axz_;
+        d.jc[1] = dxy(4) + aY2[L(0)] - Ayx - Ayz_;
+        d.jc[2] = aZ2[L(0)] - Azx - Azy;
 
         T f[3] = {T(0), T(0), T(0)};
         if (forcing) {
-          const Cplx<T> e = cmul(exy, cmul(rz[(int)(((long long)K.kmod[2] * z) % nz)], ephi));
+          const Cplx<T> e = cmul(exy, cmul(rz[mz], ephi));
 #pragma unroll
           for (int a = 0; a < 3; ++a) f[a] = fa[a] * e.re - fb[a] * e.im;
         }
         const T fr[3] = {force_in_rhs ? f[0] : T(0), force_in_rhs ? f[1] : T(0), force_in_rhs ? f[2] : T(0)};
         T r[NF];
         rhs_point(d, c, fr, r);
-        const long long cidx = ((long long)(z + OZ) * py + (y + OY)) * px + (x + OX);
         T qn[NF];
 #pragma unroll
         for (int fld = 0; fld < NF; ++fld) {
           T wv = dt * r[fld];
-          if (substep > 0) wv += alpha * w[fld * fs + cidx];
-          if (substep < 2) w[fld * fs + cidx] = wv;
-          qn[fld] = pen[fld][3] + beta * wv;
+          if (substep > 0) wv += alpha * wc[fld];
+          if (substep < 2) __stcs(w + fld * fs + cidx, wv);
+          qn[fld] = Z(fld, 0) + beta * wv;
         }
         if (force_at_end)
           for (int a = 0; a < 3; ++a) qn[1 + a] += dt * f[a];
-        int ix[7], iy[7], iz[7];
-        const int cx = periodic_images(x, nx, ix);
-        const int cy = periodic_images(y, ny, iy);
-        const int cz = periodic_images(z, nz, iz);
-        for (int a = 0; a < cz; ++a)
-          for (int b = 0; b < cy; ++b)
-            for (int e = 0; e < cx; ++e) {
-              const long long oo = ((long long)(iz[a] + OZ) * py + (iy[b] + OY)) * px + (ix[e] + OX);
+        if (!(edge_xy || z < RAD || z >= nz - RAD)) {
 #pragma unroll
-              for (int fld = 0; fld < NF; ++fld) qout[fld * fs + oo] = qn[fld];
-            }
-      }
-      // retire the accumulator of the output plane
+          for (int fld = 0; fld < NF; ++fld) __stcs(qout + fld * fs + cidx, qn[fld]);
+        } else {
+          // point near a face: also write its periodic images in the ghost zones
+          int ix[7], iy[7], iz[7];
+          const int cx = periodic_images(x, nx, ix);
+          const int cy = periodic_images(y, ny, iy);
+          const int cz = periodic_images(z, nz, iz);
+          for (int a = 0; a < cz; ++a)
+            for (int b = 0; b < cy; ++b)
+              for (int e = 0; e < cx; ++e) {
+                const long long oo = ((long long)(iz[a] + OZ) * py + (iy[b] + OY)) * px + (ix[e] + OX);
 #pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        aX1[k] = aX1[k + 1]; aY1[k] = aY1[k + 1]; aZ1[k] = aZ1[k + 1];
-        aX2[k] = aX2[k + 1]; aY2[k] = aY2[k + 1]; aZ2[k] = aZ2[k + 1];
+                for (int fld = 0; fld < NF; ++fld) __stcs(qout + fld * fs + oo, qn[fld]);
+              }
+        }
       }
-      aX1[6] = aY1[6] = aZ1[6] = aX2[6] = aY2[6] = aZ2[6] = T(0);
+      if (p >= 2 * RAD) {
+        cidx += wplane;
+        if (forcing) {
+          mz += kz;
+          if (mz >= nz) mz -= nz;
+        }
+      }
+      // retire the accumulators of the output plane: its ring slot becomes
+      // the one of output plane p+4 at the next phase
+      aX1[L(0)] = aY1[L(0)] = aZ1[L(0)] = aX2[L(0)] = aY2[L(0)] = aZ2[L(0)] = T(0);
+      if (++slot == NS) {
+        slot = 0;
+        phase ^= 1u;
+      }
       if (__syncthreads_or(!ok)) {
         failed = true;
-        break;
+        fail_run = tile.run;
+        fail_p = p;
+      }
+    };
+
+    if constexpr (UNROLL7) {
+      // seven planes per iteration: the ring indices rotate at compile time
+      for (int p = 0; p < npl && !failed; p += 7) {
+        plane(Phase<0>{}, p);
+        if (p + 1 < npl && !failed) plane(Phase<1>{}, p + 1);
+        if (p + 2 < npl && !failed) plane(Phase<2>{}, p + 2);
+        if (p + 3 < npl && !failed) plane(Phase<3>{}, p + 3);
+        if (p + 4 < npl && !failed) plane(Phase<4>{}, p + 4);
+        if (p + 5 < npl && !failed) plane(Phase<5>{}, p + 5);
+        if (p + 6 < npl && !failed) plane(Phase<6>{}, p + 6);
+      }
+    } else {
+      // one plane per iteration; the rings are shifted by register moves
+      for (int p = 0; p < npl && !failed; ++p) {
+        plane(Phase<0>{}, p);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) pen[f][k] = pen[f][k + 1];
+          aX1[k] = aX1[k + 1]; aY1[k] = aY1[k + 1]; aZ1[k] = aZ1[k + 1];
+          aX2[k] = aX2[k + 1]; aY2[k] = aY2[k + 1]; aZ2[k] = aZ2[k + 1];
+        }
+        aX1[6] = aY1[6] = aZ1[6] = aX2[6] = aY2[6] = aZ2[6] = T(0);
       }
     }
     if (!failed) G += npl;
@@ -356,8 +412,8 @@ __global__ void __launch_bounds__(32 * TY, 1)
 
   if (failed && tid == 0) {
     // record the time-out, then wait (bounded) for the copies still in flight
-    if (cur_tile) atomicOr(&runs[cur_tile->run].clock->status, 2);
-    for (int p = consumed; p < issued_hi; ++p) {
+    atomicOr(&runs[fail_run].clock->status, 2);
+    for (int p = fail_p; p < issued_hi; ++p) {
       const unsigned long long g = G + p;
       mbar_wait(&bars[(int)(g % NS)], (uint32_t)((g / NS) & 1ull));
     }
@@ -366,49 +422,52 @@ __global__ void __launch_bounds__(32 * TY, 1)
 
 namespace {
 
-template <typename T, int TY, int NS>
+template <typename T, int TY, int NS, bool U>
 int tma_smem_bytes() {
   return NS * TmaShape<T, TY>::STAGE_BYTES + NS * 8;
 }
 
-template <typename T, int TY, int NS>
+template <typename T, int TY, int NS, bool U>
 int prepare_tma() {
-  return (int)cudaFuncSetAttribute(k_substep_tma<T, TY, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   tma_smem_bytes<T, TY, NS>());
+  return (int)cudaFuncSetAttribute(k_substep_tma<T, TY, NS, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   tma_smem_bytes<T, TY, NS, U>());
 }
 
-template <typename T, int TY, int NS>
+template <typename T, int TY, int NS, bool U>
 int launch_tma(const RunDesc *runs, const Tile *tiles, int ntiles, int substep, int grid, cudaStream_t s) {
   if (grid <= 0 || grid > ntiles) grid = ntiles;
   if (grid == 0) return 0;
-  k_substep_tma<T, TY, NS><<<grid, dim3(32, TY), tma_smem_bytes<T, TY, NS>(), s>>>(runs, tiles, ntiles, substep);
+  k_substep_tma<T, TY, NS, U><<<grid, dim3(32, TY), tma_smem_bytes<T, TY, NS, U>(), s>>>(runs, tiles, ntiles,
+                                                                                       substep);
   return (int)cudaGetLastError();
 }
 
-template <typename T, int TY, int NS>
+template <typename T, int TY, int NS, bool U>
 int occupancy_tma(int *bps) {
-  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_substep_tma<T, TY, NS>, 32 * TY,
-                                                            tma_smem_bytes<T, TY, NS>());
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_substep_tma<T, TY, NS, U>, 32 * TY,
+                                                            tma_smem_bytes<T, TY, NS, U>());
 }
 
 }  // namespace
 
-// Tile variants of the TMA kernel: id -> (dtype, TY, stages).
-//   FP32: 1 = 32x8, 6 stages; 2 = 32x4, 6 stages; 3 = 32x8, 8 stages; 4 = 32x16, 6 stages
-//   FP64: 1 = 32x4, 6 stages; 2 = 32x8, 5 stages
-#define MHD_TMA_VARIANTS(X)     \
-  X(0, 1, float, 8, 6)          \
-  X(0, 2, float, 4, 6)          \
-  X(0, 3, float, 8, 8)          \
-  X(0, 4, float, 16, 6)         \
-  X(1, 1, double, 4, 6)         \
-  X(1, 2, double, 8, 5)
+// Tile variants of the TMA kernel: id -> (dtype, TY, stages, ring rotation
+// by 7-fold unrolling instead of register moves).
+//   FP32: 1 = 32x8/6; 2 = 32x4/6; 3 = 32x8/8; 4 = 32x8/6 unrolled; 5 = 32x4/6 unrolled
+//   FP64: 1 = 32x4/6; 2 = 32x4/6 unrolled
+#define MHD_TMA_VARIANTS(X)         \
+  X(0, 1, float, 8, 6, false)       \
+  X(0, 2, float, 4, 6, false)       \
+  X(0, 3, float, 8, 8, false)       \
+  X(0, 4, float, 8, 6, true)        \
+  X(0, 5, float, 4, 6, true)        \
+  X(1, 1, double, 4, 6, false)      \
+  X(1, 2, double, 4, 6, true)
 
-int tma_num_tiles(int dtype) { return dtype == 0 ? 4 : 2; }
+int tma_num_tiles(int dtype) { return dtype == 0 ? 5 : 2; }
 
 int tma_tile_shape(int dtype, int tile, int *tx, int *ty) {
   *tx = 32;
-#define X(DT, ID, T, TY, NS) \
+#define X(DT, ID, T, TY, NS, U) \
   if (dtype == DT && tile == ID) { *ty = TY; return 0; }
   MHD_TMA_VARIANTS(X)
 #undef X
@@ -416,16 +475,16 @@ int tma_tile_shape(int dtype, int tile, int *tx, int *ty) {
 }
 
 int tma_prepare(int dtype, int tile) {
-#define X(DT, ID, T, TY, NS) \
-  if (dtype == DT && tile == ID) return prepare_tma<T, TY, NS>();
+#define X(DT, ID, T, TY, NS, U) \
+  if (dtype == DT && tile == ID) return prepare_tma<T, TY, NS, U>();
   MHD_TMA_VARIANTS(X)
 #undef X
   return (int)cudaErrorInvalidValue;
 }
 
 int tma_occupancy(int dtype, int tile, int *bps) {
-#define X(DT, ID, T, TY, NS) \
-  if (dtype == DT && tile == ID) return occupancy_tma<T, TY, NS>(bps);
+#define X(DT, ID, T, TY, NS, U) \
+  if (dtype == DT && tile == ID) return occupancy_tma<T, TY, NS, U>(bps);
   MHD_TMA_VARIANTS(X)
 #undef X
   return (int)cudaErrorInvalidValue;
@@ -433,8 +492,8 @@ int tma_occupancy(int dtype, int tile, int *bps) {
 
 int tma_launch(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles, int substep, int grid,
                cudaStream_t s) {
-#define X(DT, ID, T, TY, NS) \
-  if (dtype == DT && tile == ID) return launch_tma<T, TY, NS>(runs, tiles, ntiles, substep, grid, s);
+#define X(DT, ID, T, TY, NS, U) \
+  if (dtype == DT && tile == ID) return launch_tma<T, TY, NS, U>(runs, tiles, ntiles, substep, grid, s);
   MHD_TMA_VARIANTS(X)
 #undef X
   return (int)cudaErrorInvalidValue;
