@@ -113,12 +113,12 @@ int validate(const mhd_params *p, std::string *why) {
 }
 
 // AUTO resolves to the TMA kernel; tile 0 to the default tile of the kernel
-// (the fastest measured at 256^3 on B300: FP32 32x8 with 8 stages, FP64
+// (the fastest measured at 256^3 on B300: FP32 32x8 with 6 stages, FP64
 // 32x4 with 6 stages).
 mhd_params resolved(const mhd_params *p) {
   mhd_params r = *p;
   if (r.kernel == MHD_KERNEL_AUTO) r.kernel = MHD_KERNEL_TMA;
-  if (r.kernel == MHD_KERNEL_TMA && r.tile == 0) r.tile = r.dtype == MHD_F32 ? 3 : 1;
+  if (r.kernel == MHD_KERNEL_TMA && r.tile == 0) r.tile = 1;
   return r;
 }
 
@@ -268,7 +268,7 @@ int check_status(mhd_ctx *ctx, const Clock &c) {
 
 int enqueue_step(cudaStream_t s, int dtype, int kernel, int tile, int tw, int th,
                  const RunDesc *runs, const Tile *tiles, int ntiles, int grid) {
-  int e = launch_prologue(dtype, runs, tiles, ntiles, tw, th, s);
+  int e = launch_prologue(dtype, kernel, tile, runs, tiles, ntiles, tw, th, s);
   for (int sub = 0; sub < 3 && e == 0; ++sub)
     e = launch_substep(dtype, kernel, tile, runs, tiles, ntiles, sub, grid, s);
   return e;
@@ -525,7 +525,9 @@ int mhd_step_timed(mhd_ctx *ctx, int nsteps, double *stage_ms, double *total_ms)
   cudaStream_t s = ctx->stream;
   for (int i = 0; i < nsteps && rc == MHD_OK; ++i) {
     int e = (int)cudaEventRecord(ev[4 * i], s);
-    if (!e) e = launch_prologue(ctx->p.dtype, ctx->d_run, ctx->d_tiles, ctx->ntiles, ctx->L.tw, ctx->L.th, s);
+    if (!e)
+      e = launch_prologue(ctx->p.dtype, ctx->p.kernel, ctx->p.tile, ctx->d_run, ctx->d_tiles, ctx->ntiles,
+                          ctx->L.tw, ctx->L.th, s);
     for (int sub = 0; sub < 3 && !e; ++sub) {
       e = (int)cudaEventRecord(ev[4 * i + 1 + sub], s);
       if (!e) e = launch_substep(ctx->p.dtype, ctx->p.kernel, ctx->p.tile, ctx->d_run, ctx->d_tiles,

@@ -279,6 +279,12 @@ int prepare_substep(int dtype, int kernel, int tile) {
   return dtype == 0 ? prepare_smem<float, 32, 8>() : prepare_smem<double, 32, 4>();
 }
 
+int launch_prologue(int dtype, int kernel, int tile, const RunDesc *runs, const Tile *tiles, int ntiles,
+                    int tw, int th, cudaStream_t s) {
+  if (kernel == 2) return tma_launch_prologue(dtype, tile, runs, tiles, ntiles, s);
+  return launch_prologue_plain(dtype, runs, tiles, ntiles, tw, th, s);
+}
+
 int launch_substep(int dtype, int kernel, int tile, const RunDesc *runs, const Tile *tiles,
                    int ntiles, int substep, int grid, cudaStream_t s) {
   if (kernel == 2) return tma_launch(dtype, tile, runs, tiles, ntiles, substep, grid, s);

@@ -27,6 +27,7 @@
 
 #include "mhd_internal.h"
 #include "physics.cuh"
+#include "step_device.cuh"
 
 namespace mhd {
 
@@ -214,9 +215,9 @@ __global__ void __launch_bounds__(32 * TY, 1)
 #pragma unroll
       for (int f = 0; f < NF; ++f) wc[f] = wn[f];
       if (need_w && p >= 2 * RAD - 1 && p + 1 < npl) {
-        const long long nidx = cidx + (p >= 2 * RAD ? wplane : 0);
+        const T *wp = w + cidx + (p >= 2 * RAD ? wplane : 0);
 #pragma unroll
-        for (int f = 0; f < NF; ++f) wn[f] = __ldcs(w + f * fs + nidx);
+        for (int f = 0; f < NF; ++f, wp += fs) wn[f] = __ldcs(wp);
       }
       const bool ok = mbar_wait(&bars[slot], phase);
       const T *lead = reinterpret_cast<const T *>(smem + slot * SH::STAGE_BYTES) + cxy;
@@ -226,19 +227,22 @@ __global__ void __launch_bounds__(32 * TY, 1)
       auto dys = [&](int f, int s) { return lead[f * FIELD + s * SX] - lead[f * FIELD - s * SX]; };
 #pragma unroll
       for (int s = 1; s <= 3; ++s) {
+        // plane p adds +w_s dx_s to output plane p-s and -w_s dx_s to p+s
         const T mxz = c.cm[1][s], myz = c.cm[2][s];
-        const T tX1 = mxz * dxs(3, s);                    // d_x d_z u_z
-        const T tY1 = myz * dys(3, s);                    // d_y d_z u_z
-        const T tZ1 = mxz * dxs(1, s) + myz * dys(2, s);  // d_x d_z u_x + d_y d_z u_y
-        const T tX2 = mxz * dxs(6, s);                    // d_x d_z A_z
-        const T tY2 = myz * dys(6, s);                    // d_y d_z A_z
-        const T tZ2 = mxz * dxs(4, s) + myz * dys(5, s);  // d_x d_z A_x + d_y d_z A_y
-        aX1[L(3 - s)] += tX1; aX1[L(3 + s)] -= tX1;
-        aY1[L(3 - s)] += tY1; aY1[L(3 + s)] -= tY1;
-        aZ1[L(3 - s)] += tZ1; aZ1[L(3 + s)] -= tZ1;
-        aX2[L(3 - s)] += tX2; aX2[L(3 + s)] -= tX2;
-        aY2[L(3 - s)] += tY2; aY2[L(3 + s)] -= tY2;
-        aZ2[L(3 - s)] += tZ2; aZ2[L(3 + s)] -= tZ2;
+        const T ux_ = dxs(1, s), uy_ = dys(2, s), uzx = dxs(3, s), uzy = dys(3, s);
+        const T Ax_ = dxs(4, s), Ay_ = dys(5, s), Azx = dxs(6, s), Azy = dys(6, s);
+        aX1[L(3 - s)] = fma(mxz, uzx, aX1[L(3 - s)]);   // d_x d_z u_z
+        aX1[L(3 + s)] = fma(-mxz, uzx, aX1[L(3 + s)]);
+        aY1[L(3 - s)] = fma(myz, uzy, aY1[L(3 - s)]);   // d_y d_z u_z
+        aY1[L(3 + s)] = fma(-myz, uzy, aY1[L(3 + s)]);
+        aZ1[L(3 - s)] = fma(myz, uy_, fma(mxz, ux_, aZ1[L(3 - s)]));  // d_x d_z u_x + d_y d_z u_y
+        aZ1[L(3 + s)] = fma(-myz, uy_, fma(-mxz, ux_, aZ1[L(3 + s)]));
+        aX2[L(3 - s)] = fma(mxz, Azx, aX2[L(3 - s)]);   // d_x d_z A_z
+        aX2[L(3 + s)] = fma(-mxz, Azx, aX2[L(3 + s)]);
+        aY2[L(3 - s)] = fma(myz, Azy, aY2[L(3 - s)]);   // d_y d_z A_z
+        aY2[L(3 + s)] = fma(-myz, Azy, aY2[L(3 + s)]);
+        aZ2[L(3 - s)] = fma(myz, Ay_, fma(mxz, Ax_, aZ2[L(3 - s)]));  // d_x d_z A_x + d_y d_z A_y
+        aZ2[L(3 + s)] = fma(-myz, Ay_, fma(-mxz, Ax_, aZ2[L(3 + s)]));
       }
 
       if (p >= 2 * RAD && ok && active) {
@@ -334,18 +338,20 @@ __global__ void __launch_bounds__(32 * TY, 1)
         T r[NF];
         rhs_point(d, c, fr, r);
         T qn[NF];
+        T *wp = w + cidx;
 #pragma unroll
-        for (int fld = 0; fld < NF; ++fld) {
+        for (int fld = 0; fld < NF; ++fld, wp += fs) {
           T wv = dt * r[fld];
           if (substep > 0) wv += alpha * wc[fld];
-          if (substep < 2) __stcs(w + fld * fs + cidx, wv);
+          if (substep < 2) __stcs(wp, wv);
           qn[fld] = Z(fld, 0) + beta * wv;
         }
         if (force_at_end)
           for (int a = 0; a < 3; ++a) qn[1 + a] += dt * f[a];
         if (!(edge_xy || z < RAD || z >= nz - RAD)) {
+          T *qp = qout + cidx;
 #pragma unroll
-          for (int fld = 0; fld < NF; ++fld) __stcs(qout + fld * fs + cidx, qn[fld]);
+          for (int fld = 0; fld < NF; ++fld, qp += fs) __stcs(qp, qn[fld]);
         } else {
           // point near a face: also write its periodic images in the ghost zones
           int ix[7], iy[7], iz[7];
@@ -420,6 +426,113 @@ __global__ void __launch_bounds__(32 * TY, 1)
   }
 }
 
+// Step prologue over TMA-staged planes: max over the run's points of
+// |u| + sqrt(cs^2 + |B|^2 / rho), B = curl A with the first-derivative
+// stencil (z-derivatives of A_x, A_y from register pencils, x/y derivatives
+// from shared memory).  One CTA per tile; the last CTA of each run sets dt,
+// draws the forcing and advances the clock (finalize_step).
+constexpr int PRO_NS = 6;
+
+template <typename T, int TY>
+__global__ void __launch_bounds__(32 * TY, 1)
+    k_prologue_tma(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles) {
+  using SH = TmaShape<T, TY>;
+  constexpr int TX = SH::TX, SX = SH::SX, FIELD = SH::FIELD, NS = PRO_NS, P = NS - 4;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ double sh[32 * TY];
+  __shared__ int flag;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * SH::STAGE_BYTES);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const Tile tile = tiles[blockIdx.x];
+  const RunDesc &R = runs[tile.run];
+  const long long step = R.clock->step;
+  double vmax = 0.0;
+  if (R.dt_fixed <= 0.0) {
+    if (tid == 0) {
+      for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    const CUtensorMap *map = &R.tmap[step & 1];
+    const int npl = (tile.z1 - tile.z0) + 2 * RAD;
+    auto issue = [&](int p) {
+      const int sl = p % NS;
+      mbar_arrive_expect_tx(&bars[sl], (uint32_t)(NF * FIELD * sizeof(T)));
+      tma_load_4d(smem + sl * SH::STAGE_BYTES, map, &bars[sl], tile.x0, tile.y0, tile.z0 + p, 0);
+    };
+    int issued = 0;
+    if (tid == 0) {
+      issued = npl < P ? npl : P;
+      for (int p = 0; p < issued; ++p) issue(p);
+    }
+    T w[3][4];
+    for (int a = 0; a < 3; ++a)
+      for (int s = 0; s < 4; ++s) w[a][s] = T(W1(s) * R.inv_h[a]);
+    const T cs2 = T(R.cs2);
+    const int x = tile.x0 + tx, y = tile.y0 + ty;
+    const bool active = x < R.nx && y < R.ny;
+    const int cxy = (ty + RAD) * SX + tx + 4;
+    T ax[7], ay[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) ax[k] = ay[k] = T(0);
+    bool failed = false;
+    int p = 0;
+    for (; p < npl; ++p) {
+      if (tid == 0 && p + P < npl) {
+        fence_proxy_async_smem();
+        issue(p + P);
+        issued = p + P + 1;
+      }
+      const int sl = p % NS;
+      const bool ok = mbar_wait(&bars[sl], (uint32_t)((p / NS) & 1));
+      const T *lead = reinterpret_cast<const T *>(smem + sl * SH::STAGE_BYTES) + cxy;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        ax[k] = ax[k + 1];
+        ay[k] = ay[k + 1];
+      }
+      ax[6] = lead[4 * FIELD];
+      ay[6] = lead[5 * FIELD];
+      if (p >= 2 * RAD && ok && active) {
+        const T *o = reinterpret_cast<const T *>(smem + ((p - RAD) % NS) * SH::STAGE_BYTES) + cxy;
+        auto dx = [&](int f) {
+          return w[0][1] * (o[f * FIELD + 1] - o[f * FIELD - 1]) + w[0][2] * (o[f * FIELD + 2] - o[f * FIELD - 2]) +
+                 w[0][3] * (o[f * FIELD + 3] - o[f * FIELD - 3]);
+        };
+        auto dy = [&](int f) {
+          return w[1][1] * (o[f * FIELD + SX] - o[f * FIELD - SX]) +
+                 w[1][2] * (o[f * FIELD + 2 * SX] - o[f * FIELD - 2 * SX]) +
+                 w[1][3] * (o[f * FIELD + 3 * SX] - o[f * FIELD - 3 * SX]);
+        };
+        const T dzAx = w[2][1] * (ax[4] - ax[2]) + w[2][2] * (ax[5] - ax[1]) + w[2][3] * (ax[6] - ax[0]);
+        const T dzAy = w[2][1] * (ay[4] - ay[2]) + w[2][2] * (ay[5] - ay[1]) + w[2][3] * (ay[6] - ay[0]);
+        const T Bx = dy(6) - dzAy;
+        const T By = dzAx - dx(6);
+        const T Bz = dx(5) - dy(4);
+        const T ux = o[FIELD], uy = o[2 * FIELD], uz = o[3 * FIELD];
+        const T v = sqrt(ux * ux + uy * uy + uz * uz) + sqrt(cs2 + (Bx * Bx + By * By + Bz * Bz) * exp(-o[0]));
+        const double vd = (double)v;
+        vmax = (isnan(vd) || isnan(vmax)) ? vd + vmax : fmax(vmax, vd);
+      }
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+    }
+    if (failed) {
+      if (tid == 0) {
+        atomicOr(&R.clock->status, 2);
+        for (int q = p; q < issued; ++q) mbar_wait(&bars[q % NS], (uint32_t)((q / NS) & 1));
+      }
+      vmax = __longlong_as_double(0x7ff8000000000000ll);  // NaN: the step is marked bad
+    }
+    vmax = block_max(vmax, sh);
+  }
+  if (tid == 0) R.partials[(long long)tile.slot * NPART] = vmax;
+  if (!last_tile_done(&R.counter[0], R.ntiles, &flag)) return;
+  finalize_step(R, step, 1, sh);
+}
+
 namespace {
 
 template <typename T, int TY, int NS, bool U>
@@ -463,6 +576,11 @@ int occupancy_tma(int *bps) {
   X(1, 1, double, 4, 6, false)      \
   X(1, 2, double, 4, 6, true)
 
+template <typename T, int TY>
+int pro_smem_bytes() {
+  return PRO_NS * TmaShape<T, TY>::STAGE_BYTES + PRO_NS * 8;
+}
+
 int tma_num_tiles(int dtype) { return dtype == 0 ? 5 : 2; }
 
 int tma_tile_shape(int dtype, int tile, int *tx, int *ty) {
@@ -475,8 +593,14 @@ int tma_tile_shape(int dtype, int tile, int *tx, int *ty) {
 }
 
 int tma_prepare(int dtype, int tile) {
-#define X(DT, ID, T, TY, NS, U) \
-  if (dtype == DT && tile == ID) return prepare_tma<T, TY, NS, U>();
+#define X(DT, ID, T, TY, NS, U)                                                                          \
+  if (dtype == DT && tile == ID) {                                                                       \
+    int e = prepare_tma<T, TY, NS, U>();                                                                 \
+    if (!e)                                                                                              \
+      e = (int)cudaFuncSetAttribute(k_prologue_tma<T, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                    pro_smem_bytes<T, TY>());                                            \
+    return e;                                                                                            \
+  }
   MHD_TMA_VARIANTS(X)
 #undef X
   return (int)cudaErrorInvalidValue;
@@ -485,6 +609,19 @@ int tma_prepare(int dtype, int tile) {
 int tma_occupancy(int dtype, int tile, int *bps) {
 #define X(DT, ID, T, TY, NS, U) \
   if (dtype == DT && tile == ID) return occupancy_tma<T, TY, NS, U>(bps);
+  MHD_TMA_VARIANTS(X)
+#undef X
+  return (int)cudaErrorInvalidValue;
+}
+
+int tma_launch_prologue(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles,
+                        cudaStream_t s) {
+  if (ntiles <= 0) return 0;
+#define X(DT, ID, T, TY, NS, U)                                                                       \
+  if (dtype == DT && tile == ID) {                                                                    \
+    k_prologue_tma<T, TY><<<ntiles, dim3(32, TY), pro_smem_bytes<T, TY>(), s>>>(runs, tiles);         \
+    return (int)cudaGetLastError();                                                                   \
+  }
   MHD_TMA_VARIANTS(X)
 #undef X
   return (int)cudaErrorInvalidValue;

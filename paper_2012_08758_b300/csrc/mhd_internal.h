@@ -79,8 +79,12 @@ void set_last_error(const char *msg);
 
 // ---- launchers (kernels.cu / reduce.cu) -------------------------------------
 // dtype: 0 = float, 1 = double.  All return a cudaError_t as int.
-int launch_prologue(int dtype, const RunDesc *runs, const Tile *tiles, int ntiles, int tw, int th,
-                    cudaStream_t s);
+// Step prologue (max-speed reduction, dt, forcing draw, clock) for runs of
+// the given kernel variant (TMA runs use the TMA prologue).
+int launch_prologue(int dtype, int kernel, int tile, const RunDesc *runs, const Tile *tiles, int ntiles,
+                    int tw, int th, cudaStream_t s);
+int launch_prologue_plain(int dtype, const RunDesc *runs, const Tile *tiles, int ntiles, int tw, int th,
+                          cudaStream_t s);
 int launch_substep(int dtype, int kernel, int tile, const RunDesc *runs, const Tile *tiles,
                    int ntiles, int substep, int grid, cudaStream_t s);
 int prepare_substep(int dtype, int kernel, int tile);
@@ -89,6 +93,8 @@ int tma_num_tiles(int dtype);
 int tma_tile_shape(int dtype, int tile, int *tx, int *ty);
 int tma_prepare(int dtype, int tile);
 int tma_occupancy(int dtype, int tile, int *bps);
+int tma_launch_prologue(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles,
+                        cudaStream_t s);
 int tma_launch(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles, int substep,
                int grid, cudaStream_t s);
 int substep_tile_shape(int dtype, int kernel, int tile, int *tx, int *ty);
