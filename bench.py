@@ -24,6 +24,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -280,6 +282,167 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """C4: 16 x 64^3 + 8 x 128^3 runs, nu = eta log-spaced for Re_M 5-250,
+    alternating helicity, FP32; one batch (persistent launch per stage, CUDA
+    graph) against the same runs stepped one at a time."""
+    import torch
+
+    from paper_2012_08758_b300 import autotune
+    from paper_2012_08758_b300 import binding as B
+    from paper_2012_08758_b300 import inputs
+    from paper_2012_08758_b300.run import Batch, Run
+    from paper_2012_08758_b300.serving import KF
+
+    sizes = [64] * 16 + [128] * 8
+    rems = np.exp(np.linspace(np.log(5.0), np.log(250.0), len(sizes)))
+    best = autotune.tune([(n, n, n) for n in sizes], B.MHD_F32, steps=3)
+    cells = sum(n ** 3 for n in sizes)
+
+    def make():
+        runs = []
+        for i, (n, rem) in enumerate(zip(sizes, rems)):
+            nu = 0.05 / (rem * KF)
+            r = Run(n=n, nu=nu, eta=nu, f0=0.02, sigma=float(i % 2), seed=100 + i, kernel=best["kernel"],
+                    tile=best["tile"])
+            r.set_state(inputs.seed_field_state(n, seed=i))
+            runs.append(r)
+        return runs
+
+    runs = make()
+    b = Batch(runs)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    stream = runs[0].stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    for r in runs:
+        r.sync()
+    b.close()
+    for r in runs:
+        r.close()
+    runs = make()
+    for r in runs:
+        r.step(args.warmup)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for r in runs:
+        r.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    t_serial = e0.elapsed_time(e1) / 1e3
+    for r in runs:
+        r.close()
+    line = {"workload": "batch: 16x64^3 + 8x128^3, Re_M 5-250 log-spaced, sigma 0/1 alternating, FP32",
+            "metric": UNIT, "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
+            "batched": cells * args.steps / t_batch, "one_at_a_time": cells * args.steps / t_serial,
+            "speedup": t_serial / t_batch, "autotune": best, "cells": cells}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """C5: Poisson stream of seeded requests (grid uniform over {64, 96, 128,
+    192, 256}, Re_M log-uniform 10-250, sigma in {0, 1}); the step budgets
+    are the config's 500-5000 scaled by --serve-scale.  Continuous batching
+    under a 150 GB HBM budget; p50/p99 latency and aggregate throughput,
+    against serial FP64 stepping of the same work (per-size FP64 rates
+    measured here) and growth rates against FP64 runs of the smallest
+    requests."""
+    import torch
+
+    from paper_2012_08758_b300 import binding as B
+    from paper_2012_08758_b300.run import Run
+    from paper_2012_08758_b300.serving import Server, initial_state, requests_from_inputs, run_params, summarize
+    from paper_2012_08758_b300.growth import brms_series, growth_rate
+
+    lo, hi = int(500 * args.serve_scale), int(5000 * args.serve_scale)
+    reqs = requests_from_inputs(n=args.requests, seed=2025, rate=args.serve_rate, steps=(max(lo, 20), max(hi, 40)))
+    srv = Server(budget_bytes=150e9, chunk=args.serve_chunk)
+    t0 = time.perf_counter()
+    res = srv.serve(reqs, realtime=True)
+    wall = time.perf_counter() - t0
+    summ = summarize(res, wall, srv.stepped_cells)
+    # serial FP64: measured rate per grid size on short runs
+    rates = {}
+    for n in sorted({r.n for r in reqs}):
+        rr = Run(n=n, dtype=B.MHD_F64, f0=0.02, seed=1)
+        rr.set_state(initial_state(reqs[0].__class__(0, 0, n, 100.0, 1.0, 10, 1)))
+        rr.step(1)
+        st, tot = B.mhd_step_timed(rr.ctx, 3)
+        rates[n] = n ** 3 * 3 / (tot / 1e3)
+        rr.close()
+    t_serial64 = sum(r.n ** 3 * r.steps / rates[r.n] for r in reqs)
+    # growth-rate accuracy: the served FP32 result equals the FP32 run alone
+    # (tested bit for bit), so FP32 and FP64 runs of the same request with the
+    # same sampling are compared, for the smallest requests
+    checks = []
+    for r in sorted(reqs, key=lambda q: q.n ** 3 * q.steps)[: args.serve_checks]:
+        lam = {}
+        for dt in (B.MHD_F32, B.MHD_F64):
+            rr = Run(**run_params(r, dtype=dt))
+            rr.set_state(initial_state(r))
+            ts, bs = brms_series(rr, r.steps, max(1, r.steps // 40))
+            rr.close()
+            lam[dt] = growth_rate(ts, bs, (0.5 * ts[-1], ts[-1]))
+        checks.append({"id": r.id, "n": r.n, "steps": r.steps, "lambda_f32": lam[B.MHD_F32],
+                       "lambda_f64": lam[B.MHD_F64],
+                       "rel_diff": abs(lam[B.MHD_F32] - lam[B.MHD_F64]) / max(abs(lam[B.MHD_F64]), 1e-300)})
+    line = {"workload": f"serve: {args.requests} Poisson requests (rate {args.serve_rate}/s), steps "
+                        f"{max(lo, 20)}-{max(hi, 40)}, FP32 continuous batching, 150 GB budget",
+            "metric": "p50/p99 job latency and aggregate cell-updates/s", **summ,
+            "serial_fp64_cell_updates_per_s": sum(r.n ** 3 * r.steps for r in reqs) / t_serial64,
+            "speedup_vs_serial_fp64": summ["cell_updates_per_s"] / (sum(r.n ** 3 * r.steps for r in reqs) / t_serial64),
+            "fp64_rates": rates, "growth_rate_checks": checks,
+            "max_growth_rate_rel_diff": max((c["rel_diff"] for c in checks), default=None)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_fp32vs64(args):
+    """C3: the same initial state advanced in FP32 and in FP64 on the GPU;
+    per-quantity FP32 error against FP64 (fields, rms values, energies,
+    growth rate of ln B_rms over the second half)."""
+    from paper_2012_08758_b300 import binding as B
+    from paper_2012_08758_b300 import inputs
+    from paper_2012_08758_b300.growth import brms_series, growth_rate
+    from paper_2012_08758_b300.run import Run
+
+    n = args.n
+    wl = dict(WORKLOAD, nu=1.25e-4, eta=1.25e-4)  # Re_M ~ 250 at u_rms ~ 0.05 (512^3 config)
+    q0 = inputs.seed_field_state(n, seed=0, amp=1e-5)
+    out = {}
+    for dt in (B.MHD_F32, B.MHD_F64):
+        r = Run(n=n, dtype=dt, **wl)
+        r.set_state(q0)
+        t0 = time.perf_counter()
+        ts, bs = brms_series(r, args.steps, max(1, args.steps // 20))
+        el = time.perf_counter() - t0
+        st, t, _ = r.get_state(dtype=np.float32 if dt == B.MHD_F32 else np.float64)
+        out[dt] = dict(state=st.astype(np.float64), diag=r.diagnostics(), ts=ts, bs=bs, wall=el)
+        r.close()
+    a, b = out[B.MHD_F32], out[B.MHD_F64]
+    umax = np.abs(b["state"][1:4]).max()
+    amax = np.abs(b["state"][4:7]).max()
+    scales = [max(np.abs(b["state"][0]).max(), umax), umax, umax, umax, amax, amax, amax]
+    field_err = {name: float(np.abs(a["state"][i] - b["state"][i]).max() / scales[i])
+                 for i, name in enumerate(("lnrho", "ux", "uy", "uz", "Ax", "Ay", "Az"))}
+    diag_err = {k: abs(a["diag"][k] - b["diag"][k]) / max(abs(b["diag"][k]), 1e-300)
+                for k in ("urms", "brms", "ekin", "emag", "umax", "bmax", "mass")}
+    w = (0.5 * b["ts"][-1], b["ts"][-1])
+    la, lb = growth_rate(a["ts"], a["bs"], w), growth_rate(b["ts"], b["bs"], w)
+    line = {"workload": f"{n}^3 helical forcing, Re_M ~ 250 (nu = eta = 1.25e-4), {args.steps} steps, FP32 vs FP64",
+            "field_rel_linf": field_err, "diag_rel": diag_err, "lambda_f32": la, "lambda_f64": lb,
+            "lambda_rel": abs(la - lb) / max(abs(lb), 1e-300), "t_end": b["ts"][-1],
+            "wall_s": {"f32": a["wall"], "f64": b["wall"]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -288,6 +451,14 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--workload", choices=["step", "batch", "serve", "fp32vs64"], default="step",
+                    help="step: the benchmark line; the others measure the batch (16x64^3+8x128^3), "
+                         "serving and FP32-vs-FP64 configurations")
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--serve-rate", type=float, default=3.0, help="request arrivals per second")
+    ap.add_argument("--serve-scale", type=float, default=0.1, help="scale of the 500-5000 step budgets")
+    ap.add_argument("--serve-chunk", type=int, default=25)
+    ap.add_argument("--serve-checks", type=int, default=6)
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 plane ring, 2 TMA")
     ap.add_argument("--tile", type=int, default=0, help="tile variant id (0: default)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU-baseline leg")
@@ -297,6 +468,12 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
+    if args.workload == "fp32vs64":
+        return run_fp32vs64(args)
     return run_ours(args)
 
 

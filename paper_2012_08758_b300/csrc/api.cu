@@ -658,6 +658,7 @@ int mhd_batch_create(mhd_ctx *const *runs, int nruns, mhd_batch **out) {
   if (!r0) return fail(nullptr, MHD_EINVAL, "runs[0] is NULL");
   std::vector<RunDesc> descs;
   std::vector<Tile> tiles;
+  double cells_total = 0;
   for (int i = 0; i < nruns; ++i) {
     mhd_ctx *r = runs[i];
     if (!r) return fail(nullptr, MHD_EINVAL, "runs[%d] is NULL", i);
@@ -666,11 +667,25 @@ int mhd_batch_create(mhd_ctx *const *runs, int nruns, mhd_batch **out) {
       return fail(nullptr, MHD_EINVAL, "runs of a batch must share dtype, stream, kernel and tile");
     for (int j = 0; j < i; ++j)
       if (runs[j] == r) return fail(nullptr, MHD_EINVAL, "run %d appears twice", i);
-    descs.push_back(r->h_run);
-    for (const Tile &t : r->L.tiles_host) {
-      Tile u = t;
-      u.run = i;
-      tiles.push_back(u);
+    cells_total += (double)r->p.nx * r->p.ny * r->p.nz;
+  }
+  // The batch has its own tile table: each run gets a share of about two
+  // waves of CTAs in proportion to its size (small runs get whole columns,
+  // so few z-halo planes are re-read).  Substep results are pointwise and
+  // the dt reduction is a maximum, so the tiling changes no run's result;
+  // diagnostics keep using each run's own tiles.
+  for (int i = 0; i < nruns; ++i) {
+    mhd_ctx *r = runs[i];
+    const double share = (double)r->p.nx * r->p.ny * r->p.nz / cells_total;
+    const int target = std::max(1, (int)std::lround(TARGET_CTAS * share));
+    std::vector<Tile> rt = make_tiles(r->p.nx, r->p.ny, r->p.nz, r->L.tw, r->L.th, target);
+    if (rt.size() > r->L.tiles_host.size()) rt = r->L.tiles_host;  // partial slots are sized for these
+    RunDesc d = r->h_run;
+    d.ntiles = (int)rt.size();
+    descs.push_back(d);
+    for (Tile t : rt) {
+      t.run = i;
+      tiles.push_back(t);
     }
   }
   mhd_batch *b = new mhd_batch();

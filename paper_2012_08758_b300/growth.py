@@ -1,0 +1,42 @@
+"""Growth rate of the magnetic field (Sec. 4, after Eq. 7): B_rms ~ exp(lambda t)
+during the kinematic stage; lambda is the least-squares slope of ln B_rms
+against t over a fixed window, computed on the host in FP64."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import binding as B
+
+
+def growth_rate(t, brms, window=None) -> float:
+    """Slope of ln(brms) versus t by linear least squares (FP64).
+
+    window: (t_a, t_b) to restrict the fit, or None for all samples."""
+    t = np.asarray(t, dtype=np.float64)
+    y = np.log(np.asarray(brms, dtype=np.float64))
+    if window is not None:
+        m = (t >= window[0]) & (t <= window[1])
+        t, y = t[m], y[m]
+    if t.size < 2:
+        raise ValueError("need at least two samples in the window")
+    A = np.stack([t, np.ones_like(t)], axis=1)
+    slope, _ = np.linalg.lstsq(A, y, rcond=None)[0]
+    return float(slope)
+
+
+def brms_series(run, nsteps: int, every: int = 1):
+    """Steps `run` (a Run) nsteps times, sampling (t, B_rms) every `every`
+    steps (and at the start).  Returns two numpy arrays."""
+    ts, bs = [], []
+    t, _, _ = run.time()
+    ts.append(t)
+    bs.append(run.reduce(B.MHD_BRMS))
+    done = 0
+    while done < nsteps:
+        k = min(every, nsteps - done)
+        run.step(k)
+        done += k
+        t, _, _ = run.time()
+        ts.append(t)
+        bs.append(run.reduce(B.MHD_BRMS))
+    return np.array(ts), np.array(bs)

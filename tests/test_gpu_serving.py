@@ -1,0 +1,70 @@
+"""Batching and serving: each run's result is the same alone and inside a
+continuously batched serving loop (bit for bit: per-run reductions have a
+fixed order and substeps are pointwise); the autotuner returns a variant
+that runs; admission honours the HBM budget."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests():
+    from paper_2012_08758_b300.serving import Request
+    return [Request(0, 0.0, 24, 50.0, 1.0, 30, 11), Request(1, 0.0, 16, 120.0, 0.0, 45, 12),
+            Request(2, 0.05, 32, 20.0, 1.0, 25, 13), Request(3, 0.10, 16, 200.0, 0.0, 60, 14)]
+
+
+def test_serving_results_equal_runs_alone():
+    from paper_2012_08758_b300 import binding as B
+    from paper_2012_08758_b300.run import Run
+    from paper_2012_08758_b300.serving import Server, initial_state, run_params
+
+    reqs = _requests()
+    srv = Server(chunk=10, time_scale=1.0)
+    res = {r.id: r for r in srv.serve(reqs, realtime=True)}
+    assert sorted(res) == [0, 1, 2, 3]
+    for req in reqs:
+        run = Run(**run_params(req))
+        run.set_state(initial_state(req))
+        # the server stepped this run in chunks inside changing batches; the
+        # final state must be the one of an uninterrupted run
+        run.step(req.steps)
+        d = run.diagnostics()
+        t_end, _, step = run.time()
+        run.close()
+        r = res[req.id]
+        assert step == req.steps
+        assert abs(r.t[-1] - t_end) == 0.0
+        for key in ("urms", "brms", "ekin", "emag", "mass", "vmax", "umax", "bmax"):
+            assert r.diagnostics[key] == d[key], key
+        assert r.latency >= 0 and r.finished >= r.admitted >= 0
+        assert np.isfinite(r.growth_rate)
+
+
+def test_admission_respects_budget():
+    from paper_2012_08758_b300.serving import Server
+
+    reqs = _requests()
+    srv = Server(chunk=10)
+    one = max(srv.footprint(r) for r in reqs)
+    srv = Server(chunk=10, budget_bytes=one * 1.5)  # room for one run at a time
+    peak = []
+    orig = srv._admit
+
+    def spy(req, now):
+        orig(req, now)
+        peak.append(srv.used)
+    srv._admit = spy
+    res = srv.serve(reqs, realtime=False)
+    assert len(res) == 4 and max(peak) <= one * 1.5
+
+
+def test_autotuner_returns_a_working_variant():
+    from paper_2012_08758_b300 import autotune
+    from paper_2012_08758_b300 import binding as B
+
+    best = autotune.tune([(24, 20, 16)], B.MHD_F32, steps=2)
+    assert (best["kernel"], best["tile"]) in autotune.CANDIDATES[B.MHD_F32]
+    assert all(v > 0 for v in best["ms"].values()) and len(best["ms"]) >= 2
+    both = autotune.tune([(16, 16, 16), (24, 24, 24)], B.MHD_F32, steps=2)
+    assert both["ms"]
