@@ -358,7 +358,7 @@ def run_serve(args):
     from paper_2012_08758_b300 import binding as B
     from paper_2012_08758_b300.run import Run
     from paper_2012_08758_b300.serving import Server, initial_state, requests_from_inputs, run_params, summarize
-    from paper_2012_08758_b300.growth import brms_series, growth_rate
+    from paper_2012_08758_b300.growth import brms_series, fit_last
 
     lo, hi = int(500 * args.serve_scale), int(5000 * args.serve_scale)
     reqs = requests_from_inputs(n=args.requests, seed=2025, rate=args.serve_rate, steps=(max(lo, 20), max(hi, 40)))
@@ -388,7 +388,7 @@ def run_serve(args):
             rr.set_state(initial_state(r))
             ts, bs = brms_series(rr, r.steps, max(1, r.steps // 40))
             rr.close()
-            lam[dt] = growth_rate(ts, bs, (0.5 * ts[-1], ts[-1]))
+            lam[dt] = fit_last(ts, bs, 0.5)
         checks.append({"id": r.id, "n": r.n, "steps": r.steps, "lambda_f32": lam[B.MHD_F32],
                        "lambda_f64": lam[B.MHD_F64],
                        "rel_diff": abs(lam[B.MHD_F32] - lam[B.MHD_F64]) / max(abs(lam[B.MHD_F64]), 1e-300)})
@@ -409,7 +409,7 @@ def run_fp32vs64(args):
     growth rate of ln B_rms over the second half)."""
     from paper_2012_08758_b300 import binding as B
     from paper_2012_08758_b300 import inputs
-    from paper_2012_08758_b300.growth import brms_series, growth_rate
+    from paper_2012_08758_b300.growth import brms_series, fit_last
     from paper_2012_08758_b300.run import Run
 
     n = args.n
@@ -433,8 +433,7 @@ def run_fp32vs64(args):
                  for i, name in enumerate(("lnrho", "ux", "uy", "uz", "Ax", "Ay", "Az"))}
     diag_err = {k: abs(a["diag"][k] - b["diag"][k]) / max(abs(b["diag"][k]), 1e-300)
                 for k in ("urms", "brms", "ekin", "emag", "umax", "bmax", "mass")}
-    w = (0.5 * b["ts"][-1], b["ts"][-1])
-    la, lb = growth_rate(a["ts"], a["bs"], w), growth_rate(b["ts"], b["bs"], w)
+    la, lb = fit_last(a["ts"], a["bs"], 0.5), fit_last(b["ts"], b["bs"], 0.5)
     line = {"workload": f"{n}^3 helical forcing, Re_M ~ 250 (nu = eta = 1.25e-4), {args.steps} steps, FP32 vs FP64",
             "field_rel_linf": field_err, "diag_rel": diag_err, "lambda_f32": la, "lambda_f64": lb,
             "lambda_rel": abs(la - lb) / max(abs(lb), 1e-300), "t_end": b["ts"][-1],

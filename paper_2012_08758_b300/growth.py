@@ -11,7 +11,10 @@ from . import binding as B
 def growth_rate(t, brms, window=None) -> float:
     """Slope of ln(brms) versus t by linear least squares (FP64).
 
-    window: (t_a, t_b) to restrict the fit, or None for all samples."""
+    window: (t_a, t_b) to restrict the fit, or None for all samples.  To
+    compare two runs, fit the same samples of each (e.g. via fit_last);
+    an absolute time window can take a boundary sample in one run and not in
+    the other when their times differ by rounding."""
     t = np.asarray(t, dtype=np.float64)
     y = np.log(np.asarray(brms, dtype=np.float64))
     if window is not None:
@@ -22,6 +25,13 @@ def growth_rate(t, brms, window=None) -> float:
     A = np.stack([t, np.ones_like(t)], axis=1)
     slope, _ = np.linalg.lstsq(A, y, rcond=None)[0]
     return float(slope)
+
+
+def fit_last(t, brms, fraction: float = 0.5) -> float:
+    """Growth rate over the last `fraction` of the samples."""
+    t = np.asarray(t)
+    k = int(len(t) * (1.0 - fraction))
+    return growth_rate(t[k:], np.asarray(brms)[k:])
 
 
 def brms_series(run, nsteps: int, every: int = 1):

@@ -23,7 +23,7 @@ import numpy as np
 
 from . import binding as B
 from . import inputs
-from .growth import growth_rate
+from .growth import fit_last
 
 KF = 3.134  # mean |k| of the integer shell 2.5 <= |k| <= 3.5 (98 vectors)
 
@@ -107,8 +107,7 @@ class Server:
     def _retire(self, entry, now: float) -> None:
         run, req, _, admitted, ts, bs, nbytes = entry
         diag = run.diagnostics()
-        t = np.array(ts)
-        lam = growth_rate(t, bs, (t[-1] * (1.0 - self.window), t[-1])) if len(ts) > 2 else float("nan")
+        lam = fit_last(ts, bs, self.window) if len(ts) > 2 else float("nan")
         self.results.append(Result(req.id, req.n, req.steps, req.arrival, admitted, now, lam, diag,
                                    list(ts), list(bs)))
         run.close()
