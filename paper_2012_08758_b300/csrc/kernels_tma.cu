@@ -431,13 +431,17 @@ __global__ void __launch_bounds__(32 * TY, 1)
 // stencil (z-derivatives of A_x, A_y from register pencils, x/y derivatives
 // from shared memory).  One CTA per tile; the last CTA of each run sets dt,
 // draws the forcing and advances the clock (finalize_step).
-constexpr int PRO_NS = 6;
+// Stage count of the prologue: small enough for two CTAs per SM.
+template <typename T, int TY>
+__host__ __device__ constexpr int pro_stages() {
+  return TmaShape<T, TY>::STAGE_BYTES * 6 <= 110 * 1024 ? 6 : 5;
+}
 
 template <typename T, int TY>
 __global__ void __launch_bounds__(32 * TY, 1)
     k_prologue_tma(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles) {
   using SH = TmaShape<T, TY>;
-  constexpr int TX = SH::TX, SX = SH::SX, FIELD = SH::FIELD, NS = PRO_NS, P = NS - 4;
+  constexpr int TX = SH::TX, SX = SH::SX, FIELD = SH::FIELD, NS = pro_stages<T, TY>(), P = NS - 4;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double sh[32 * TY];
   __shared__ int flag;
@@ -565,23 +569,28 @@ int occupancy_tma(int *bps) {
 
 // Tile variants of the TMA kernel: id -> (dtype, TY, stages, ring rotation
 // by 7-fold unrolling instead of register moves).
-//   FP32: 1 = 32x8/6; 2 = 32x4/6; 3 = 32x8/8; 4 = 32x8/6 unrolled; 5 = 32x4/6 unrolled
+//   FP32: 1 = 32x8/6; 2 = 32x4/6; 3 = 32x8/8; 4 = 32x12/6; 5 = 32x12/5; 6 = 32x16/5
 //   FP64: 1 = 32x4/6; 2 = 32x4/6 unrolled
+// (the unrolled FP32 variants measured 1.7x slower on B300: the 7-fold body
+// overflows the instruction cache)
 #define MHD_TMA_VARIANTS(X)         \
   X(0, 1, float, 8, 6, false)       \
   X(0, 2, float, 4, 6, false)       \
   X(0, 3, float, 8, 8, false)       \
-  X(0, 4, float, 8, 6, true)        \
-  X(0, 5, float, 4, 6, true)        \
+  X(0, 4, float, 12, 6, false)      \
+  X(0, 5, float, 12, 5, false)      \
+  X(0, 6, float, 16, 5, false)      \
   X(1, 1, double, 4, 6, false)      \
   X(1, 2, double, 4, 6, true)
 
+int tma_num_tiles(int dtype) { return dtype == 0 ? 6 : 2; }
+
 template <typename T, int TY>
 int pro_smem_bytes() {
-  return PRO_NS * TmaShape<T, TY>::STAGE_BYTES + PRO_NS * 8;
+  return pro_stages<T, TY>() * TmaShape<T, TY>::STAGE_BYTES + pro_stages<T, TY>() * 8;
 }
 
-int tma_num_tiles(int dtype) { return dtype == 0 ? 5 : 2; }
+static_assert(32 * 16 <= MAX_TILE_THREADS, "reduction kernels run with the tile's block shape");
 
 int tma_tile_shape(int dtype, int tile, int *tx, int *ty) {
   *tx = 32;

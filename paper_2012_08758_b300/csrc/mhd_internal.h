@@ -14,6 +14,7 @@ constexpr int OX = 4;            // padded x index of interior point 0 (one spar
 constexpr int OY = 3, OZ = 3;    // padded y / z index of interior point 0
 constexpr int NDIAG = 9;         // quantities of mhd_diagnostics
 constexpr int NPART = 8;         // doubles per reduction tile
+constexpr int MAX_TILE_THREADS = 512;  // largest tile (block) of any substep variant
 
 // Device-resident clock of one run: time, last dt and index of the state
 // currently held in q[step & 1].  Advanced on the device by the step

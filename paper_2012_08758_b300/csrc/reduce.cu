@@ -30,9 +30,9 @@ constexpr int PRO_SPLIT = 1;
 static_assert(PRO_SPLIT <= NPART, "sub-maxima must fit the tile's partial slot");
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_prologue(const RunDesc *__restrict__ runs,
+__global__ void __launch_bounds__(MAX_TILE_THREADS) k_prologue(const RunDesc *__restrict__ runs,
                                                   const Tile *__restrict__ tiles) {
-  __shared__ double sh[256];
+  __shared__ double sh[MAX_TILE_THREADS];
   __shared__ int flag;
   const Tile tile = tiles[blockIdx.x];
   const RunDesc &R = runs[tile.run];
@@ -84,7 +84,7 @@ int launch_prologue_plain(int dtype, const RunDesc *runs, const Tile *tiles, int
 // steps), periodic halo of B, then one reduction pass.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_curl(const RunDesc *__restrict__ runs,
+__global__ void __launch_bounds__(MAX_TILE_THREADS) k_curl(const RunDesc *__restrict__ runs,
                                               const Tile *__restrict__ tiles) {
   const Tile tile = tiles[blockIdx.x];
   const RunDesc &R = runs[tile.run];
@@ -106,9 +106,9 @@ __global__ void __launch_bounds__(256) k_curl(const RunDesc *__restrict__ runs,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_diag(const RunDesc *__restrict__ runs,
+__global__ void __launch_bounds__(MAX_TILE_THREADS) k_diag(const RunDesc *__restrict__ runs,
                                               const Tile *__restrict__ tiles) {
-  __shared__ double sh[256];
+  __shared__ double sh[MAX_TILE_THREADS];
   __shared__ int flag;
   const Tile tile = tiles[blockIdx.x];
   const RunDesc &R = runs[tile.run];

@@ -101,28 +101,39 @@ __device__ __forceinline__ void make_coeffs(const RunDesc &R, long long draw_ste
 // ---------------------------------------------------------------------------
 // Block reduction helpers (fixed tree order: deterministic).
 // ---------------------------------------------------------------------------
+// Any block size: the entries above the largest power of two p2 <= n are
+// folded onto the first ones, then a halving tree; the order is fixed.
 __device__ __forceinline__ double block_sum(double v, double *sh) {
   const int n = blockDim.x * blockDim.y, t = threadIdx.y * blockDim.x + threadIdx.x;
+  int p2 = 1;
+  while (2 * p2 <= n) p2 *= 2;
   __syncthreads();
   sh[t] = v;
   __syncthreads();
-  for (int s = n / 2; s > 0; s >>= 1) {
+  if (t < n - p2) sh[t] += sh[t + p2];
+  __syncthreads();
+  for (int s = p2 / 2; s > 0; s >>= 1) {
     if (t < s) sh[t] += sh[t + s];
     __syncthreads();
   }
   return sh[0];
 }
 
+__device__ __forceinline__ double nan_max(double a, double b) {
+  return (isnan(a) || isnan(b)) ? (a + b) : fmax(a, b);
+}
+
 __device__ __forceinline__ double block_max(double v, double *sh) {
   const int n = blockDim.x * blockDim.y, t = threadIdx.y * blockDim.x + threadIdx.x;
+  int p2 = 1;
+  while (2 * p2 <= n) p2 *= 2;
   __syncthreads();
   sh[t] = v;
   __syncthreads();
-  for (int s = n / 2; s > 0; s >>= 1) {
-    if (t < s) {
-      const double a = sh[t], b = sh[t + s];
-      sh[t] = (isnan(a) || isnan(b)) ? (a + b) : fmax(a, b);
-    }
+  if (t < n - p2) sh[t] = nan_max(sh[t], sh[t + p2]);
+  __syncthreads();
+  for (int s = p2 / 2; s > 0; s >>= 1) {
+    if (t < s) sh[t] = nan_max(sh[t], sh[t + s]);
     __syncthreads();
   }
   return sh[0];

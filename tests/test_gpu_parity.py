@@ -50,7 +50,7 @@ SHAPES = [(32, 32, 32), (37, 23, 11), (40, 8, 20), (12, 9, 1), (16, 1, 1), (1, 1
 
 
 KERNELS = [(2, 0), (1, 0)]  # (kernel, tile): TMA default tile, plane ring
-TMA_TILES = [(2, 1), (2, 2), (2, 3), (2, 4), (2, 5)]
+TMA_TILES = [(2, 1), (2, 2), (2, 3), (2, 4), (2, 5), (2, 6)]
 
 
 @pytest.mark.parametrize("kernel,tile", KERNELS)
@@ -133,6 +133,10 @@ def test_every_tma_tile_fp32_step_parity(kernel, tile):
     q = q0.copy()
     O.run(oracle_params(**kw), q, 5)
     assert rel_linf_state(got, q).max() < 2e-5
+    d = run.diagnostics()  # reductions run with this tile's block shape
+    o = O.diagnostics(oracle_params(**kw), q)
+    for key in ("urms", "brms", "ekin", "emag", "mass", "vmax"):
+        assert d[key] == pytest.approx(o[key], rel=2e-5), key
     run.close()
 
 
