@@ -217,6 +217,7 @@ struct mhd_ctx {
   Tile *d_tiles;
   int ntiles;
   int grid;  // substep launch grid (persistent CTAs)
+  int iso;   // equal grid spacings on all axes
   std::string err;
 };
 
@@ -226,7 +227,7 @@ struct mhd_batch {
   int dtype, kernel, tile, tw, th;
   RunDesc *d_runs;
   Tile *d_tiles;
-  int ntiles, grid;
+  int ntiles, grid, iso;
   cudaGraphExec_t exec;
   int graph_steps;
 };
@@ -267,10 +268,10 @@ int check_status(mhd_ctx *ctx, const Clock &c) {
 }
 
 int enqueue_step(cudaStream_t s, int dtype, int kernel, int tile, int tw, int th,
-                 const RunDesc *runs, const Tile *tiles, int ntiles, int grid) {
+                 const RunDesc *runs, const Tile *tiles, int ntiles, int grid, int iso) {
   int e = launch_prologue(dtype, kernel, tile, runs, tiles, ntiles, tw, th, s);
   for (int sub = 0; sub < 3 && e == 0; ++sub)
-    e = launch_substep(dtype, kernel, tile, runs, tiles, ntiles, sub, grid, s);
+    e = launch_substep(dtype, kernel, tile, runs, tiles, ntiles, sub, grid, iso, s);
   return e;
 }
 
@@ -379,6 +380,7 @@ int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t worksp
     R.kscale[a] = 2.0 * M_PI / Lb[a];
     R.dmin = std::min(R.dmin, h);
   }
+  ctx->iso = R.inv_h[0] == R.inv_h[1] && R.inv_h[1] == R.inv_h[2];
   R.cfl = p->cfl;
   R.cfl_visc = p->cfl_visc;
   R.dt_fixed = p->dt_fixed;
@@ -504,7 +506,7 @@ int mhd_step(mhd_ctx *ctx, int nsteps) {
   if (nsteps < 0) return fail(ctx, MHD_EINVAL, "nsteps must be >= 0");
   for (int i = 0; i < nsteps; ++i) {
     int e = enqueue_step(ctx->stream, ctx->p.dtype, ctx->p.kernel, ctx->p.tile, ctx->L.tw, ctx->L.th,
-                         ctx->d_run, ctx->d_tiles, ctx->ntiles, ctx->grid);
+                         ctx->d_run, ctx->d_tiles, ctx->ntiles, ctx->grid, ctx->iso);
     if (e) return cuda_fail(ctx, e, "mhd_step launch");
   }
   return MHD_OK;
@@ -531,7 +533,7 @@ int mhd_step_timed(mhd_ctx *ctx, int nsteps, double *stage_ms, double *total_ms)
     for (int sub = 0; sub < 3 && !e; ++sub) {
       e = (int)cudaEventRecord(ev[4 * i + 1 + sub], s);
       if (!e) e = launch_substep(ctx->p.dtype, ctx->p.kernel, ctx->p.tile, ctx->d_run, ctx->d_tiles,
-                                 ctx->ntiles, sub, ctx->grid, s);
+                                 ctx->ntiles, sub, ctx->grid, ctx->iso, s);
     }
     if (e) rc = cuda_fail(ctx, e, "mhd_step_timed launch");
   }
@@ -626,7 +628,7 @@ int mhd_eval_rhs(mhd_ctx *ctx, int64_t step, double dt_forcing, void *host_rhs, 
   // overwritten (it is dead between steps) and serves as staging.
   CK(ctx, launch_coeffs(ctx->p.dtype, ctx->d_run, step, 1.0, dt_forcing, par, s));
   CK(ctx, launch_substep(ctx->p.dtype, ctx->p.kernel, ctx->p.tile, ctx->d_run, ctx->d_tiles,
-                         ctx->ntiles, 0, ctx->grid, s));
+                         ctx->ntiles, 0, ctx->grid, ctx->iso, s));
   const size_t npts = (size_t)R.nx * R.ny * R.nz, hb = npts * host_esz(host_dtype);
   void *staging = R.q[par ^ 1];
   for (int f = 0; f < NF; ++f) {
@@ -690,6 +692,8 @@ int mhd_batch_create(mhd_ctx *const *runs, int nruns, mhd_batch **out) {
   }
   mhd_batch *b = new mhd_batch();
   b->runs.assign(runs, runs + nruns);
+  b->iso = 1;
+  for (int i = 0; i < nruns; ++i) b->iso &= runs[i]->iso;
   b->stream = r0->stream;
   b->dtype = r0->p.dtype;
   b->kernel = r0->p.kernel;
@@ -735,7 +739,7 @@ int mhd_batch_step(mhd_batch *b, int nsteps) {
     int le = 0;
     for (int i = 0; i < g && e == cudaSuccess && !le; ++i)
       le = enqueue_step(s, b->dtype, b->kernel, b->tile, b->tw, b->th, b->d_runs, b->d_tiles,
-                        b->ntiles, b->grid);
+                        b->ntiles, b->grid, b->iso);
     cudaError_t e2 = cudaStreamEndCapture(s, &graph);
     if (e == cudaSuccess && !le && e2 == cudaSuccess) {
       if (cudaGraphInstantiate(&b->exec, graph, 0) == cudaSuccess) b->graph_steps = g;
@@ -753,7 +757,7 @@ int mhd_batch_step(mhd_batch *b, int nsteps) {
   }
   for (; done < nsteps; ++done) {
     int e = enqueue_step(s, b->dtype, b->kernel, b->tile, b->tw, b->th, b->d_runs, b->d_tiles,
-                         b->ntiles, b->grid);
+                         b->ntiles, b->grid, b->iso);
     if (e) return fail(nullptr, MHD_ECUDA, "batch step launch: %s", cudaGetErrorString((cudaError_t)e));
   }
   return MHD_OK;

@@ -286,8 +286,8 @@ int launch_prologue(int dtype, int kernel, int tile, const RunDesc *runs, const 
 }
 
 int launch_substep(int dtype, int kernel, int tile, const RunDesc *runs, const Tile *tiles,
-                   int ntiles, int substep, int grid, cudaStream_t s) {
-  if (kernel == 2) return tma_launch(dtype, tile, runs, tiles, ntiles, substep, grid, s);
+                   int ntiles, int substep, int grid, int iso, cudaStream_t s) {
+  if (kernel == 2) return tma_launch(dtype, tile, runs, tiles, ntiles, substep, grid, iso, s);
   if (dtype == 0) return launch_smem<float, 32, 8>(runs, tiles, ntiles, substep, grid, s);
   return launch_smem<double, 32, 4>(runs, tiles, ntiles, substep, grid, s);
 }

@@ -104,7 +104,7 @@ struct Phase {
   static constexpr int value = V;
 };
 
-template <typename T, int TY, int NS, bool UNROLL7>
+template <typename T, int TY, int NS, bool UNROLL7, bool ISO>
 __global__ void __launch_bounds__(32 * TY, 1)
     k_substep_tma(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles, int ntiles,
                   int substep) {
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(32 * TY, 1)
     const Tile tile = tiles[t];
     const RunDesc &R = runs[tile.run];
     const StepCoeffs &K = *R.coeffs;
-    Coefs<T> c;
+    StencilCoefs<T, ISO> c;
     c.load(R);
     const int nx = R.nx, ny = R.ny, nz = R.nz, px = R.px, py = R.py;
     const long long fs = R.fstride;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(32 * TY, 1)
 #pragma unroll
       for (int s = 1; s <= 3; ++s) {
         // plane p adds +w_s dx_s to output plane p-s and -w_s dx_s to p+s
-        const T mxz = c.cm[1][s], myz = c.cm[2][s];
+        const T mxz = c.wm(1, s), myz = c.wm(2, s);
         const T ux_ = dxs(1, s), uy_ = dys(2, s), uzx = dxs(3, s), uzy = dys(3, s);
         const T Ax_ = dxs(4, s), Ay_ = dys(5, s), Azx = dxs(6, s), Azy = dys(6, s);
         aX1[L(3 - s)] = fma(mxz, uzx, aX1[L(3 - s)]);   // d_x d_z u_z
@@ -255,34 +255,34 @@ __global__ void __launch_bounds__(32 * TY, 1)
         auto D = [&](int f, int sa, int sb) { return o[f * FIELD + sa + sb * SX]; };
         auto Z = [&](int f, int k) { return pen[f][L(k + 3)]; };  // z offset k in -3..3
         auto d1x = [&](int f) {
-          return c.c1[0][1] * (X(f, 1) - X(f, -1)) + c.c1[0][2] * (X(f, 2) - X(f, -2)) +
-                 c.c1[0][3] * (X(f, 3) - X(f, -3));
+          return c.w1(0, 1) * (X(f, 1) - X(f, -1)) + c.w1(0, 2) * (X(f, 2) - X(f, -2)) +
+                 c.w1(0, 3) * (X(f, 3) - X(f, -3));
         };
         auto d1y = [&](int f) {
-          return c.c1[1][1] * (Y(f, 1) - Y(f, -1)) + c.c1[1][2] * (Y(f, 2) - Y(f, -2)) +
-                 c.c1[1][3] * (Y(f, 3) - Y(f, -3));
+          return c.w1(1, 1) * (Y(f, 1) - Y(f, -1)) + c.w1(1, 2) * (Y(f, 2) - Y(f, -2)) +
+                 c.w1(1, 3) * (Y(f, 3) - Y(f, -3));
         };
         auto d1z = [&](int f) {
-          return c.c1[2][1] * (Z(f, 1) - Z(f, -1)) + c.c1[2][2] * (Z(f, 2) - Z(f, -2)) +
-                 c.c1[2][3] * (Z(f, 3) - Z(f, -3));
+          return c.w1(2, 1) * (Z(f, 1) - Z(f, -1)) + c.w1(2, 2) * (Z(f, 2) - Z(f, -2)) +
+                 c.w1(2, 3) * (Z(f, 3) - Z(f, -3));
         };
         auto d2x = [&](int f) {
-          return c.c2[0][0] * Z(f, 0) + c.c2[0][1] * (X(f, 1) + X(f, -1)) +
-                 c.c2[0][2] * (X(f, 2) + X(f, -2)) + c.c2[0][3] * (X(f, 3) + X(f, -3));
+          return c.w2(0, 0) * Z(f, 0) + c.w2(0, 1) * (X(f, 1) + X(f, -1)) +
+                 c.w2(0, 2) * (X(f, 2) + X(f, -2)) + c.w2(0, 3) * (X(f, 3) + X(f, -3));
         };
         auto d2y = [&](int f) {
-          return c.c2[1][0] * Z(f, 0) + c.c2[1][1] * (Y(f, 1) + Y(f, -1)) +
-                 c.c2[1][2] * (Y(f, 2) + Y(f, -2)) + c.c2[1][3] * (Y(f, 3) + Y(f, -3));
+          return c.w2(1, 0) * Z(f, 0) + c.w2(1, 1) * (Y(f, 1) + Y(f, -1)) +
+                 c.w2(1, 2) * (Y(f, 2) + Y(f, -2)) + c.w2(1, 3) * (Y(f, 3) + Y(f, -3));
         };
         auto d2z = [&](int f) {
-          return c.c2[2][0] * Z(f, 0) + c.c2[2][1] * (Z(f, 1) + Z(f, -1)) +
-                 c.c2[2][2] * (Z(f, 2) + Z(f, -2)) + c.c2[2][3] * (Z(f, 3) + Z(f, -3));
+          return c.w2(2, 0) * Z(f, 0) + c.w2(2, 1) * (Z(f, 1) + Z(f, -1)) +
+                 c.w2(2, 2) * (Z(f, 2) + Z(f, -2)) + c.w2(2, 3) * (Z(f, 3) + Z(f, -3));
         };
         auto dxy = [&](int f) {
           T r = T(0);
 #pragma unroll
           for (int s = 1; s <= 3; ++s)
-            r += c.cm[0][s] * ((D(f, s, s) - D(f, -s, s)) - (D(f, s, -s) - D(f, -s, -s)));
+            r += c.wm(0, s) * ((D(f, s, s) - D(f, -s, s)) - (D(f, s, -s) - D(f, -s, -s)));
           return r;
         };
 
@@ -546,22 +546,30 @@ int tma_smem_bytes() {
 
 template <typename T, int TY, int NS, bool U>
 int prepare_tma() {
-  return (int)cudaFuncSetAttribute(k_substep_tma<T, TY, NS, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   tma_smem_bytes<T, TY, NS, U>());
+  int e = (int)cudaFuncSetAttribute(k_substep_tma<T, TY, NS, U, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, tma_smem_bytes<T, TY, NS, U>());
+  if (!e)
+    e = (int)cudaFuncSetAttribute(k_substep_tma<T, TY, NS, U, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tma_smem_bytes<T, TY, NS, U>());
+  return e;
 }
 
 template <typename T, int TY, int NS, bool U>
-int launch_tma(const RunDesc *runs, const Tile *tiles, int ntiles, int substep, int grid, cudaStream_t s) {
+int launch_tma(const RunDesc *runs, const Tile *tiles, int ntiles, int substep, int grid, bool iso,
+               cudaStream_t s) {
   if (grid <= 0 || grid > ntiles) grid = ntiles;
   if (grid == 0) return 0;
-  k_substep_tma<T, TY, NS, U><<<grid, dim3(32, TY), tma_smem_bytes<T, TY, NS, U>(), s>>>(runs, tiles, ntiles,
-                                                                                       substep);
+  const int smem = tma_smem_bytes<T, TY, NS, U>();
+  if (iso)
+    k_substep_tma<T, TY, NS, U, true><<<grid, dim3(32, TY), smem, s>>>(runs, tiles, ntiles, substep);
+  else
+    k_substep_tma<T, TY, NS, U, false><<<grid, dim3(32, TY), smem, s>>>(runs, tiles, ntiles, substep);
   return (int)cudaGetLastError();
 }
 
 template <typename T, int TY, int NS, bool U>
 int occupancy_tma(int *bps) {
-  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_substep_tma<T, TY, NS, U>, 32 * TY,
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_substep_tma<T, TY, NS, U, true>, 32 * TY,
                                                             tma_smem_bytes<T, TY, NS, U>());
 }
 
@@ -637,9 +645,9 @@ int tma_launch_prologue(int dtype, int tile, const RunDesc *runs, const Tile *ti
 }
 
 int tma_launch(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles, int substep, int grid,
-               cudaStream_t s) {
+               int iso, cudaStream_t s) {
 #define X(DT, ID, T, TY, NS, U) \
-  if (dtype == DT && tile == ID) return launch_tma<T, TY, NS, U>(runs, tiles, ntiles, substep, grid, s);
+  if (dtype == DT && tile == ID) return launch_tma<T, TY, NS, U>(runs, tiles, ntiles, substep, grid, iso != 0, s);
   MHD_TMA_VARIANTS(X)
 #undef X
   return (int)cudaErrorInvalidValue;

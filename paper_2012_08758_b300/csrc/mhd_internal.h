@@ -86,8 +86,9 @@ int launch_prologue(int dtype, int kernel, int tile, const RunDesc *runs, const 
                     int tw, int th, cudaStream_t s);
 int launch_prologue_plain(int dtype, const RunDesc *runs, const Tile *tiles, int ntiles, int tw, int th,
                           cudaStream_t s);
+// iso != 0: every run of the launch has equal grid spacings on all axes
 int launch_substep(int dtype, int kernel, int tile, const RunDesc *runs, const Tile *tiles,
-                   int ntiles, int substep, int grid, cudaStream_t s);
+                   int ntiles, int substep, int grid, int iso, cudaStream_t s);
 int prepare_substep(int dtype, int kernel, int tile);
 // TMA variant (kernels_tma.cu); tile ids start at 1
 int tma_num_tiles(int dtype);
@@ -97,7 +98,7 @@ int tma_occupancy(int dtype, int tile, int *bps);
 int tma_launch_prologue(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles,
                         cudaStream_t s);
 int tma_launch(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles, int substep,
-               int grid, cudaStream_t s);
+               int grid, int iso, cudaStream_t s);
 int substep_tile_shape(int dtype, int kernel, int tile, int *tx, int *ty);
 int substep_max_grid(int dtype, int kernel, int tile, int *blocks_per_sm);
 int launch_halo(int dtype, void *fields, int nfields, long long fstride, int nx, int ny, int nz,

@@ -67,10 +67,36 @@ struct Derivs {
                        // cancelled analytically (mu0 = 1)
 };
 
+// Stencil coefficients for the TMA kernel.  ISO: all three grid spacings
+// equal (every configuration of the benchmarks), so the three axes -- and
+// the three mixed pairs -- share one set of 10 weights, which frees
+// registers for more warps per SM.
+template <typename T, bool ISO>
+struct StencilCoefs {
+  static constexpr int NA = ISO ? 1 : 3;
+  T c1[NA][4], c2[NA][4], cm[NA][4];
+  T cs2, nu, eta;
+  __device__ __forceinline__ void load(const RunDesc &R) {
+    const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+    for (int a = 0; a < NA; ++a)
+      for (int s = 0; s < 4; ++s) {
+        c1[a][s] = T(W1(s) * R.inv_h[a]);
+        c2[a][s] = T(W2(s) * R.inv_h[a] * R.inv_h[a]);
+        cm[a][s] = T(WM(s) * R.inv_h[pa[a]] * R.inv_h[pb[a]]);
+      }
+    cs2 = T(R.cs2);
+    nu = T(R.nu);
+    eta = T(R.eta);
+  }
+  __device__ __forceinline__ T w1(int a, int s) const { return c1[ISO ? 0 : a][s]; }
+  __device__ __forceinline__ T w2(int a, int s) const { return c2[ISO ? 0 : a][s]; }
+  __device__ __forceinline__ T wm(int pair, int s) const { return cm[ISO ? 0 : pair][s]; }
+};
+
 // dq/dt of Eqs. 1-3 at one point; f = forcing (already evaluated).
-template <typename T>
-__device__ __forceinline__ void rhs_point(const Derivs<T> &d, const Coefs<T> &c, const T f[3],
-                                          T out[NF]) {
+// C provides cs2, nu, eta in the working precision.
+template <typename T, class C>
+__device__ __forceinline__ void rhs_point(const Derivs<T> &d, const C &c, const T f[3], T out[NF]) {
   const T rho_inv = exp(-d.lnr);
   const T divu = d.G[0][0] + d.G[1][1] + d.G[2][2];
   const T B[3] = {d.gA[2][1] - d.gA[1][2], d.gA[0][2] - d.gA[2][0], d.gA[1][0] - d.gA[0][1]};
