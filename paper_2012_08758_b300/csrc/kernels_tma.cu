@@ -426,6 +426,324 @@ __global__ void __launch_bounds__(32 * TY, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Packed-FP32 variant (FP32, isotropic grid).  Same pipeline and arithmetic as
+// k_substep_tma, but derivatives of two fields that share their stencil
+// weights are computed together with the sm_100-family paired FP32
+// instructions (__ffma2_rn, __fadd2_rn, __fmul2_rn): (u_x, u_y), (A_x, A_y),
+// (u_z, A_z), and cross-axis pairs such as (d_y A_x, d_x A_y) or
+// (d_x ln rho, d_y ln rho), whose weights coincide when h_x = h_y = h_z.
+// Pencils and the x-z / y-z accumulators are kept as pairs too.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+template <int TY, int NS>
+__global__ void __launch_bounds__(32 * TY, 1)
+    k_substep_tma_f2(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles, int ntiles,
+                     int substep) {
+  using T = float;
+  using SH = TmaShape<T, TY>;
+  constexpr int TX = SH::TX, SX = SH::SX, F = SH::FIELD;
+  constexpr int P = NS - 4;
+  static_assert(P >= 1, "need at least one plane of prefetch");
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * SH::STAGE_BYTES);
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * TX + tx;
+  if (tid == 0) {
+    for (int q = 0; q < NS; ++q) mbar_init(&bars[q], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  unsigned long long G = 0;
+  bool failed = false;
+  int fail_run = -1, fail_p = 0, issued_hi = 0;
+
+  for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+    const Tile tile = tiles[t];
+    const RunDesc &R = runs[tile.run];
+    const StepCoeffs &K = *R.coeffs;
+    StencilCoefs<T, true> c;
+    c.load(R);
+    const float2 M1 = pk(-1.f, -1.f);
+    float2 W1[4], W2[4], WMp[4], WMn[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      W1[q] = pk(c.w1(0, q), c.w1(0, q));
+      W2[q] = pk(c.w2(0, q), c.w2(0, q));
+      WMp[q] = pk(c.wm(0, q), c.wm(0, q));
+      WMn[q] = pk(-c.wm(0, q), -c.wm(0, q));
+    }
+    const int nx = R.nx, ny = R.ny, nz = R.nz, px = R.px, py = R.py;
+    const long long fs = R.fstride;
+    const int par = (K.parity + substep) & 1;
+    const CUtensorMap *map = &R.tmap[par];
+    T *__restrict__ qout = static_cast<T *>(R.q[par ^ 1]);
+    T *__restrict__ w = static_cast<T *>(R.w);
+    const T dt = T(K.dt);
+    const T alpha = T(RK_ALPHA(substep)), beta = T(RK_BETA(substep));
+    const int x = tile.x0 + tx, y = tile.y0 + ty;
+    const bool active = x < nx && y < ny;
+    const bool edge_xy = x < RAD || x >= nx - RAD || y < RAD || y >= ny - RAD;
+    const int npl = (tile.z1 - tile.z0) + 2 * RAD;
+
+    const bool forcing = K.forcing != 0;
+    const bool force_in_rhs = forcing && R.forcing_mode == 0;
+    const bool force_at_end = forcing && R.forcing_mode == 1 && substep == 2;
+    Cplx<T> exy = {T(1), T(0)};
+    T fa[3] = {T(0), T(0), T(0)}, fb[3] = {T(0), T(0), T(0)};
+    int mz = 0;
+    if (forcing) {
+      const Cplx<T> *rx = static_cast<const Cplx<T> *>(R.roots[0]);
+      const Cplx<T> *ry = static_cast<const Cplx<T> *>(R.roots[1]);
+      if (active)
+        exy = cmul(rx[(int)(((long long)K.kmod[0] * x) % nx)], ry[(int)(((long long)K.kmod[1] * y) % ny)]);
+      for (int a = 0; a < 3; ++a) {
+        fa[a] = T(K.fa[a]);
+        fb[a] = T(K.fb[a]);
+      }
+      mz = (int)(((long long)K.kmod[2] * tile.z0) % nz);
+    }
+    const int kz = K.kmod[2];
+    const Cplx<T> ephi = {T(K.cphi), T(K.sphi)};
+    const Cplx<T> *rz = static_cast<const Cplx<T> *>(R.roots[2]);
+
+    int slot = (int)(G % NS);
+    uint32_t phase = (uint32_t)((G / NS) & 1ull);
+    auto issue = [&](int p, int sl) {
+      uint64_t *bar = &bars[sl];
+      mbar_arrive_expect_tx(bar, (uint32_t)(NF * F * sizeof(T)));
+      tma_load_4d(smem + sl * SH::STAGE_BYTES, map, bar, tile.x0, tile.y0, tile.z0 + p, 0);
+    };
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      const int first = npl < P ? npl : P;
+      for (int p = 0; p < first; ++p) issue(p, (slot + p) % NS);
+      issued_hi = first;
+    }
+
+    // pencils: pU = (u_x, u_y), pA = (A_x, A_y), pZ = (u_z, A_z), pL = ln rho;
+    // index k holds lead plane p-6+k
+    float2 pU[7], pA[7], pZ[7];
+    float pL[7];
+    // accumulators of output planes p-3 .. p+3:
+    // aU = (d_x d_z u_z, d_y d_z u_z), aA = (d_x d_z A_z, d_y d_z A_z),
+    // zU = d_x d_z u_x + d_y d_z u_y, zA = d_x d_z A_x + d_y d_z A_y
+    float2 aU[7], aA[7];
+    float zU[7], zA[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      pU[k] = pA[k] = pZ[k] = aU[k] = aA[k] = pk(0.f, 0.f);
+      pL[k] = zU[k] = zA[k] = 0.f;
+    }
+    const int cxy = (ty + RAD) * SX + tx + 4;
+    const bool need_w = substep > 0 && active;
+    const long long wplane = (long long)py * px;
+    long long cidx = ((long long)(tile.z0 + OZ) * py + (y + OY)) * px + (x + OX);
+    T wn[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) wn[f] = T(0);
+
+    for (int p = 0; p < npl && !failed; ++p) {
+      if (tid == 0 && p + P < npl) {
+        fence_proxy_async_smem();
+        int sl = slot + P;
+        if (sl >= NS) sl -= NS;
+        issue(p + P, sl);
+        issued_hi = p + P + 1;
+      }
+      T wc[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) wc[f] = wn[f];
+      if (need_w && p >= 2 * RAD - 1 && p + 1 < npl) {
+        const T *wp = w + cidx + (p >= 2 * RAD ? wplane : 0);
+#pragma unroll
+        for (int f = 0; f < NF; ++f, wp += fs) wn[f] = __ldcs(wp);
+      }
+      const bool ok = mbar_wait(&bars[slot], phase);
+      const T *lead = reinterpret_cast<const T *>(smem + slot * SH::STAGE_BYTES) + cxy;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        pU[k] = pU[k + 1];
+        pA[k] = pA[k + 1];
+        pZ[k] = pZ[k + 1];
+        pL[k] = pL[k + 1];
+      }
+      pL[6] = lead[0];
+      pU[6] = pk(lead[1 * F], lead[2 * F]);
+      pZ[6] = pk(lead[3 * F], lead[6 * F]);
+      pA[6] = pk(lead[4 * F], lead[5 * F]);
+#pragma unroll
+      for (int s = 1; s <= 3; ++s) {
+        // (f(+s) - f(-s)) along x for the first lane and along y for the second
+        const float2 dUZ = fma2(pk(lead[3 * F - s], lead[3 * F - s * SX]), M1, pk(lead[3 * F + s], lead[3 * F + s * SX]));
+        const float2 dAZ = fma2(pk(lead[6 * F - s], lead[6 * F - s * SX]), M1, pk(lead[6 * F + s], lead[6 * F + s * SX]));
+        const float2 dUU = fma2(pk(lead[1 * F - s], lead[2 * F - s * SX]), M1, pk(lead[1 * F + s], lead[2 * F + s * SX]));
+        const float2 dAA = fma2(pk(lead[4 * F - s], lead[5 * F - s * SX]), M1, pk(lead[4 * F + s], lead[5 * F + s * SX]));
+        aU[3 - s] = fma2(WMp[s], dUZ, aU[3 - s]);
+        aU[3 + s] = fma2(WMn[s], dUZ, aU[3 + s]);
+        aA[3 - s] = fma2(WMp[s], dAZ, aA[3 - s]);
+        aA[3 + s] = fma2(WMn[s], dAZ, aA[3 + s]);
+        const float su = dUU.x + dUU.y, sa = dAA.x + dAA.y;
+        zU[3 - s] = fmaf(WMp[s].x, su, zU[3 - s]);
+        zU[3 + s] = fmaf(WMn[s].x, su, zU[3 + s]);
+        zA[3 - s] = fmaf(WMp[s].x, sa, zA[3 - s]);
+        zA[3 + s] = fmaf(WMn[s].x, sa, zA[3 + s]);
+      }
+
+      if (p >= 2 * RAD && ok && active) {
+        const int z = tile.z0 + p - 2 * RAD;
+        int oslot = slot - RAD;
+        if (oslot < 0) oslot += NS;
+        const T *o = reinterpret_cast<const T *>(smem + oslot * SH::STAGE_BYTES) + cxy;
+        // paired first derivative from samples g(s), s = +-1..3
+        auto d1p = [&](auto g) {
+          const float2 t1 = fma2(g(-1), M1, g(1));
+          const float2 t2 = fma2(g(-2), M1, g(2));
+          const float2 t3 = fma2(g(-3), M1, g(3));
+          return fma2(W1[3], t3, fma2(W1[2], t2, mul2(W1[1], t1)));
+        };
+        // paired second derivative, centre values c0
+        auto d2p = [&](float2 c0, auto g) {
+          const float2 s1 = add2(g(1), g(-1)), s2 = add2(g(2), g(-2)), s3 = add2(g(3), g(-3));
+          return fma2(W2[3], s3, fma2(W2[2], s2, fma2(W2[1], s1, mul2(W2[0], c0))));
+        };
+        // paired x-y mixed derivative of fields fa (lane 0) and fb (lane 1)
+        auto dxyp = [&](int f0, int f1) {
+          float2 r = pk(0.f, 0.f);
+#pragma unroll
+          for (int q = 1; q <= 3; ++q) {
+            auto D = [&](int sa, int sb) { return pk(o[f0 * F + sa + sb * SX], o[f1 * F + sa + sb * SX]); };
+            const float2 S = add2(fma2(D(-q, q), M1, D(q, q)), fma2(D(q, -q), M1, D(-q, -q)));
+            r = fma2(WMp[q], S, r);
+          }
+          return r;
+        };
+        auto xs = [&](int f0, int f1) { return [=](int q) { return pk(o[f0 * F + q], o[f1 * F + q]); }; };
+        auto ys = [&](int f0, int f1) { return [=](int q) { return pk(o[f0 * F + q * SX], o[f1 * F + q * SX]); }; };
+
+        Derivs<T> d;
+        d.lnr = pL[3];
+        d.u[0] = pU[3].x; d.u[1] = pU[3].y; d.u[2] = pZ[3].x;
+        d.A[0] = pA[3].x; d.A[1] = pA[3].y; d.A[2] = pZ[3].y;
+        const float2 Ux = d1p(xs(1, 2)), Uy = d1p(ys(1, 2)), Uz = d1p([&](int q) { return pU[3 + q]; });
+        const float2 Zx = d1p(xs(3, 6)), Zy = d1p(ys(3, 6));
+        const float2 Az = d1p([&](int q) { return pA[3 + q]; });
+        const float2 Ac = d1p([&](int q) { return pk(o[4 * F + q * SX], o[5 * F + q]); });  // (d_y A_x, d_x A_y)
+        const float2 Lg = d1p([&](int q) { return pk(o[q], o[q * SX]); });                   // (d_x ln rho, d_y ln rho)
+        const float uzz1 = c.w1(0, 1) * (pZ[4].x - pZ[2].x) + c.w1(0, 2) * (pZ[5].x - pZ[1].x) +
+                           c.w1(0, 3) * (pZ[6].x - pZ[0].x);
+        const float lz1 = c.w1(0, 1) * (pL[4] - pL[2]) + c.w1(0, 2) * (pL[5] - pL[1]) + c.w1(0, 3) * (pL[6] - pL[0]);
+        d.g[0] = Lg.x; d.g[1] = Lg.y; d.g[2] = lz1;
+        d.G[0][0] = Ux.x; d.G[0][1] = Uy.x; d.G[0][2] = Uz.x;
+        d.G[1][0] = Ux.y; d.G[1][1] = Uy.y; d.G[1][2] = Uz.y;
+        d.G[2][0] = Zx.x; d.G[2][1] = Zy.x; d.G[2][2] = uzz1;
+        d.gA[0][0] = d.gA[1][1] = d.gA[2][2] = 0.f;  // not used by B = curl A
+        d.gA[0][1] = Ac.x; d.gA[0][2] = Az.x;
+        d.gA[1][0] = Ac.y; d.gA[1][2] = Az.y;
+        d.gA[2][0] = Zx.y; d.gA[2][1] = Zy.y;
+        // second derivatives: lane 0 / lane 1 of each pair
+        const float2 UUx = d2p(pU[3], xs(1, 2)), UUy = d2p(pU[3], ys(1, 2)),
+                     UUz = d2p(pU[3], [&](int q) { return pU[3 + q]; });
+        const float2 AAx = d2p(pA[3], xs(4, 5)), AAy = d2p(pA[3], ys(4, 5)),
+                     AAz = d2p(pA[3], [&](int q) { return pA[3 + q]; });
+        const float2 ZZx = d2p(pZ[3], xs(3, 6)), ZZy = d2p(pZ[3], ys(3, 6)),
+                     ZZz = d2p(pZ[3], [&](int q) { return pZ[3 + q]; });
+        const float2 lapU = add2(add2(UUx, UUy), UUz);  // (lap u_x, lap u_y)
+        const float2 lapA = add2(add2(AAx, AAy), AAz);  // (lap A_x, lap A_y)
+        const float2 lapZ = add2(add2(ZZx, ZZy), ZZz);  // (lap u_z, lap A_z)
+        d.lapu[0] = lapU.x; d.lapu[1] = lapU.y; d.lapu[2] = lapZ.x;
+        d.lapA[0] = lapA.x; d.lapA[1] = lapA.y; d.lapA[2] = lapZ.y;
+        const float2 DU = dxyp(1, 2);  // (d_x d_y u_x, d_x d_y u_y)
+        const float2 DA = dxyp(4, 5);  // (d_x d_y A_x, d_x d_y A_y)
+        d.gdu[0] = UUx.x + DU.y + aU[0].x;
+        d.gdu[1] = DU.x + UUy.y + aU[0].y;
+        d.gdu[2] = zU[0] + ZZz.x;
+        d.jc[0] = DA.y + aA[0].x - AAy.x - AAz.x;
+        d.jc[1] = DA.x + aA[0].y - AAx.y - AAz.y;
+        d.jc[2] = zA[0] - ZZx.y - ZZy.y;
+
+        T fz[3] = {T(0), T(0), T(0)};
+        if (forcing) {
+          const Cplx<T> e = cmul(exy, cmul(rz[mz], ephi));
+#pragma unroll
+          for (int a = 0; a < 3; ++a) fz[a] = fa[a] * e.re - fb[a] * e.im;
+        }
+        const T fr[3] = {force_in_rhs ? fz[0] : T(0), force_in_rhs ? fz[1] : T(0), force_in_rhs ? fz[2] : T(0)};
+        T r[NF];
+        rhs_point(d, c, fr, r);
+        const T qc[NF] = {d.lnr, d.u[0], d.u[1], d.u[2], d.A[0], d.A[1], d.A[2]};
+        T qn[NF];
+        T *wp = w + cidx;
+#pragma unroll
+        for (int fld = 0; fld < NF; ++fld, wp += fs) {
+          T wv = dt * r[fld];
+          if (substep > 0) wv += alpha * wc[fld];
+          if (substep < 2) __stcs(wp, wv);
+          qn[fld] = qc[fld] + beta * wv;
+        }
+        if (force_at_end)
+          for (int a = 0; a < 3; ++a) qn[1 + a] += dt * fz[a];
+        if (!(edge_xy || z < RAD || z >= nz - RAD)) {
+          T *qp = qout + cidx;
+#pragma unroll
+          for (int fld = 0; fld < NF; ++fld, qp += fs) __stcs(qp, qn[fld]);
+        } else {
+          int ix[7], iy[7], iz[7];
+          const int cx = periodic_images(x, nx, ix);
+          const int cy = periodic_images(y, ny, iy);
+          const int cz = periodic_images(z, nz, iz);
+          for (int a = 0; a < cz; ++a)
+            for (int b = 0; b < cy; ++b)
+              for (int e = 0; e < cx; ++e) {
+                const long long oo = ((long long)(iz[a] + OZ) * py + (iy[b] + OY)) * px + (ix[e] + OX);
+#pragma unroll
+                for (int fld = 0; fld < NF; ++fld) __stcs(qout + fld * fs + oo, qn[fld]);
+              }
+        }
+      }
+      if (p >= 2 * RAD) {
+        cidx += wplane;
+        if (forcing) {
+          mz += kz;
+          if (mz >= nz) mz -= nz;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        aU[k] = aU[k + 1];
+        aA[k] = aA[k + 1];
+        zU[k] = zU[k + 1];
+        zA[k] = zA[k + 1];
+      }
+      aU[6] = aA[6] = pk(0.f, 0.f);
+      zU[6] = zA[6] = 0.f;
+      if (++slot == NS) {
+        slot = 0;
+        phase ^= 1u;
+      }
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        fail_run = tile.run;
+        fail_p = p;
+      }
+    }
+    if (!failed) G += npl;
+  }
+
+  if (failed && tid == 0) {
+    atomicOr(&runs[fail_run].clock->status, 2);
+    for (int p = fail_p; p < issued_hi; ++p) {
+      const unsigned long long g = G + p;
+      mbar_wait(&bars[(int)(g % NS)], (uint32_t)((g / NS) & 1ull));
+    }
+  }
+}
+
 // Step prologue over TMA-staged planes: max over the run's points of
 // |u| + sqrt(cs^2 + |B|^2 / rho), B = curl A with the first-derivative
 // stencil (z-derivatives of A_x, A_y from register pencils, x/y derivatives
@@ -578,6 +896,8 @@ int occupancy_tma(int *bps) {
 // Tile variants of the TMA kernel: id -> (dtype, TY, stages, ring rotation
 // by 7-fold unrolling instead of register moves).
 //   FP32: 1 = 32x8/6; 2 = 32x4/6; 3 = 32x8/8; 4 = 32x12/6; 5 = 32x12/5; 6 = 32x16/5
+//   FP32 packed (isotropic grids; anisotropic runs fall back to the tile
+//   of the same shape above): 7 = 32x12/5; 8 = 32x8/6
 //   FP64: 1 = 32x4/6; 2 = 32x4/6 unrolled
 // (the unrolled FP32 variants measured 1.7x slower on B300: the 7-fold body
 // overflows the instruction cache)
@@ -591,7 +911,7 @@ int occupancy_tma(int *bps) {
   X(1, 1, double, 4, 6, false)      \
   X(1, 2, double, 4, 6, true)
 
-int tma_num_tiles(int dtype) { return dtype == 0 ? 6 : 2; }
+int tma_num_tiles(int dtype) { return dtype == 0 ? 8 : 2; }
 
 template <typename T, int TY>
 int pro_smem_bytes() {
@@ -600,8 +920,17 @@ int pro_smem_bytes() {
 
 static_assert(32 * 16 <= MAX_TILE_THREADS, "reduction kernels run with the tile's block shape");
 
+// packed tiles: id -> (scalar tile of the same shape, TY, stages)
+#define MHD_PACKED_VARIANTS(X) \
+  X(7, 5, 12, 5)               \
+  X(8, 1, 8, 6)
+
 int tma_tile_shape(int dtype, int tile, int *tx, int *ty) {
   *tx = 32;
+#define X(ID, SC, TY, NS) \
+  if (dtype == 0 && tile == ID) { *ty = TY; return 0; }
+  MHD_PACKED_VARIANTS(X)
+#undef X
 #define X(DT, ID, T, TY, NS, U) \
   if (dtype == DT && tile == ID) { *ty = TY; return 0; }
   MHD_TMA_VARIANTS(X)
@@ -610,6 +939,14 @@ int tma_tile_shape(int dtype, int tile, int *tx, int *ty) {
 }
 
 int tma_prepare(int dtype, int tile) {
+#define X(ID, SC, TY, NS)                                                                            \
+  if (dtype == 0 && tile == ID) {                                                                    \
+    int e = (int)cudaFuncSetAttribute(k_substep_tma_f2<TY, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                      tma_smem_bytes<float, TY, NS, false>());                       \
+    return e ? e : tma_prepare(0, SC);                                                               \
+  }
+  MHD_PACKED_VARIANTS(X)
+#undef X
 #define X(DT, ID, T, TY, NS, U)                                                                          \
   if (dtype == DT && tile == ID) {                                                                       \
     int e = prepare_tma<T, TY, NS, U>();                                                                 \
@@ -624,6 +961,12 @@ int tma_prepare(int dtype, int tile) {
 }
 
 int tma_occupancy(int dtype, int tile, int *bps) {
+#define X(ID, SC, TY, NS)                                                                                \
+  if (dtype == 0 && tile == ID)                                                                          \
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_substep_tma_f2<TY, NS>, 32 * TY,    \
+                                                              tma_smem_bytes<float, TY, NS, false>());
+  MHD_PACKED_VARIANTS(X)
+#undef X
 #define X(DT, ID, T, TY, NS, U) \
   if (dtype == DT && tile == ID) return occupancy_tma<T, TY, NS, U>(bps);
   MHD_TMA_VARIANTS(X)
@@ -634,6 +977,10 @@ int tma_occupancy(int dtype, int tile, int *bps) {
 int tma_launch_prologue(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles,
                         cudaStream_t s) {
   if (ntiles <= 0) return 0;
+#define X(ID, SC, TY, NS) \
+  if (dtype == 0 && tile == ID) return tma_launch_prologue(0, SC, runs, tiles, ntiles, s);
+  MHD_PACKED_VARIANTS(X)
+#undef X
 #define X(DT, ID, T, TY, NS, U)                                                                       \
   if (dtype == DT && tile == ID) {                                                                    \
     k_prologue_tma<T, TY><<<ntiles, dim3(32, TY), pro_smem_bytes<T, TY>(), s>>>(runs, tiles);         \
@@ -646,6 +993,17 @@ int tma_launch_prologue(int dtype, int tile, const RunDesc *runs, const Tile *ti
 
 int tma_launch(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles, int substep, int grid,
                int iso, cudaStream_t s) {
+#define X(ID, SC, TY, NS)                                                                             \
+  if (dtype == 0 && tile == ID) {                                                                     \
+    if (!iso) return tma_launch(0, SC, runs, tiles, ntiles, substep, grid, iso, s);                   \
+    if (grid <= 0 || grid > ntiles) grid = ntiles;                                                    \
+    if (grid == 0) return 0;                                                                          \
+    k_substep_tma_f2<TY, NS><<<grid, dim3(32, TY), tma_smem_bytes<float, TY, NS, false>(), s>>>(     \
+        runs, tiles, ntiles, substep);                                                                \
+    return (int)cudaGetLastError();                                                                   \
+  }
+  MHD_PACKED_VARIANTS(X)
+#undef X
 #define X(DT, ID, T, TY, NS, U) \
   if (dtype == DT && tile == ID) return launch_tma<T, TY, NS, U>(runs, tiles, ntiles, substep, grid, iso != 0, s);
   MHD_TMA_VARIANTS(X)
