@@ -145,10 +145,8 @@ def cpu_baseline(seconds=12.0, n=64):
 
 
 def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_2012_08758_b300.replicas import env
+    return env()
 
 
 def run_reference(args):
@@ -185,31 +183,26 @@ def run_ours(args):
     n, dtype = args.n, args.dtype
     cells = n ** 3
     run = Run(n=n, device=dev, dtype=B.MHD_F32 if dtype == "f32" else B.MHD_F64, kernel=args.kernel,
-              tile=args.tile, **WORKLOAD)
-    q0 = inputs.seed_field_state(n, seed=rank)
+              tile=args.tile, **dict(WORKLOAD, seed=WORKLOAD["seed"] + rank))
+    from paper_2012_08758_b300.replicas import replica_seed
+    q0 = inputs.seed_field_state(n, seed=replica_seed(0, rank))
     run.set_state(q0)
     run.step(args.warmup)
     run.sync()
 
+    from paper_2012_08758_b300 import replicas as RP
+
     def barrier():
-        torch.cuda.synchronize(dev)
-        if world > 1:
-            torch.distributed.barrier()
+        RP.barrier(dev)
 
     # --- device-timed region: K steps, events on the context's stream ---
     barrier()
     with ClockSampler(local) as clk:
         stage_ms, total_ms = B.mhd_step_timed(run.ctx, args.steps)
     barrier()
-    t_local = total_ms / 1e3
-    if world > 1:
-        t = torch.tensor([t_local], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
+    t_max = RP.max_over_ranks(total_ms / 1e3, dev)
     run.sync()  # raises if the run blew up
-    value = world * cells * args.steps / t_max
+    value = RP.job_throughput(world, cells * args.steps, t_max)
 
     # --- roofline of the dominant kernel (fused substep, 3 launches/step) ---
     sub_ms = sum(stage_ms[1:4])
@@ -239,11 +232,7 @@ def run_ours(args):
         B.mhd_reduce(run.ctx, B.MHD_BRMS)  # one double back per step
     B.mhd_get_state(run.ctx, host_out)
     barrier()
-    e2e_t = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_t = float(t.item())
+    e2e_t = RP.max_over_ranks(time.perf_counter() - t0, dev)
     state_bytes = host_in.nbytes
     e2e = {"value": world * cells * e2e_steps / e2e_t, "unit": UNIT,
            "h2d_bytes_per_step": state_bytes / e2e_steps,
