@@ -124,20 +124,23 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS) k_diag(const RunDesc *__rest
   if (x < R.nx && y < R.ny) {
     for (int z = tile.z0; z < tile.z1; ++z) {
       const long long c = ((long long)(z + OZ) * R.py + (y + OY)) * R.px + (x + OX);
-      const double ux = q[fs + c], uy = q[2 * fs + c], uz = q[3 * fs + c];
-      const double bx = B[c], by = B[fs + c], bz = B[2 * fs + c];
-      const double u2 = ux * ux + uy * uy + uz * uz, b2 = bx * bx + by * by + bz * bz;
-      const double rho = exp((double)q[c]);
-      const double div = (double)(d1_at<T, 0>(B, c, 1, w[0]) + d1_at<T, 1>(B + fs, c, sy, w[1]) +
-                                  d1_at<T, 2>(B + 2 * fs, c, sz, w[2]));
-      su2 += u2;
-      sb2 += b2;
-      sk += rho * u2;
-      sm += rho;
-      mu = fmax(mu, sqrt(u2));
-      mb = fmax(mb, sqrt(b2));
-      mv = fmax(mv, sqrt(u2) + sqrt(cs2 + b2 / rho));
-      md = fmax(md, fabs(div));
+      // per-point values in the working precision (FP64 arithmetic is slow
+      // on B300), accumulated in FP64
+      const T ux = q[fs + c], uy = q[2 * fs + c], uz = q[3 * fs + c];
+      const T bx = B[c], by = B[fs + c], bz = B[2 * fs + c];
+      const T u2 = ux * ux + uy * uy + uz * uz, b2 = bx * bx + by * by + bz * bz;
+      const T rho = exp(q[c]);
+      const T div = d1_at<T, 0>(B, c, 1, w[0]) + d1_at<T, 1>(B + fs, c, sy, w[1]) +
+                    d1_at<T, 2>(B + 2 * fs, c, sz, w[2]);
+      const T umag = sqrt(u2);
+      su2 += (double)u2;
+      sb2 += (double)b2;
+      sk += (double)(rho * u2);
+      sm += (double)rho;
+      mu = fmax(mu, (double)umag);
+      mb = fmax(mb, (double)sqrt(b2));
+      mv = fmax(mv, (double)(umag + sqrt(T(cs2) + b2 / rho)));
+      md = fmax(md, (double)fabs(div));
     }
   }
   const double vals[NPART] = {su2, sb2, sk, sm, mu, mb, mv, md};
