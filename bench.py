@@ -76,6 +76,30 @@ def ncu_traffic(n, dtype):
     return None if ent is None else ent.get("bytes_per_launch")
 
 
+def ncu_flops(dtype):
+    """Floating-point operations per cell-update (three substeps, an FMA
+    counted as 2) executed by the substep kernel, from the committed ncu
+    instruction counts, or None when the kernels changed since."""
+    path = os.path.join(ROOT, "profiles", "substep_flops.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    ent = d.get("dtypes", {}).get(dtype)
+    return None if ent is None else ent.get("flops_per_cell_update")
+
+
+def alu_peaks():
+    """Measured FMA throughput of this GPU (flop/s): FP32 scalar, FP32
+    packed pairs and FP64."""
+    from paper_2012_08758_b300 import binding as B
+    return {"f32": B.mhd_alu_peak(B.MHD_F32)[0], "f32x2": B.mhd_alu_peak(B.MHD_F32X2)[0],
+            "f64": B.mhd_alu_peak(B.MHD_F64)[0]}
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during a region."""
 
@@ -251,9 +275,26 @@ def run_ours(args):
         st64, tot64 = B.mhd_step_timed(run64.ctx, 3)
         run64.close()
         sub64 = sum(st64[1:4])
+        peaks = alu_peaks()
+        fl64 = ncu_flops("f64")
+        alu = {"bound": "alu", "peak": peaks["f64"] / 1e12, "unit": "TFLOP/s",
+               "peak_source": "measured FP64 FMA chains on this GPU (mhd_alu_peak)",
+               "flops_per_cell_update": fl64, "achieved": None, "frac": None}
+        if fl64:
+            alu["achieved"] = fl64 * cells * 3 / (sub64 / 1e3) / 1e12
+            alu["frac"] = alu["achieved"] / alu["peak"]
         fp64 = {"value": cells * 3 / (tot64 / 1e3), "unit": UNIT, "steps": 3,
                 "ms_per_step": tot64 / 3,
-                "hbm_frac": BYTES_PER_CELL["f64"] * cells * 3 / (sub64 / 1e3) / 1e9 / peak}
+                "hbm_frac": BYTES_PER_CELL["f64"] * cells * 3 / (sub64 / 1e3) / 1e9 / peak,
+                "roofline": alu,
+                "fma_peaks_tflops": {k: v / 1e12 for k, v in peaks.items()}}
+        fl32 = ncu_flops("f32")
+        if fl32:
+            roof["alu"] = {"achieved": fl32 * cells * args.steps / (sub_ms / 1e3) / 1e12,
+                           "peak": peaks["f32"] / 1e12, "unit": "TFLOP/s",
+                           "flops_per_cell_update": fl32,
+                           "peak_source": "measured FP32 FMA chains on this GPU (mhd_alu_peak)"}
+            roof["alu"]["frac"] = roof["alu"]["achieved"] / roof["alu"]["peak"]
     run.close()
 
     cb = cpu_baseline() if (rank == 0 and world == 1 and not args.skip_cpu) else None
@@ -393,6 +434,41 @@ def run_serve(args):
     return 0
 
 
+def run_paper_protocol(args):
+    """The paper's timing protocol (App. A): all seven fields uniform in
+    [0, 1), fixed dt = 1.19209e-7, forcing off, 10 warm-up steps, then
+    per-step device times of 100 steps; p50 / p90 and ns per step per
+    point."""
+    import torch
+
+    from paper_2012_08758_b300 import binding as B
+    from paper_2012_08758_b300 import inputs
+    from paper_2012_08758_b300.run import Run
+
+    n = args.n
+    dt = B.MHD_F32 if args.dtype == "f32" else B.MHD_F64
+    run = Run(n=n, dtype=dt, kernel=args.kernel, tile=args.tile,
+              **dict(WORKLOAD, f0=0.0, dt_fixed=1.19209e-7))
+    run.set_state(inputs.uniform_state(n, seed=0, dtype=np.float32 if dt == B.MHD_F32 else np.float64))
+    run.step(10)
+    run.sync()
+    steps = max(args.steps, 100)
+    ms = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(steps):
+            ms.append(B.mhd_step_timed(run.ctx, 1)[1])
+    run.sync()
+    run.close()
+    ms.sort()
+    p50, p90 = ms[len(ms) // 2], ms[int(0.9 * (len(ms) - 1))]
+    line = {"workload": f"{n}^3, all fields U[0,1), dt = 1.19209e-7, forcing off ({args.dtype.upper()}), "
+                        f"10 warm-up + {steps} timed steps",
+            "p50_ms": p50, "p90_ms": p90, "ns_per_step_per_point_p50": p50 * 1e6 / n ** 3,
+            "cell_updates_per_s_p50": n ** 3 / (p50 / 1e3), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_fp32vs64(args):
     """C3: the same initial state advanced in FP32 and in FP64 on the GPU;
     per-quantity FP32 error against FP64 (fields, rms values, energies,
@@ -440,9 +516,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
-    ap.add_argument("--workload", choices=["step", "batch", "serve", "fp32vs64"], default="step",
+    ap.add_argument("--workload", choices=["step", "batch", "serve", "fp32vs64", "paper"], default="step",
                     help="step: the benchmark line; the others measure the batch (16x64^3+8x128^3), "
-                         "serving and FP32-vs-FP64 configurations")
+                         "serving and FP32-vs-FP64 configurations and the paper's timing protocol")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--serve-rate", type=float, default=3.0, help="request arrivals per second")
     ap.add_argument("--serve-scale", type=float, default=0.1, help="scale of the 500-5000 step budgets")
@@ -463,6 +539,8 @@ def main():
         return run_serve(args)
     if args.workload == "fp32vs64":
         return run_fp32vs64(args)
+    if args.workload == "paper":
+        return run_paper_protocol(args)
     return run_ours(args)
 
 

@@ -76,6 +76,7 @@ def lib():
             "mhd_batch_destroy": (None, [vp]),
             "mhd_diagnostics_noalloc": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                                   C.c_double, C.c_double, C.c_double, vp, vp]),
+            "mhd_alu_peak": (C.c_int, [C.c_int, vp, dp, dp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -228,6 +229,18 @@ def mhd_diagnostics_noalloc(state_dev: int, dtype: int, nx: int, ny: int, nz: in
     _check(lib().mhd_diagnostics_noalloc(C.c_void_p(state_dev), int(dtype), int(nx), int(ny), int(nz),
                                          float(lx), float(ly), float(lz), float(cs),
                                          C.c_void_p(out_dev), C.c_void_p(stream or None)))
+
+
+MHD_F32X2 = 2  # mhd_alu_peak: FP32 packed pairs
+
+
+def mhd_alu_peak(dtype: int, stream: int = 0) -> tuple[float, float]:
+    """Measured FMA throughput (flop/s, an FMA counts 2) and the median
+    launch time in ms of the current device for MHD_F32, MHD_F64 or
+    MHD_F32X2; synchronises the stream."""
+    flops, ms = C.c_double(), C.c_double()
+    _check(lib().mhd_alu_peak(int(dtype), C.c_void_p(stream or None), C.byref(flops), C.byref(ms)))
+    return flops.value, ms.value
 
 
 def default_box() -> float:

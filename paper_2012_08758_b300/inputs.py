@@ -25,12 +25,17 @@ def seed_field_state(nx: int, ny: int | None = None, nz: int | None = None,
 
 
 def uniform_state(nx: int, ny: int | None = None, nz: int | None = None,
-                  seed: int = 0, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+                  seed: int = 0, lo: float = 0.0, hi: float = 1.0, dtype=np.float64) -> np.ndarray:
     """All seven fields uniform in [lo, hi): the benchmark state of App. A."""
     ny = nx if ny is None else ny
     nz = nx if nz is None else nz
     rng = np.random.default_rng(seed)
-    return rng.uniform(lo, hi, size=(7, nz, ny, nx))
+    if np.dtype(dtype) == np.float64:
+        return rng.uniform(lo, hi, size=(7, nz, ny, nx))
+    q = rng.random(size=(7, nz, ny, nx), dtype=np.dtype(dtype))
+    q *= np.asarray(hi - lo, dtype=dtype)
+    q += np.asarray(lo, dtype=dtype)
+    return q
 
 
 def random_modes_state(nx: int, ny: int | None = None, nz: int | None = None,

@@ -76,3 +76,12 @@ def test_invalid_parameters_are_rejected(B, bad, msg):
     with pytest.raises(B.MhdError) as e:
         B.mhd_workspace_bytes(B.mhd_default_params(**bad))
     assert e.value.code == B.MHD_EINVAL and msg in str(e.value)
+
+
+def test_alu_peak_rejects_bad_arguments_without_touching_the_gpu(B):
+    """Argument checks of the measurement helper run before any CUDA call."""
+    L = B.lib()
+    import ctypes as C
+    f = C.c_double()
+    assert L.mhd_alu_peak(7, None, C.byref(f), None) == B.MHD_EINVAL
+    assert L.mhd_alu_peak(B.MHD_F32, None, None, None) == B.MHD_EINVAL

@@ -330,6 +330,46 @@ def test_mass_constant_without_flow():
     assert O.diagnostics(p, q)["mass"] == pytest.approx(m0, rel=1e-15)
 
 
+def _mass_rate(n, mixed):
+    """(d/dt sum rho) / sum rho of the semi-discrete continuity equation for a
+    smooth periodic state; the continuum value is the integral of
+    -div(rho u), i.e. zero."""
+    p = O.Params(nx=n, ny=n, nz=n, nu=0.0, eta=0.0)
+    X, Y, Z = coords(n, n, n)
+    q = np.zeros(p.shape)
+    q[0] = 0.3 * np.sin(X + 0.4) * np.cos(Y + Z + 0.2) + 0.2 * np.sin(Z - X + 0.3)
+    q[1] = 0.4 * np.sin(X + 2 * Y + 0.1) * np.cos(Z - 0.7)
+    q[2] = 0.3 * np.cos(X - 0.5) * np.sin(Y + Z + 0.2)
+    q[3] = 0.2 * np.sin(X + Y - Z + 0.9)
+    if mixed:  # modes whose wavenumber along a differentiated axis is 2
+        q[0] += 0.2 * np.sin(2 * Z - X + 0.3) + 0.1 * np.cos(2 * X + Y)
+        q[1] += 0.1 * np.cos(2 * X - Z + 0.5)
+        q[2] += 0.1 * np.sin(2 * Y + X)
+        q[3] += 0.1 * np.cos(2 * Z + 0.1)
+    rho = np.exp(q[0])
+    return (rho * O.rhs(p, q)[0]).sum() / rho.sum()
+
+
+def test_mass_rate_exact_when_every_derivative_sees_one_wavenumber():
+    """Every differentiated field has wavenumber 0 or +-1 along the axis of
+    its derivative, so D1 = c d/dx exactly with one factor c = k1(1) for
+    all three axes; the discrete rate is then c times the trapezoid sum of
+    -div(rho u), which vanishes to rounding for a smooth periodic field."""
+    for n in (12, 24):
+        assert abs(_mass_rate(n, mixed=False)) < 1e-15
+
+
+def test_mass_drift_converges_at_sixth_order():
+    """A ln rho scheme does not conserve sum rho exactly; the rate of mass
+    change is the truncation error of D1 (6th order), so it falls by 2^6
+    when the grid is refined by 2."""
+    r16, r32, r64 = (_mass_rate(n, mixed=True) for n in (16, 32, 64))
+    assert abs(r16) > 1e-8  # not zero: the test sees the truncation error
+    for a, b in ((r16, r32), (r32, r64)):
+        order = math.log2(abs(a / b))
+        assert 5.6 < order < 6.3, order
+
+
 # --------------------------------------------------------------------------
 # Time integration: exact linear decays at the modified wavenumber
 # --------------------------------------------------------------------------
