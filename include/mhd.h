@@ -92,12 +92,17 @@ typedef struct {
   int dtype;                /* mhd_dtype                                     */
   int kernel;               /* MHD_KERNEL_*                                  */
   int tile;                 /* 0: automatic tile choice, else a tile id      */
+  int upwind;               /* 0: central ln rho advection (default); 1: the */
+                            /* high-order upwinding of the continuity        */
+                            /* equation (Sec. 4): per axis the fifth-order   */
+                            /* upwind-biased first derivative, i.e. the      */
+                            /* central one minus |u_a| h_a^5/60 d^6/dx_a^6   */
 } mhd_params;
 
 /* Fills p with the defaults: 32^3, L = 2 pi, cs = 1, nu = eta = 5e-3,
  * no forcing (f0 = 0), shell [2.5, 3.5], sigma = 0, seed = 1, cfl = 0.4,
  * cfl_visc = 0.08, CFL time step, forcing in every substep, FP32, automatic
- * kernel and tile.  p must be non-NULL. */
+ * kernel and tile, no upwinding.  p must be non-NULL. */
 void mhd_default_params(mhd_params *p);
 
 /* Device bytes a context with parameters p needs when the caller supplies

@@ -35,6 +35,12 @@
  *  R6  time step: dt = min(cfl*dmin/max(|u| + sqrt(cs^2 + B^2/rho)),
  *      cfl_visc*dmin^2/max(nu, eta)); dt_fixed > 0 overrides it.
  *  R7  grid points x_i = i*L/N (vertex centred).
+ *  R8  upwinding (Sec. 4 names a high-order upwinding of the continuity
+ *      equation without giving it): with upwind = 1 the advection term
+ *      u . grad ln rho takes, along each axis a, the fifth-order
+ *      upwind-biased first derivative, i.e. the six-point stencil from three
+ *      points upstream to two downstream of the centre, chosen by the sign
+ *      of u_a.  Only the continuity equation is upwinded.
  */
 #include <math.h>
 #include <stdint.h>
@@ -54,6 +60,7 @@ typedef struct {
   uint64_t seed;
   double cfl, cfl_visc, dt_fixed;
   int forcing_mode; /* R4: 0 = in every substep, 1 = once per step */
+  int upwind;       /* R8: 0 = central ln rho advection, 1 = upwind-biased */
 } orc_params;
 
 /* One realisation of the forcing of Sec. 4 Eqs. 4-6 for one step.
@@ -111,6 +118,19 @@ double orc_stencil_d2(const double *line7, double h) {
           2.0 * (f[3] + f[-3])) / (180.0 * h * h);
 }
 
+/* R8: fifth-order upwind-biased first derivative from f(-3..3).  For a
+ * flow towards +axis (direction >= 0) the upstream side is -axis and the
+ * stencil uses f(-3..2); otherwise it is mirrored and uses f(-2..3).  The
+ * weights are the unique ones exact on polynomials of degree <= 5 over
+ * those six points. */
+double orc_stencil_up(const double *line7, double h, int direction) {
+  const double *f = line7 + 3;
+  if (direction >= 0)
+    return (-2.0 * f[-3] + 15.0 * f[-2] - 60.0 * f[-1] + 20.0 * f[0] + 30.0 * f[1] - 3.0 * f[2]) /
+           (60.0 * h);
+  return (3.0 * f[-2] - 30.0 * f[-1] - 20.0 * f[0] + 60.0 * f[1] - 15.0 * f[2] + 2.0 * f[3]) / (60.0 * h);
+}
+
 /* Mixed derivative d2f/(da db) from a 7x7 patch, patch[(sb+3)*7 + (sa+3)]
  * holding f(a + sa*ha, b + sb*hb); only the two diagonals are used:
  * S_s = f(+s,+s) + f(-s,-s) - f(+s,-s) - f(-s,+s). */
@@ -139,6 +159,16 @@ double orc_d1(const orc_params *p, const double *f, int i, int j, int k, int axi
     line[s + 3] = f[at(p, i + di, j + dj, k + dk)];
   }
   return orc_stencil_d1(line, spacing(p, axis));
+}
+
+double orc_dup(const orc_params *p, const double *f, int i, int j, int k, int axis, int direction) {
+  double line[7];
+  for (int s = -3; s <= 3; ++s) {
+    int di, dj, dk;
+    offset(axis, s, &di, &dj, &dk);
+    line[s + 3] = f[at(p, i + di, j + dj, k + dk)];
+  }
+  return orc_stencil_up(line, spacing(p, axis), direction);
 }
 
 double orc_d2(const orc_params *p, const double *f, int i, int j, int k, int axis) {
@@ -318,8 +348,11 @@ void orc_rhs_at(const orc_params *p, const double *q, const orc_forcing *F, int 
   double f[3] = {0.0, 0.0, 0.0};
   if (F && F->amp != 0.0 && p->forcing_mode == 0) orc_forcing_at(p, F, i, j, k, f);
 
-  /* Eq. 1: D ln rho / Dt = -div u */
-  out[0] = -(uu[0] * g[0] + uu[1] * g[1] + uu[2] * g[2]) - divu;
+  /* Eq. 1: D ln rho / Dt = -div u; R8: upwind-biased advection if asked */
+  double adv_lnrho = 0.0;
+  for (int a = 0; a < 3; ++a)
+    adv_lnrho += uu[a] * (p->upwind ? orc_dup(p, lnrho, i, j, k, a, uu[a] >= 0.0 ? 1 : -1) : g[a]);
+  out[0] = -adv_lnrho - divu;
   for (int a = 0; a < 3; ++a) {
     /* Eq. 2: Du/Dt = -cs^2 grad ln rho + j x B / rho
      *         + nu [lap u + grad(div u)/3 + 2 S.grad ln rho] + f */

@@ -50,7 +50,7 @@ class OrcParams(C.Structure):
         ("f0", C.c_double), ("kmin", C.c_double), ("kmax", C.c_double), ("sigma", C.c_double),
         ("seed", C.c_uint64),
         ("cfl", C.c_double), ("cfl_visc", C.c_double), ("dt_fixed", C.c_double),
-        ("forcing_mode", C.c_int),
+        ("forcing_mode", C.c_int), ("upwind", C.c_int),
     ]
 
 
@@ -83,12 +83,13 @@ class Params:
     cfl_visc: float = 0.08
     dt_fixed: float = 0.0
     forcing_mode: int = 0
+    upwind: int = 0
 
     def c(self) -> OrcParams:
         return OrcParams(self.nx, self.ny, self.nz, self.lx, self.ly, self.lz, self.cs,
                          self.nu, self.eta, self.f0, self.kmin, self.kmax, self.sigma,
                          self.seed & 0xFFFFFFFFFFFFFFFF, self.cfl, self.cfl_visc,
-                         self.dt_fixed, self.forcing_mode)
+                         self.dt_fixed, self.forcing_mode, self.upwind)
 
     @property
     def shape(self):
@@ -111,6 +112,10 @@ def lib():
         for name in ("orc_stencil_d1", "orc_stencil_d2"):
             getattr(L, name).argtypes = [dp, C.c_double]
             getattr(L, name).restype = C.c_double
+        L.orc_stencil_up.argtypes = [dp, C.c_double, C.c_int]
+        L.orc_stencil_up.restype = C.c_double
+        L.orc_dup.argtypes = [pp, dp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]
+        L.orc_dup.restype = C.c_double
         L.orc_stencil_dmix.argtypes = [dp, C.c_double, C.c_double]
         L.orc_stencil_dmix.restype = C.c_double
         L.orc_d1.argtypes = [pp, dp, C.c_int, C.c_int, C.c_int, C.c_int]
@@ -166,6 +171,18 @@ def stencil_d1(line7, h):
 def stencil_d2(line7, h):
     a = np.ascontiguousarray(line7, dtype=np.float64)
     return lib().orc_stencil_d2(_dp(a), float(h))
+
+
+def stencil_up(line7, h, direction):
+    """Upwind-biased first derivative (R8): direction >= 0 for a flow
+    towards +axis (uses f(-3..2)), < 0 for the mirror (f(-2..3))."""
+    a = np.ascontiguousarray(line7, dtype=np.float64)
+    return lib().orc_stencil_up(_dp(a), float(h), int(direction))
+
+
+def dup(p: Params, f, axis, direction):
+    """Periodic upwind-biased first derivative of one field along axis."""
+    return _field_op(p, f, lib().orc_dup, axis, direction)
 
 
 def stencil_dmix(patch7x7, ha, hb):

@@ -37,6 +37,7 @@ class MhdParams(C.Structure):
         ("seed", C.c_uint64),
         ("cfl", C.c_double), ("cfl_visc", C.c_double), ("dt_fixed", C.c_double),
         ("forcing_mode", C.c_int), ("dtype", C.c_int), ("kernel", C.c_int), ("tile", C.c_int),
+        ("upwind", C.c_int),
     ]
 
 

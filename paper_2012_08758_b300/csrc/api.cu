@@ -104,6 +104,7 @@ int validate(const mhd_params *p, std::string *why) {
   if (!(p->dt_fixed >= 0)) return bad("dt_fixed must be >= 0");
   if (p->dt_fixed == 0 && !(p->cfl > 0 && p->cfl_visc > 0)) return bad("cfl and cfl_visc must be > 0");
   if (p->forcing_mode != 0 && p->forcing_mode != 1) return bad("forcing_mode must be 0 or 1");
+  if (p->upwind != 0 && p->upwind != 1) return bad("upwind must be 0 or 1");
   if (p->dtype != MHD_F32 && p->dtype != MHD_F64) return bad("dtype must be MHD_F32 or MHD_F64");
   if (p->kernel != MHD_KERNEL_AUTO && p->kernel != MHD_KERNEL_SMEM && p->kernel != MHD_KERNEL_TMA)
     return bad("kernel must be MHD_KERNEL_AUTO, MHD_KERNEL_SMEM or MHD_KERNEL_TMA");
@@ -297,6 +298,7 @@ void mhd_default_params(mhd_params *p) {
   p->cfl_visc = 0.08;
   p->dt_fixed = 0.0;
   p->forcing_mode = 0;
+  p->upwind = 0;
   p->dtype = MHD_F32;
   p->kernel = MHD_KERNEL_AUTO;
   p->tile = 0;
@@ -360,6 +362,7 @@ int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t worksp
   R.kshell = reinterpret_cast<const int *>(ws + L.kshell);
   R.nk = L.nk;
   R.forcing_mode = p->forcing_mode;
+  R.upwind = p->upwind;
   R.clock = reinterpret_cast<Clock *>(ws + L.clock);
   R.coeffs = reinterpret_cast<StepCoeffs *>(ws + L.coeffs);
   R.partials = reinterpret_cast<double *>(ws + L.partials);

@@ -10,6 +10,8 @@
 // finds its halo ready without a separate fill pass.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "mhd_internal.h"
 #include "physics.cuh"
 
@@ -76,6 +78,17 @@ __device__ __forceinline__ void derivs_from_ring(const RingView<T, TX, TY> &S, c
   d.g[0] = S.template d1<0>(0, c);
   d.g[1] = S.template d1<1>(0, c);
   d.g[2] = S.template d1<2>(0, c);
+  d.up = T(0);
+  if (c.upwind) {
+    auto d6 = [&](auto AXc) {
+      constexpr int AX = decltype(AXc)::value;
+      return delta6(S.template nb<AX>(0, -3), S.template nb<AX>(0, -2), S.template nb<AX>(0, -1), d.lnr,
+                    S.template nb<AX>(0, 1), S.template nb<AX>(0, 2), S.template nb<AX>(0, 3));
+    };
+    d.up = c.c6[0] * fabs(d.u[0]) * d6(std::integral_constant<int, 0>{}) +
+           c.c6[1] * fabs(d.u[1]) * d6(std::integral_constant<int, 1>{}) +
+           c.c6[2] * fabs(d.u[2]) * d6(std::integral_constant<int, 2>{});
+  }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     d.G[a][0] = S.template d1<0>(1 + a, c);

@@ -296,6 +296,11 @@ __global__ void __launch_bounds__(32 * TY, 1)
         d.g[0] = d1x(0);
         d.g[1] = d1y(0);
         d.g[2] = d1z(0);
+        d.up = T(0);
+        if (c.upwind)
+          d.up = c.w6(0) * fabs(d.u[0]) * delta6(X(0, -3), X(0, -2), X(0, -1), Z(0, 0), X(0, 1), X(0, 2), X(0, 3)) +
+                 c.w6(1) * fabs(d.u[1]) * delta6(Y(0, -3), Y(0, -2), Y(0, -1), Z(0, 0), Y(0, 1), Y(0, 2), Y(0, 3)) +
+                 c.w6(2) * fabs(d.u[2]) * delta6(Z(0, -3), Z(0, -2), Z(0, -1), Z(0, 0), Z(0, 1), Z(0, 2), Z(0, 3));
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           d.G[a][0] = d1x(1 + a);
@@ -639,6 +644,11 @@ __global__ void __launch_bounds__(32 * TY, 1)
                            c.w1(0, 3) * (pZ[6].x - pZ[0].x);
         const float lz1 = c.w1(0, 1) * (pL[4] - pL[2]) + c.w1(0, 2) * (pL[5] - pL[1]) + c.w1(0, 3) * (pL[6] - pL[0]);
         d.g[0] = Lg.x; d.g[1] = Lg.y; d.g[2] = lz1;
+        d.up = 0.f;
+        if (c.upwind)
+          d.up = c.w6(0) * (fabsf(d.u[0]) * delta6(o[-3], o[-2], o[-1], pL[3], o[1], o[2], o[3]) +
+                            fabsf(d.u[1]) * delta6(o[-3 * SX], o[-2 * SX], o[-SX], pL[3], o[SX], o[2 * SX], o[3 * SX]) +
+                            fabsf(d.u[2]) * delta6(pL[0], pL[1], pL[2], pL[3], pL[4], pL[5], pL[6]));
         d.G[0][0] = Ux.x; d.G[0][1] = Uy.x; d.G[0][2] = Uz.x;
         d.G[1][0] = Ux.y; d.G[1][1] = Uy.y; d.G[1][2] = Uz.y;
         d.G[2][0] = Zx.x; d.G[2][1] = Zy.x; d.G[2][2] = uzz1;

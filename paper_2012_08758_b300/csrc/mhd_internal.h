@@ -63,7 +63,7 @@ struct RunDesc {
   double cfl, cfl_visc, dt_fixed, dmin;
   unsigned long long seed;
   int ntiles;               // reduction tiles of this run
-  int pad;
+  int upwind;               // 1: upwind-biased ln rho advection (Sec. 4)
 };
 
 static_assert(alignof(RunDesc) >= 64 && sizeof(RunDesc) % 64 == 0,

@@ -37,7 +37,9 @@ struct Coefs {
   T c1[3][4];   // first-derivative weights / h, per axis
   T c2[3][4];   // second-derivative weights / h^2, per axis
   T cm[3][4];   // mixed weights / (h_a h_b), index by the pair (xy=0, xz=1, yz=2)
+  T c6[3];      // 1 / (60 h) per axis: weight of the upwinding sixth difference
   T cs2, nu, eta;
+  int upwind;
   __device__ void load(const RunDesc &R) {
     for (int a = 0; a < 3; ++a)
       for (int s = 0; s < 4; ++s) {
@@ -47,9 +49,11 @@ struct Coefs {
     const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
     for (int p = 0; p < 3; ++p)
       for (int s = 0; s < 4; ++s) cm[p][s] = T(WM(s) * R.inv_h[pa[p]] * R.inv_h[pb[p]]);
+    for (int a = 0; a < 3; ++a) c6[a] = T(R.inv_h[a] / 60.0);
     cs2 = T(R.cs2);
     nu = T(R.nu);
     eta = T(R.eta);
+    upwind = R.upwind;
   }
 };
 
@@ -65,7 +69,19 @@ struct Derivs {
   T lapA[3];           // Laplacian of A_a
   T jc[3];             // j = grad div A - lap A with the d_a d_a A_a terms
                        // cancelled analytically (mu0 = 1)
+  T up;                // upwinding term of d ln rho / dt (0 when off)
 };
+
+// Sixth difference f(-3) - 6 f(-2) + 15 f(-1) - 20 f(0) + 15 f(1) - 6 f(2) + f(3)
+// from the samples at offsets -3..3.  The fifth-order upwind-biased first
+// derivative (the six points from three upstream to two downstream) equals
+// the central sixth-order one minus sign(u) * delta6 / (60 h), so
+// u d_up f = u D1 f - |u| delta6 / (60 h): upwinding adds |u_a| delta6_a / (60 h_a)
+// to d ln rho / dt for every axis a.
+template <typename T>
+__device__ __forceinline__ T delta6(T m3, T m2, T m1, T c0, T p1, T p2, T p3) {
+  return ((m3 + p3) - T(6) * (m2 + p2)) + (T(15) * (m1 + p1) - T(20) * c0);
+}
 
 // Stencil coefficients for the TMA kernel.  ISO: all three grid spacings
 // equal (every configuration of the benchmarks), so the three axes -- and
@@ -75,19 +91,25 @@ template <typename T, bool ISO>
 struct StencilCoefs {
   static constexpr int NA = ISO ? 1 : 3;
   T c1[NA][4], c2[NA][4], cm[NA][4];
+  T c6[NA];  // 1 / (60 h): weight of the upwinding sixth difference
   T cs2, nu, eta;
+  int upwind;
   __device__ __forceinline__ void load(const RunDesc &R) {
     const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
-    for (int a = 0; a < NA; ++a)
+    for (int a = 0; a < NA; ++a) {
       for (int s = 0; s < 4; ++s) {
         c1[a][s] = T(W1(s) * R.inv_h[a]);
         c2[a][s] = T(W2(s) * R.inv_h[a] * R.inv_h[a]);
         cm[a][s] = T(WM(s) * R.inv_h[pa[a]] * R.inv_h[pb[a]]);
       }
+      c6[a] = T(R.inv_h[a] / 60.0);
+    }
     cs2 = T(R.cs2);
     nu = T(R.nu);
     eta = T(R.eta);
+    upwind = R.upwind;
   }
+  __device__ __forceinline__ T w6(int a) const { return c6[ISO ? 0 : a]; }
   __device__ __forceinline__ T w1(int a, int s) const { return c1[ISO ? 0 : a][s]; }
   __device__ __forceinline__ T w2(int a, int s) const { return c2[ISO ? 0 : a][s]; }
   __device__ __forceinline__ T wm(int pair, int s) const { return cm[ISO ? 0 : pair][s]; }
@@ -101,7 +123,7 @@ __device__ __forceinline__ void rhs_point(const Derivs<T> &d, const C &c, const 
   const T divu = d.G[0][0] + d.G[1][1] + d.G[2][2];
   const T B[3] = {d.gA[2][1] - d.gA[1][2], d.gA[0][2] - d.gA[2][0], d.gA[1][0] - d.gA[0][1]};
   // Eq. 1: D ln rho / Dt = -div u
-  out[0] = -(d.u[0] * d.g[0] + d.u[1] * d.g[1] + d.u[2] * d.g[2]) - divu;
+  out[0] = -(d.u[0] * d.g[0] + d.u[1] * d.g[1] + d.u[2] * d.g[2]) - divu + d.up;
   const T third = T(1.0 / 3.0);
   const T jxB[3] = {d.jc[1] * B[2] - d.jc[2] * B[1], d.jc[2] * B[0] - d.jc[0] * B[2],
                     d.jc[0] * B[1] - d.jc[1] * B[0]};

@@ -69,7 +69,7 @@ def test_workspace_bytes_scale_with_grid(B):
 @pytest.mark.parametrize("bad,msg", [
     (dict(nx=0), "nx"), (dict(cs=0.0), "cs"), (dict(nu=-1.0), "nu"),
     (dict(f0=0.1, kmin=0.0), "shell"), (dict(f0=0.1, kmin=0.2, kmax=0.5), "no integer"),
-    (dict(f0=0.1, sigma=1.5), "sigma"), (dict(dtype=7), "dtype"), (dict(forcing_mode=3), "forcing_mode"),
+    (dict(f0=0.1, sigma=1.5), "sigma"), (dict(dtype=7), "dtype"), (dict(forcing_mode=3), "forcing_mode"), (dict(upwind=2), "upwind"),
     (dict(cfl=0.0), "cfl"), (dict(kernel=99), "kernel"),
 ])
 def test_invalid_parameters_are_rejected(B, bad, msg):

@@ -140,6 +140,56 @@ def test_every_tma_tile_fp32_step_parity(kernel, tile):
     run.close()
 
 
+# --------------------------------------------------------------------------
+# Upwinding of the continuity equation (upwind = 1)
+# --------------------------------------------------------------------------
+UPWIND_KERNELS = [(2, 0), (1, 0), (2, 1), (2, 7)]
+
+
+@pytest.mark.parametrize("kernel,tile", UPWIND_KERNELS)
+@pytest.mark.parametrize("shape", [(32, 32, 32), (37, 23, 11), (12, 9, 1)])
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_upwinded_rhs_matches_oracle(shape, dtype, tol, kernel, tile):
+    if dtype == "f64" and tile > 2:
+        pytest.skip("packed FP32 tile")
+    nx, ny, nz = shape
+    kw = dict(nx=nx, ny=ny, nz=nz, nu=0.02, eta=0.03, cs=1.1, f0=0.05, sigma=0.7, kmin=1.0,
+              kmax=2.0, seed=5, dtype=dtype, kernel=kernel, tile=tile, upwind=1)
+    # flows of both signs on every axis, and grid-scale structure in ln rho
+    q = inputs.random_modes_state(nx, ny, nz, seed=13, amp=0.4) + inputs.noise_state(nx, ny, nz, seed=14,
+                                                                                     amp=0.05)
+    run = make_run(**kw)
+    run.set_state(q)
+    got = run.eval_rhs(step=3, dt_forcing=0.05)
+    p = oracle_params(**kw)
+    want = O.rhs(p, q, O.forcing_draw(p, 3, dt=0.05))
+    err = rel_linf(got, want, floor=1e-3)
+    assert err.max() < tol, err
+    # the upwinding changed the continuity equation and nothing else
+    central = O.rhs(oracle_params(**dict(kw, upwind=0)), q, O.forcing_draw(p, 3, dt=0.05))
+    assert np.abs(want[0] - central[0]).max() > 100 * tol * np.abs(want[0]).max()
+    assert np.array_equal(want[1:], central[1:])
+    run.close()
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_upwinded_step_parity(dtype, tol):
+    """C1 with upwinding: 32^3, forcing, CFL dt, 10 steps from a state with
+    density and velocity structure."""
+    kw = dict(C1, dtype=dtype, upwind=1)
+    q0 = inputs.random_modes_state(32, 32, 32, seed=21, amp=0.2)
+    run = make_run(**kw)
+    run.set_state(q0)
+    run.step(10)
+    got, t_gpu, _ = run.get_state()
+    q = q0.copy()
+    t_or, _ = O.run(oracle_params(**kw), q, 10)
+    assert abs(t_gpu - t_or) <= (1e-13 if dtype == "f64" else 1e-6) * t_or
+    err = rel_linf_state(got, q, cs=1.0)
+    assert err.max() < tol, err
+    run.close()
+
+
 def test_forcing_once_per_step_mode():
     kw = dict(nx=20, ny=16, nz=12, nu=0.01, eta=0.01, f0=0.05, sigma=0.5, kmin=1.0, kmax=2.0,
               seed=3, forcing_mode=1, dtype="f64")

@@ -41,6 +41,9 @@ MUTANTS = {
     "dt_max_spacing": ("double dmin = fmin(spacing(p, 0),", "double dmin = fmax(spacing(p, 0),"),
     "dt_alfven_rho": ("sqrt(cs2 + B2 / exp(q[c]))", "sqrt(cs2 + B2 * exp(q[c]))"),
     "ekin_density": ("kadd(&sk, rho * u2);", "kadd(&sk, u2);"),
+    "upwind_downstream": ("uu[a] >= 0.0 ? 1 : -1", "uu[a] >= 0.0 ? -1 : 1"),
+    "upwind_weight": ("+ 30.0 * f[1] - 3.0 * f[2]", "+ 30.0 * f[1] - 2.0 * f[2]"),
+    "upwind_ignored": ("p->upwind ? orc_dup", "0 ? orc_dup"),
 }
 
 

@@ -330,6 +330,84 @@ def test_mass_constant_without_flow():
     assert O.diagnostics(p, q)["mass"] == pytest.approx(m0, rel=1e-15)
 
 
+# --------------------------------------------------------------------------
+# Upwinding of the continuity equation (Sec. 4; reading: fifth-order
+# upwind-biased first derivative)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("direction", [1, -1])
+@pytest.mark.parametrize("p", range(0, 8))
+def test_upwind_stencil_polynomial_exactness(direction, p):
+    h, x0 = 0.1, 0.29
+    line = [(x0 + s * h) ** p for s in range(-3, 4)]
+    exact = p * x0 ** (p - 1) if p > 0 else 0.0
+    got = O.stencil_up(line, h, direction)
+    if p <= 5:
+        assert got == pytest.approx(exact, rel=1e-10, abs=1e-10)
+    else:  # order exactly 5
+        assert abs(got - exact) > 1e-8
+
+
+@pytest.mark.parametrize("direction", [1, -1])
+def test_upwind_stencil_ignores_the_far_downstream_point(direction):
+    """Flow towards +axis: the point three downstream (+3) is not used, the
+    point three upstream (-3) is; mirrored for the other direction."""
+    rng = np.random.default_rng(11)
+    line = rng.standard_normal(7)
+    base = O.stencil_up(line, 0.2, direction)
+    far_down, far_up = (6, 0) if direction > 0 else (0, 6)
+    bumped = line.copy()
+    bumped[far_down] += 1.0
+    assert O.stencil_up(bumped, 0.2, direction) == base
+    bumped = line.copy()
+    bumped[far_up] += 1.0
+    assert O.stencil_up(bumped, 0.2, direction) != base
+
+
+def test_upwind_stencil_mirror_symmetry():
+    rng = np.random.default_rng(12)
+    line = rng.standard_normal(7)
+    assert O.stencil_up(line, 0.3, -1) == pytest.approx(-O.stencil_up(line[::-1], 0.3, 1), rel=1e-14)
+
+
+@pytest.mark.parametrize("U", [0.7, -0.4])
+def test_upwinded_advection_of_a_sine_mode(U):
+    """ln rho = eps sin(k x), uniform u_x = U: the upwind-biased derivative of
+    a Fourier mode is the central one plus a damping part, so
+    d ln rho/dt = -U eps k1 cos(kx) - |U| eps (16/(15h)) sin^6(kh/2) sin(kx)
+    (the sixth difference of e^{ikx} is -64 sin^6(kh/2) e^{ikx})."""
+    n, k, eps = 16, 3, 0.01
+    h = 2 * math.pi / n
+    X, Y, Z = coords(n, n, n)
+    q = zero_state(n, n, n)
+    q[0] = eps * np.sin(k * X)
+    q[1] = U
+    p = O.Params(nx=n, ny=n, nz=n, nu=0.0, eta=0.0, upwind=1)
+    r = O.rhs(p, q)
+    damp = 16.0 / (15.0 * h) * math.sin(k * h / 2) ** 6
+    exact = -U * eps * k1_mod(k, h) * np.cos(k * X) - abs(U) * eps * damp * np.sin(k * X)
+    assert np.abs(r[0] - exact).max() < 1e-14
+    p0 = O.Params(nx=n, ny=n, nz=n, nu=0.0, eta=0.0, upwind=0)
+    r0 = O.rhs(p0, q)
+    assert np.abs(r0[0] + U * eps * k1_mod(k, h) * np.cos(k * X)).max() < 1e-14
+    # upwinding touches only the continuity equation
+    assert np.array_equal(r[1:], r0[1:])
+
+
+def test_upwinding_in_every_axis():
+    """The same closed form along y and z with the flow along that axis."""
+    n, k, eps, U = 12, 2, 0.02, 0.5
+    h = 2 * math.pi / n
+    X, Y, Z = coords(n, n, n)
+    damp = 16.0 / (15.0 * h) * math.sin(k * h / 2) ** 6
+    for axis, coord in ((1, Y), (2, Z)):
+        q = zero_state(n, n, n)
+        q[0] = eps * np.sin(k * coord)
+        q[1 + axis] = -U
+        r = O.rhs(O.Params(nx=n, ny=n, nz=n, nu=0.0, eta=0.0, upwind=1), q)
+        exact = U * eps * k1_mod(k, h) * np.cos(k * coord) - U * eps * damp * np.sin(k * coord)
+        assert np.abs(r[0] - exact).max() < 1e-14
+
+
 def _mass_rate(n, mixed):
     """(d/dt sum rho) / sum rho of the semi-discrete continuity equation for a
     smooth periodic state; the continuum value is the integral of
