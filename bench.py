@@ -469,6 +469,41 @@ def run_paper_protocol(args):
     return 0
 
 
+def run_spectrum(args):
+    """Magnetic energy spectrum (Sec. 5) of the n^3 workload state after a
+    few steps: device time of one mhd_spectrum call (curl, cuFFT
+    real-to-complex transform, shell sums, copy of the shells), p50 of 10."""
+    import torch
+
+    from paper_2012_08758_b300 import binding as B
+    from paper_2012_08758_b300 import inputs
+    from paper_2012_08758_b300.run import Run
+
+    n = args.n
+    dt = B.MHD_F32 if args.dtype == "f32" else B.MHD_F64
+    run = Run(n=n, dtype=dt, **WORKLOAD)
+    run.set_state(inputs.seed_field_state(n, seed=0))
+    run.step(args.warmup)
+    E = run.spectrum()
+    emag = run.diagnostics()["emag"]
+    ms = []
+    for _ in range(10):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(run.stream)
+        run.spectrum()
+        e1.record(run.stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    run.close()
+    ms.sort()
+    line = {"workload": f"magnetic spectrum E_B(k) of the {n}^3 workload state ({args.dtype.upper()}), "
+                        f"{len(E)} shells",
+            "p50_ms": ms[len(ms) // 2], "cells_per_s": n ** 3 / (ms[len(ms) // 2] / 1e3),
+            "parseval_rel": abs(E.sum() - emag) / emag, "shells": len(E)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_fp32vs64(args):
     """C3: the same initial state advanced in FP32 and in FP64 on the GPU;
     per-quantity FP32 error against FP64 (fields, rms values, energies,
@@ -516,7 +551,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
-    ap.add_argument("--workload", choices=["step", "batch", "serve", "fp32vs64", "paper"], default="step",
+    ap.add_argument("--workload", choices=["step", "batch", "serve", "fp32vs64", "paper", "spectrum"],
+                    default="step",
                     help="step: the benchmark line; the others measure the batch (16x64^3+8x128^3), "
                          "serving and FP32-vs-FP64 configurations and the paper's timing protocol")
     ap.add_argument("--requests", type=int, default=200)
@@ -541,6 +577,8 @@ def main():
         return run_fp32vs64(args)
     if args.workload == "paper":
         return run_paper_protocol(args)
+    if args.workload == "spectrum":
+        return run_spectrum(args)
     return run_ours(args)
 
 

@@ -180,6 +180,32 @@ int mhd_forcing_draw(mhd_ctx *ctx, int64_t step, double *out);
  * change the state.  Synchronising. */
 int mhd_eval_rhs(mhd_ctx *ctx, int64_t step, double dt_forcing, void *host_rhs, int host_dtype);
 
+/* ---- magnetic energy spectrum (Sec. 5, power spectra) ----------------------
+ * E_B(m) for shells m = 0 .. nshells-1 of the current state:
+ *   B = curl A with the first-derivative stencil (the B of mhd_diagnostics),
+ *   B^(k) = N^-3 sum_x B(x) exp(-i k.x) over the N = nx*ny*nz points, k the
+ *   integer wave vector (units of 2 pi / L),
+ *   E_B(m) = 1/2 sum of |B^(k)|^2 over the k with m - 1/2 <= |k| < m + 1/2,
+ * so sum_m E_B(m) = <|B|^2>/2 = MHD_EMAG (energy per unit volume; the paper's
+ * normalisation, the integral of B^2/2 over the box, is this times lx*ly*lz).
+ * Shell m = 0 is the mean field (zero for a periodic A).  Needs a cubic box
+ * (lx = ly = lz; the grid sizes may differ) and nx >= 2; nshells =
+ * floor(sqrt((nx/2)^2 + (ny/2)^2 + (nz/2)^2) + 1/2) + 1 (integer halves). */
+
+/* Number of shells for parameters p (host only).  Errors: MHD_EINVAL
+ * (invalid parameters, non-cubic box, nx < 2, NULL nshells). */
+int mhd_spectrum_shells(const mhd_params *p, int *nshells);
+
+/* Computes E_B of the current state into host_out[0 .. min(nshells,
+ * max_shells) - 1] (host doubles owned by the caller); *nshells (may be
+ * NULL) receives the shell count.  The transform is cuFFT's real-to-complex
+ * FFT in the context's precision; the shell sums are FP64 in a fixed order
+ * (bitwise reproducible).  Uses the RK register as scratch (free between
+ * steps); the first call makes a cuFFT plan, whose work area cuFFT allocates
+ * and mhd_destroy frees.  Synchronising.  Errors: MHD_EINVAL (NULL
+ * arguments, non-cubic box, nx < 2), MHD_ECUDA (CUDA or cuFFT failure). */
+int mhd_spectrum(mhd_ctx *ctx, double *host_out, int max_shells, int *nshells);
+
 /* Message of the last failure on ctx (or of the calling thread when ctx is
  * NULL); never NULL. */
 const char *mhd_last_error(const mhd_ctx *ctx);

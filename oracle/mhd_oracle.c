@@ -485,6 +485,22 @@ static void kadd(ksum *k, double x) {
 }
 static double kval(const ksum *k) { return k->s + k->c; }
 
+/* B = curl A with the first-derivative stencil at every point:
+ * B[3*n], component-major, x fastest (the B of the diagnostics and of the
+ * magnetic spectrum). */
+void orc_curl(const orc_params *p, const double *q, double *B) {
+  const long n = (long)p->nx * p->ny * p->nz;
+  const double *A[3] = {q + 4 * n, q + 5 * n, q + 6 * n};
+  for (int k = 0; k < p->nz; ++k)
+    for (int j = 0; j < p->ny; ++j)
+      for (int i = 0; i < p->nx; ++i) {
+        const long c = ((long)k * p->ny + j) * p->nx + i;
+        B[c] = orc_d1(p, A[2], i, j, k, 1) - orc_d1(p, A[1], i, j, k, 2);
+        B[n + c] = orc_d1(p, A[0], i, j, k, 2) - orc_d1(p, A[2], i, j, k, 0);
+        B[2 * n + c] = orc_d1(p, A[1], i, j, k, 0) - orc_d1(p, A[0], i, j, k, 1);
+      }
+}
+
 /* out[0..8] = u_rms, B_rms, max|u|, max|B|, E_kin = <rho u^2>/2,
  * E_mag = <B^2>/2, max|div B|, <rho>, max(|u| + sqrt(cs^2 + B^2/rho)). */
 void orc_diagnostics(const orc_params *p, const double *q, double *out) {

@@ -146,6 +146,8 @@ def lib():
         L.orc_step.restype = C.c_double
         L.orc_run.argtypes = [pp, dp, C.c_int64, C.c_int, C.c_double, dp]
         L.orc_run.restype = C.c_double
+        L.orc_curl.argtypes = [pp, dp, dp]
+        L.orc_curl.restype = None
         L.orc_diagnostics.argtypes = [pp, dp, dp]
         L.orc_diagnostics.restype = None
         _lib = L
@@ -323,6 +325,33 @@ def diagnostics(p: Params, q) -> dict:
     out = np.zeros(len(DIAG_NAMES))
     lib().orc_diagnostics(C.byref(p.c()), _dp(q), _dp(out))
     return dict(zip(DIAG_NAMES, out.tolist()))
+
+
+def curl(p: Params, q) -> np.ndarray:
+    """B = curl A with the first-derivative stencil, shape (3, nz, ny, nx)."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    assert q.shape == p.shape
+    B = np.empty((3, p.nz, p.ny, p.nx))
+    lib().orc_curl(C.byref(p.c()), _dp(q), _dp(B))
+    return B
+
+
+def spectrum(p: Params, q) -> np.ndarray:
+    """Magnetic energy spectrum of Sec. 5 (power spectra), per unit volume:
+    E_B(m) = 1/2 sum over integer wave vectors k with m - 1/2 <= |k| < m + 1/2
+    of |B^(k)|^2, B^ = N^-3 * (discrete Fourier transform of B); the sum over
+    m is <B^2>/2.  The library FFT is the primitive; shells m = 0 .. M with
+    M = floor(sqrt((nx//2)^2 + (ny//2)^2 + (nz//2)^2) + 1/2).  Cubic box."""
+    B = curl(p, q)
+    n = p.nx * p.ny * p.nz
+    power = sum(np.abs(np.fft.fftn(B[c])) ** 2 for c in range(3)) / float(n) ** 2
+    kz = np.fft.fftfreq(p.nz, 1.0 / p.nz)
+    ky = np.fft.fftfreq(p.ny, 1.0 / p.ny)
+    kx = np.fft.fftfreq(p.nx, 1.0 / p.nx)
+    K2 = kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2
+    m = np.floor(np.sqrt(K2) + 0.5).astype(np.int64)
+    mmax = int(math.floor(math.sqrt((p.nx // 2) ** 2 + (p.ny // 2) ** 2 + (p.nz // 2) ** 2) + 0.5))
+    return 0.5 * np.bincount(m.ravel(), weights=power.ravel(), minlength=mmax + 1)
 
 
 def growth_rate(t, brms) -> float:

@@ -78,6 +78,8 @@ def lib():
             "mhd_diagnostics_noalloc": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
                                                   C.c_double, C.c_double, C.c_double, vp, vp]),
             "mhd_alu_peak": (C.c_int, [C.c_int, vp, dp, dp]),
+            "mhd_spectrum_shells": (C.c_int, [pp, C.POINTER(C.c_int)]),
+            "mhd_spectrum": (C.c_int, [vp, dp, C.c_int, C.POINTER(C.c_int)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -230,6 +232,22 @@ def mhd_diagnostics_noalloc(state_dev: int, dtype: int, nx: int, ny: int, nz: in
     _check(lib().mhd_diagnostics_noalloc(C.c_void_p(state_dev), int(dtype), int(nx), int(ny), int(nz),
                                          float(lx), float(ly), float(lz), float(cs),
                                          C.c_void_p(out_dev), C.c_void_p(stream or None)))
+
+
+def mhd_spectrum_shells(p: MhdParams) -> int:
+    n = C.c_int()
+    _check(lib().mhd_spectrum_shells(C.byref(p), C.byref(n)))
+    return n.value
+
+
+def mhd_spectrum(ctx: int, max_shells: int) -> np.ndarray:
+    """Magnetic energy spectrum E_B(m), m = 0 .. min(nshells, max_shells)-1
+    (FP64 host array)."""
+    n = C.c_int()
+    out = np.zeros(max(int(max_shells), 1))
+    _check(lib().mhd_spectrum(C.c_void_p(ctx), out.ctypes.data_as(C.POINTER(C.c_double)), int(max_shells),
+                              C.byref(n)), ctx)
+    return out[:min(n.value, int(max_shells))]
 
 
 MHD_F32X2 = 2  # mhd_alu_peak: FP32 packed pairs

@@ -12,6 +12,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 NVCC_FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
               "-Xcompiler", "-fPIC", "-shared"]
+LIBS = ["-lcufft"]  # the FFT of the magnetic spectrum (a plain library transform)
 
 
 def sources():
@@ -35,7 +36,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not stale():
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = ["nvcc", *NVCC_FLAGS, "-I", INCLUDE, "-o", tmp, *sources()]
+    cmd = ["nvcc", *NVCC_FLAGS, "-I", INCLUDE, "-o", tmp, *sources(), *LIBS]
     if verbose:
         print(" ".join(cmd))
     subprocess.check_call(cmd)

@@ -2,6 +2,7 @@
 // device workspace layout, tile tables, step orchestration and batching.
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <cufft.h>
 
 #include <algorithm>
 #include <cmath>
@@ -220,6 +221,8 @@ struct mhd_ctx {
   int grid;  // substep launch grid (persistent CTAs)
   int iso;   // equal grid spacings on all axes
   std::string err;
+  cufftHandle fft = 0;  // spectrum plan, made by the first mhd_spectrum call
+  bool fft_made = false;
 };
 
 struct mhd_batch {
@@ -448,6 +451,7 @@ int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t worksp
 void mhd_destroy(mhd_ctx *ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->fft_made) cufftDestroy(ctx->fft);
   if (ctx->owns_ws) cudaFree(ctx->ws);
   delete ctx;
 }
@@ -612,6 +616,83 @@ int mhd_forcing_draw(mhd_ctx *ctx, int64_t step, double *out) {
   double *scratch = reinterpret_cast<double *>(ctx->ws + ctx->L.scratch);
   CK(ctx, launch_forcing_draw(ctx->d_run, step, scratch, ctx->stream));
   CK(ctx, cudaMemcpyAsync(out, scratch, sizeof(double) * 13, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return MHD_OK;
+}
+
+int mhd_spectrum_shells(const mhd_params *p, int *nshells) {
+  std::string why;
+  if (validate(p, &why)) return fail(nullptr, MHD_EINVAL, "%s", why.c_str());
+  if (!nshells) return fail(nullptr, MHD_EINVAL, "nshells is NULL");
+  if (p->lx != p->ly || p->lx != p->lz) return fail(nullptr, MHD_EINVAL, "spectra need a cubic box (lx = ly = lz)");
+  if (p->nx < 2) return fail(nullptr, MHD_EINVAL, "spectra need nx >= 2");
+  *nshells = spectrum_nshells(p->nx, p->ny, p->nz);
+  return MHD_OK;
+}
+
+int mhd_spectrum(mhd_ctx *ctx, double *host_out, int max_shells, int *nshells) {
+  if (!ctx) return fail(nullptr, MHD_EINVAL, "ctx is NULL");
+  if (!host_out || max_shells < 0) return fail(ctx, MHD_EINVAL, "host_out is NULL or max_shells < 0");
+  const mhd_params &p = ctx->p;
+  if (p.lx != p.ly || p.lx != p.lz) return fail(ctx, MHD_EINVAL, "spectra need a cubic box (lx = ly = lz)");
+  if (p.nx < 2) return fail(ctx, MHD_EINVAL, "spectra need nx >= 2");
+  const RunDesc &R = ctx->h_run;
+  const int ns = spectrum_nshells(R.nx, R.ny, R.nz);
+  if (nshells) *nshells = ns;
+  // scratch: the RK register w, dead between steps (alpha_1 = 0): fields
+  // 0..2 hold B, 3..5 the half spectrum, 6 the shell sums
+  const long long nh = R.nx / 2 + 1, nrows = (long long)R.ny * R.nz, odist = nrows * nh;
+  const size_t esz = ctx->L.esz, fbytes = (size_t)R.fstride * esz;
+  char *w = static_cast<char *>(R.w);
+  void *bh = w + 3 * fbytes;
+  char *scratch = w + 6 * fbytes;
+  if ((size_t)(3 * odist) * 2 * esz > 3 * fbytes || spectrum_scratch_bytes(R.nx, R.ny, R.nz) > fbytes)
+    return fail(ctx, MHD_ENOMEM, "spectrum scratch does not fit the RK register");
+  const size_t rows_bytes = ((size_t)(nrows * nh * 8) + 15) / 16 * 16;
+  double *shells = reinterpret_cast<double *>(scratch + rows_bytes + ((size_t)nrows * 8 + 15) / 16 * 16);
+  if (!ctx->fft_made) {
+    if (cufftCreate(&ctx->fft) != CUFFT_SUCCESS) return fail(ctx, MHD_ECUDA, "cufftCreate failed");
+    // axes of one point are left out of the transform (x, the halved
+    // axis, always stays); inembed gives each kept axis' stride in units of
+    // the next inner kept axis
+    long long n[3], inembed[3], onembed[3];
+    int rank = 0;
+    if (R.nz > 1) {
+      n[rank] = R.nz;
+      inembed[rank] = R.pz;
+      onembed[rank++] = R.nz;
+    }
+    if (R.ny > 1) {
+      n[rank] = R.ny;
+      inembed[rank] = R.py;
+      onembed[rank++] = R.ny;
+    } else if (rank == 1) {
+      inembed[0] = R.pz;  // ignored by cuFFT for the outermost axis
+    }
+    n[rank] = R.nx;
+    inembed[rank] = (R.ny > 1 || rank == 0) ? R.px : (long long)R.py * R.px;
+    onembed[rank++] = nh;
+    size_t work = 0;
+    const cufftResult r = cufftMakePlanMany64(ctx->fft, rank, n, inembed, 1, R.fstride, onembed, 1, odist,
+                                              p.dtype == MHD_F32 ? CUFFT_R2C : CUFFT_D2Z, 3, &work);
+    if (r != CUFFT_SUCCESS) {
+      cufftDestroy(ctx->fft);
+      return fail(ctx, MHD_ECUDA, "cuFFT plan failed (cufftResult %d)", (int)r);
+    }
+    ctx->fft_made = true;
+  }
+  if (cufftSetStream(ctx->fft, ctx->stream) != CUFFT_SUCCESS) return fail(ctx, MHD_ECUDA, "cufftSetStream failed");
+  CK(ctx, launch_curl(p.dtype, ctx->d_run, ctx->d_tiles, ctx->ntiles, ctx->L.tw, ctx->L.th, ctx->stream));
+  const size_t in_off = ((size_t)OZ * R.py + OY) * R.px + OX;  // first interior point (elements)
+  const cufftResult r = p.dtype == MHD_F32
+      ? cufftExecR2C(ctx->fft, reinterpret_cast<cufftReal *>(R.w) + in_off, static_cast<cufftComplex *>(bh))
+      : cufftExecD2Z(ctx->fft, reinterpret_cast<cufftDoubleReal *>(R.w) + in_off,
+                     static_cast<cufftDoubleComplex *>(bh));
+  if (r != CUFFT_SUCCESS) return fail(ctx, MHD_ECUDA, "cuFFT transform failed (cufftResult %d)", (int)r);
+  CK(ctx, launch_spectrum_bins(p.dtype, bh, odist, R.nx, R.ny, R.nz, scratch, shells, ctx->stream));
+  const int ncopy = std::min(ns, max_shells);
+  if (ncopy > 0)
+    CK(ctx, cudaMemcpyAsync(host_out, shells, sizeof(double) * ncopy, cudaMemcpyDeviceToHost, ctx->stream));
   CK(ctx, cudaStreamSynchronize(ctx->stream));
   return MHD_OK;
 }

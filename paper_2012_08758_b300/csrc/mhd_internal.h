@@ -107,6 +107,18 @@ int launch_set_field(int dtype, int host_dtype, const void *src, void *dst_field
                      int nz, int px, int py, cudaStream_t s);
 int launch_get_field(int dtype, int host_dtype, const void *src_field, void *dst, int nx, int ny,
                      int nz, int px, int py, cudaStream_t s);
+// B = curl A of the run's current state into fields 0..2 of its w buffer
+// (interior points only).
+int launch_curl(int dtype, const RunDesc *run_dev, const Tile *tiles, int ntiles, int tw, int th,
+                cudaStream_t s);
+// Magnetic spectrum shells (spectrum.cu): shell count of an nx x ny x nz
+// grid, device scratch bytes of the shell sum, and the shell sum itself from
+// the half-spectrum bh (3 components, odist complex values apart) into
+// shells_out[spectrum_nshells] (device doubles).
+int spectrum_nshells(int nx, int ny, int nz);
+size_t spectrum_scratch_bytes(int nx, int ny, int nz);
+int launch_spectrum_bins(int dtype, const void *bh, long long odist, int nx, int ny, int nz, void *scratch,
+                         double *shells_out, cudaStream_t s);
 int launch_diagnostics(int dtype, const RunDesc *run_dev, const RunDesc &run_host,
                        const Tile *tiles, int ntiles, int tw, int th, cudaStream_t s);
 int launch_coeffs(int dtype, const RunDesc *run, int64_t draw_step, double dt_update,

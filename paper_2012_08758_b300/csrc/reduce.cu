@@ -177,6 +177,15 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS) k_diag(const RunDesc *__rest
   R.counter[1] = 0u;
 }
 
+int launch_curl(int dtype, const RunDesc *run_dev, const Tile *tiles, int ntiles, int tw, int th,
+                cudaStream_t s) {
+  if (dtype == 0)
+    k_curl<float><<<ntiles, dim3(tw, th), 0, s>>>(run_dev, tiles);
+  else
+    k_curl<double><<<ntiles, dim3(tw, th), 0, s>>>(run_dev, tiles);
+  return (int)cudaGetLastError();
+}
+
 int launch_diagnostics(int dtype, const RunDesc *run_dev, const RunDesc &run_host,
                        const Tile *tiles, int ntiles, int tw, int th, cudaStream_t s) {
   int e;

@@ -72,6 +72,10 @@ class Run:
     def diagnostics(self) -> dict:
         return B.mhd_diagnostics(self.ctx)
 
+    def spectrum(self) -> np.ndarray:
+        """Magnetic energy spectrum E_B(m) of the current state (cubic box)."""
+        return B.mhd_spectrum(self.ctx, B.mhd_spectrum_shells(self.params))
+
     def reduce(self, kind: int) -> float:
         return B.mhd_reduce(self.ctx, kind)
 

@@ -85,3 +85,12 @@ def test_alu_peak_rejects_bad_arguments_without_touching_the_gpu(B):
     f = C.c_double()
     assert L.mhd_alu_peak(7, None, C.byref(f), None) == B.MHD_EINVAL
     assert L.mhd_alu_peak(B.MHD_F32, None, None, None) == B.MHD_EINVAL
+
+
+def test_spectrum_shell_count_and_box_checks(B):
+    assert B.mhd_spectrum_shells(B.mhd_default_params(nx=16, ny=16, nz=16)) == 15
+    assert B.mhd_spectrum_shells(B.mhd_default_params(nx=9, ny=7, nz=5)) == 6  # sqrt(16+9+4)=5.39
+    for bad in (dict(lx=1.0), dict(nx=1)):
+        with pytest.raises(B.MhdError) as e:
+            B.mhd_spectrum_shells(B.mhd_default_params(**bad))
+        assert e.value.code == B.MHD_EINVAL

@@ -630,3 +630,74 @@ def test_diagnostics_closed_forms():
 def test_growth_rate_fit_recovers_exponential():
     t = np.linspace(0, 50, 101)
     assert O.growth_rate(t, 1e-5 * np.exp(0.0173 * t)) == pytest.approx(0.0173, rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Magnetic energy spectrum (Sec. 5, power spectra)
+# --------------------------------------------------------------------------
+def test_spectrum_of_one_mode_sits_in_its_shell():
+    """A_z = sin(3x + 0.2): B_y = -k1(3) cos(3x + 0.2) exactly, so all of
+    <B^2>/2 = k1^2/4 lies in shell 3."""
+    n = 16
+    h = 2 * math.pi / n
+    X, Y, Z = coords(n, n, n)
+    q = zero_state(n)
+    q[6] = np.sin(3 * X + 0.2)
+    p = O.Params(nx=n, ny=n, nz=n)
+    E = O.spectrum(p, q)
+    assert len(E) == 15  # floor(sqrt(3 * 8^2) + 1/2) + 1
+    want = k1_mod(3, h) ** 2 / 4
+    assert E[3] == pytest.approx(want, rel=1e-13)
+    assert np.abs(np.delete(E, 3)).max() < 1e-15 * want
+
+
+def test_spectrum_of_a_diagonal_mode():
+    """A_z = sin(3x + 4y): |k| = 5; B_x = k1(4) cos, B_y = -k1(3) cos."""
+    n = 20
+    h = 2 * math.pi / n
+    X, Y, Z = coords(n, n, n)
+    q = zero_state(n)
+    q[6] = np.sin(3 * X + 4 * Y)
+    E = O.spectrum(O.Params(nx=n, ny=n, nz=n), q)
+    want = (k1_mod(3, h) ** 2 + k1_mod(4, h) ** 2) / 4
+    assert E[5] == pytest.approx(want, rel=1e-13)
+    assert np.abs(np.delete(E, 5)).max() < 1e-15 * want
+
+
+@pytest.mark.parametrize("k,shell", [((1, 1, 0), 1), ((1, 1, 1), 2), ((2, 1, 1), 2), ((2, 2, 1), 3),
+                                     ((3, 2, 0), 4), ((4, 4, 2), 6)])
+def test_spectrum_shell_is_the_nearest_integer_of_k(k, shell):
+    """Shell m holds m - 1/2 <= |k| < m + 1/2: sqrt2 -> 1, sqrt3 -> 2,
+    sqrt6 -> 2, 3 -> 3, sqrt13 -> 4, 6 -> 6."""
+    n = 12
+    X, Y, Z = coords(n, n, n)
+    q = zero_state(n)
+    q[4] = np.cos(k[0] * Y + k[1] * Z + k[2] * X + 0.4)  # A_x varying in y, z (and x)
+    E = O.spectrum(O.Params(nx=n, ny=n, nz=n), q)
+    assert E[shell] > 0
+    assert np.abs(np.delete(E, shell)).max() < 1e-14 * E[shell]
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 16), (12, 10, 8), (9, 7, 5)])
+def test_spectrum_sums_to_the_magnetic_energy(shape):
+    """Parseval: sum_m E_B(m) = <B^2>/2, the real-space mean of the
+    diagnostics (compensated sum); shell 0 (mean field) vanishes."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(9)
+    p = O.Params(nx=nx, ny=ny, nz=nz)
+    q = 0.1 * rng.standard_normal(p.shape)
+    E = O.spectrum(p, q)
+    m = int(math.floor(math.sqrt((nx // 2) ** 2 + (ny // 2) ** 2 + (nz // 2) ** 2) + 0.5))
+    assert len(E) == m + 1
+    assert E.sum() == pytest.approx(O.diagnostics(p, q)["emag"], rel=1e-13)
+    assert E[0] < 1e-28 * E.sum()
+
+
+def test_channel_growth_rates_of_exact_exponentials():
+    from paper_2012_08758_b300.growth import channel_growth_rates
+    t = np.linspace(0.0, 3.0, 13)
+    lam = np.array([0.0, 0.3, -0.1, 0.05])
+    S = np.exp(2 * lam[None, :] * t[:, None]) * np.array([1.0, 2e-3, 5.0, 1e-8])
+    got = channel_growth_rates(t, S, channels=[1, 2, 3])
+    for k in (1, 2, 3):
+        assert got[k] == pytest.approx(lam[k], rel=1e-12, abs=1e-13)
