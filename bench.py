@@ -504,6 +504,96 @@ def run_spectrum(args):
     return 0
 
 
+def paper_tables():
+    """Growth rates and Re_M printed in the paper's Tables 1 and 2 (stored
+    with their citation in tests/golden)."""
+    rows = []
+    with open(os.path.join(ROOT, "tests", "golden", "growth_rates_tables_1_2.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            s, n, eta, lam, rem = line.split()
+            rows.append(dict(sigma=float(s), n=int(n), eta=float(eta), lam=float(lam), rem=float(rem)))
+    return rows
+
+
+def shell_mean_k(kmin, kmax):
+    K = int(math.floor(kmax))
+    ks = [math.sqrt(a * a + b * b + c * c) for a in range(-K, K + 1) for b in range(-K, K + 1)
+          for c in range(-K, K + 1) if kmin <= math.sqrt(a * a + b * b + c * c) <= kmax]
+    return sum(ks) / len(ks)
+
+
+def run_tables(args):
+    """Kinematic growth rates at the setup of the paper's Tables 1-2 (Sec. 4:
+    f0 = 0.08, shell 4.5 <= |k| <= 5.5, nu = eta, seed field 1e-5, upwinding
+    on, CFL 0.4), all rows of the chosen grids stepped as one FP32 batch to
+    t = --tables-tmax.  lambda = slope of ln B_rms over t in [100, t_b], t_b the
+    end of the run or the first sample with B_rms > 0.1 u_rms (the field
+    starts to act back); Re_M = <u_rms> over that window / (eta k_f), k_f the
+    mean |k| of the shell."""
+    from paper_2012_08758_b300 import binding as B
+    from paper_2012_08758_b300 import inputs
+    from paper_2012_08758_b300.growth import growth_rate
+    from paper_2012_08758_b300.run import Batch, Run
+
+    grids = [int(g) for g in args.tables_grids.split(",")]
+    rows = [r for r in paper_tables() if r["n"] in grids]
+    kf = shell_mean_k(4.5, 5.5)
+    runs, series, live = [], [], []
+    for i, r in enumerate(rows):
+        run = Run(n=r["n"], nu=r["eta"], eta=r["eta"], f0=0.08, kmin=4.5, kmax=5.5, sigma=r["sigma"],
+                  seed=1000 + i, upwind=1, cfl=0.4)
+        run.set_state(inputs.seed_field_state(r["n"], seed=i, amp=1e-5))
+        d = run.diagnostics()
+        runs.append(run)
+        series.append([(0.0, d["brms"], d["urms"])])
+        live.append(i)
+    status = ["ok"] * len(rows)
+    t0 = time.perf_counter()
+    steps = 0
+    batch = None
+    while live:
+        if batch is None:
+            batch = Batch([runs[i] for i in live])
+        batch.step(args.tables_chunk)
+        steps += args.tables_chunk
+        done = []
+        for i in live:
+            try:
+                d = runs[i].diagnostics()
+            except B.MhdError as e:
+                status[i] = f"failed: {e}"
+                done.append(i)
+                continue
+            t = runs[i].time()[0]
+            series[i].append((t, d["brms"], d["urms"]))
+            if t >= args.tables_tmax:
+                done.append(i)
+        if done:
+            batch.close()
+            batch = None
+            live = [i for i in live if i not in done]
+    wall = time.perf_counter() - t0
+    out = []
+    for i, r in enumerate(rows):
+        runs[i].close()
+        ts, bs, us = (np.array(c) for c in zip(*series[i]))
+        m = ts >= 100.0
+        sat = np.nonzero(m & (bs > 0.1 * us))[0]
+        if len(sat):
+            m &= ts < ts[sat[0]]
+        res = dict(sigma=r["sigma"], n=r["n"], eta=r["eta"], lambda_paper=r["lam"], rem_paper=r["rem"],
+                   status=status[i], t_end=float(ts[-1]))
+        if status[i] == "ok" and m.sum() >= 3:
+            res.update(lambda_=growth_rate(ts[m], bs[m]), rem=float(us[m].mean() / (r["eta"] * kf)),
+                       window=[float(ts[m][0]), float(ts[m][-1])])
+        out.append(res)
+    print(json.dumps({"workload": f"growth rates at the setup of Tables 1-2, grids {grids}, t <= {args.tables_tmax}",
+                      "k_f": kf, "steps": steps, "wall_s": wall, "rows": out}), flush=True)
+    return 0
+
+
 def run_fp32vs64(args):
     """C3: the same initial state advanced in FP32 and in FP64 on the GPU;
     per-quantity FP32 error against FP64 (fields, rms values, energies,
@@ -551,7 +641,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
-    ap.add_argument("--workload", choices=["step", "batch", "serve", "fp32vs64", "paper", "spectrum"],
+    ap.add_argument("--workload", choices=["step", "batch", "serve", "fp32vs64", "paper", "spectrum", "tables"],
                     default="step",
                     help="step: the benchmark line; the others measure the batch (16x64^3+8x128^3), "
                          "serving and FP32-vs-FP64 configurations and the paper's timing protocol")
@@ -560,6 +650,9 @@ def main():
     ap.add_argument("--serve-scale", type=float, default=0.1, help="scale of the 500-5000 step budgets")
     ap.add_argument("--serve-chunk", type=int, default=25)
     ap.add_argument("--serve-checks", type=int, default=6)
+    ap.add_argument("--tables-grids", default="64", help="grids of the Tables 1-2 rows to run")
+    ap.add_argument("--tables-tmax", type=float, default=600.0)
+    ap.add_argument("--tables-chunk", type=int, default=200)
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 plane ring, 2 TMA")
     ap.add_argument("--tile", type=int, default=0, help="tile variant id (0: default)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU-baseline leg")
@@ -579,6 +672,8 @@ def main():
         return run_paper_protocol(args)
     if args.workload == "spectrum":
         return run_spectrum(args)
+    if args.workload == "tables":
+        return run_tables(args)
     return run_ours(args)
 
 

@@ -701,3 +701,17 @@ def test_channel_growth_rates_of_exact_exponentials():
     got = channel_growth_rates(t, S, channels=[1, 2, 3])
     for k in (1, 2, 3):
         assert got[k] == pytest.approx(lam[k], rel=1e-12, abs=1e-13)
+
+
+def test_golden_tables_of_growth_rates_are_complete():
+    """The stored Tables 1-2 (25 helical, 27 non-helical rows): helical
+    growth rates are all positive; non-helical ones change sign between
+    Re_M 17 and 28 (the small-scale dynamo onset the paper reports)."""
+    rows = [line.split() for line in open(os.path.join(GOLDEN, "growth_rates_tables_1_2.txt"))
+            if line.strip() and not line.startswith("#")]
+    hel = [r for r in rows if r[0] == "1"]
+    non = [r for r in rows if r[0] == "0"]
+    assert len(hel) == 25 and len(non) == 27
+    assert all(float(r[3]) > 0 for r in hel)
+    for r in non:
+        assert (float(r[3]) > 0) == (float(r[4]) > 25.0)
