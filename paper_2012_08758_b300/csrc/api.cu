@@ -34,7 +34,8 @@ struct Layout {
   int px, py, pz;
   long long fstride;
   size_t esz;
-  size_t q[2], w, roots[3], kshell, clock, coeffs, partials, counter, diag, scratch, run, tiles;
+  size_t q[2], w, roots[3], kshell, clock, coeffs, partials, counter, diag, scratch, run, tiles, sub_tiles;
+  size_t sub_cap;  // entries reserved for the substep work split
   size_t total;
   int nk;
   int tw, th;
@@ -81,6 +82,82 @@ std::vector<Tile> make_tiles(int nx, int ny, int nz, int tw, int th, int target_
   for (int z0 = 0; z0 < nz; z0 += chunk)
     for (int j = 0; j < nty; ++j)
       for (int i = 0; i < ntx; ++i) t.push_back(Tile{0, i * tw, j * th, z0, std::min(nz, z0 + chunk), slot++});
+  return t;
+}
+
+// ---- work split of the fused substep over the persistent CTAs --------------
+// The substep kernel is persistent (about one CTA per SM) and walks a table
+// of (column, z-range) tiles.  Whole columns keep the z-pipeline long (six
+// halo planes per tile) and let concurrently running CTAs sweep neighbouring
+// columns at the same z (their shared halo rows meet in L2); an equal number
+// of tiles per CTA balances the load.  Both at once: every CTA takes q whole
+// columns (q full waves), and the remaining columns, laid end to end, are cut
+// into equal shares of work, one per CTA.  A column's work per plane is
+// weighted by its active fraction (ragged edge tiles do the TMA and lead-plane
+// work for the full tile but compute fewer points).  The table is laid out
+// round-robin (entry c + G*j = tile j of CTA c), padded with empty tiles.
+constexpr int GMAX = 4 * 148;   // most persistent CTAs of any variant on a B300
+constexpr double MIN_SHARE = 6.0;  // smallest remainder share, in weighted planes
+
+struct SubCol {
+  int run, x0, y0, nz;
+  double w;  // work per plane relative to a full tile
+};
+
+void add_columns(std::vector<SubCol> *cols, int run, int nx, int ny, int nz, int tw, int th) {
+  for (int y0 = 0; y0 < ny; y0 += th)
+    for (int x0 = 0; x0 < nx; x0 += tw) {
+      const double act = (double)std::min(tw, nx - x0) * std::min(th, ny - y0) / ((double)tw * th);
+      cols->push_back(SubCol{run, x0, y0, nz, 0.15 + 0.85 * act});
+    }
+}
+
+std::vector<Tile> split_columns(const std::vector<SubCol> &cols, int G, int *grid_out) {
+  G = std::max(1, G);
+  std::vector<std::vector<Tile>> per(G);
+  // whole-column waves over the full columns of the largest length
+  int nzmax = 0;
+  for (const SubCol &c : cols) nzmax = std::max(nzmax, c.nz);
+  std::vector<size_t> full, rest;
+  for (size_t i = 0; i < cols.size(); ++i) (cols[i].w == 1.0 && cols[i].nz == nzmax ? full : rest).push_back(i);
+  const size_t q = full.size() / G;
+  for (size_t k = 0; k < q * G; ++k) {
+    const SubCol &c = cols[full[k]];
+    per[k % G].push_back(Tile{c.run, c.x0, c.y0, 0, c.nz, 0});
+  }
+  for (size_t k = q * G; k < full.size(); ++k) rest.push_back(full[k]);
+  std::sort(rest.begin(), rest.end());
+  // the rest, end to end, in equal weighted shares
+  double R = 0;
+  for (size_t i : rest) R += cols[i].w * cols[i].nz;
+  const int Gr = rest.empty() ? 0 : (int)std::max(1.0, std::min((double)G, std::floor(R / MIN_SHARE)));
+  auto plane_at = [&](double d, const SubCol &c) {
+    return (int)std::min<long>(c.nz, std::max<long>(0, std::lround(d / c.w)));
+  };
+  size_t ci = 0;
+  double S = 0;  // weighted start of column rest[ci]
+  for (int g = 0; g < Gr; ++g) {
+    const double a = R * g / Gr, b = (g + 1 == Gr) ? R : R * (g + 1) / Gr;
+    while (ci < rest.size() && S + cols[rest[ci]].w * cols[rest[ci]].nz <= a) {
+      S += cols[rest[ci]].w * cols[rest[ci]].nz;
+      ++ci;
+    }
+    double Sj = S;
+    for (size_t cj = ci; cj < rest.size() && Sj < b; ++cj) {
+      const SubCol &c = cols[rest[cj]];
+      const double W = c.w * c.nz;
+      const int z0 = plane_at(std::max(a, Sj) - Sj, c), z1 = plane_at(std::min(b, Sj + W) - Sj, c);
+      if (z1 > z0) per[g].push_back(Tile{c.run, c.x0, c.y0, z0, z1, 0});
+      Sj += W;
+    }
+  }
+  const int used = q > 0 ? G : std::max(Gr, 1);
+  size_t k = 0;
+  for (int g = 0; g < used; ++g) k = std::max(k, per[g].size());
+  std::vector<Tile> t((size_t)used * k, Tile{0, 0, 0, 0, 0, 0});
+  for (int g = 0; g < used; ++g)
+    for (size_t j = 0; j < per[g].size(); ++j) t[g + (size_t)used * j] = per[g][j];
+  *grid_out = used;
   return t;
 }
 
@@ -202,6 +279,9 @@ Layout make_layout(const mhd_params *p_in) {
   L.scratch = take(sizeof(double) * 16);
   L.run = take(sizeof(RunDesc));
   L.tiles = take(sizeof(Tile) * L.tiles_host.size());
+  const size_t ncols = (size_t)((p->nx + L.tw - 1) / L.tw) * ((p->ny + L.th - 1) / L.th);
+  L.sub_cap = ncols + 3 * (size_t)GMAX;
+  L.sub_tiles = take(sizeof(Tile) * L.sub_cap);
   L.total = o;
   return L;
 }
@@ -219,6 +299,8 @@ struct mhd_ctx {
   Tile *d_tiles;
   int ntiles;
   int grid;  // substep launch grid (persistent CTAs)
+  Tile *d_sub;  // substep work split (split_columns) and its grid
+  int nsub, sub_grid;
   int iso;   // equal grid spacings on all axes
   std::string err;
   cufftHandle fft = 0;  // spectrum plan, made by the first mhd_spectrum call
@@ -232,6 +314,8 @@ struct mhd_batch {
   RunDesc *d_runs;
   Tile *d_tiles;
   int ntiles, grid, iso;
+  Tile *d_sub;  // substep work split over all runs' columns
+  int nsub, sub_grid;
   cudaGraphExec_t exec;
   int graph_steps;
 };
@@ -272,10 +356,11 @@ int check_status(mhd_ctx *ctx, const Clock &c) {
 }
 
 int enqueue_step(cudaStream_t s, int dtype, int kernel, int tile, int tw, int th,
-                 const RunDesc *runs, const Tile *tiles, int ntiles, int grid, int iso) {
+                 const RunDesc *runs, const Tile *tiles, int ntiles, const Tile *sub_tiles, int nsub,
+                 int sub_grid, int iso) {
   int e = launch_prologue(dtype, kernel, tile, runs, tiles, ntiles, tw, th, s);
   for (int sub = 0; sub < 3 && e == 0; ++sub)
-    e = launch_substep(dtype, kernel, tile, runs, tiles, ntiles, sub, grid, iso, s);
+    e = launch_substep(dtype, kernel, tile, runs, sub_tiles, nsub, sub, sub_grid, iso, s);
   return e;
 }
 
@@ -406,6 +491,20 @@ int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t worksp
   int bps = 1;
   if (substep_max_grid(p->dtype, p->kernel, p->tile, &bps) != 0 || bps < 1) bps = 1;
   ctx->grid = std::min(ctx->ntiles, bps * num_sms());
+  std::vector<SubCol> cols;
+  add_columns(&cols, 0, p->nx, p->ny, p->nz, L.tw, L.th);
+  int sub_grid = 1;
+  std::vector<Tile> sub_tiles = split_columns(cols, std::min(bps * num_sms(), GMAX), &sub_grid);
+  if (sub_tiles.size() <= L.sub_cap) {
+    ctx->d_sub = reinterpret_cast<Tile *>(ws + L.sub_tiles);
+    ctx->nsub = (int)sub_tiles.size();
+    ctx->sub_grid = sub_grid;
+  } else {  // cannot happen for columns of one run; keep the reduction tiles
+    sub_tiles.clear();
+    ctx->d_sub = ctx->d_tiles;
+    ctx->nsub = ctx->ntiles;
+    ctx->sub_grid = ctx->grid;
+  }
 
   // host tables: roots of unity (FP64 cos/sin, rounded to the working
   // precision), shell list, tiles
@@ -438,6 +537,9 @@ int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t worksp
   if (!e) e = (int)cudaMemcpyAsync(ctx->d_run, &R, sizeof(R), cudaMemcpyHostToDevice, s);
   if (!e)
     e = (int)cudaMemcpyAsync(ctx->d_tiles, L.tiles_host.data(), sizeof(Tile) * L.tiles_host.size(),
+                             cudaMemcpyHostToDevice, s);
+  if (!e && !sub_tiles.empty())
+    e = (int)cudaMemcpyAsync(ctx->d_sub, sub_tiles.data(), sizeof(Tile) * sub_tiles.size(),
                              cudaMemcpyHostToDevice, s);
   if (!e) e = (int)cudaStreamSynchronize(s);
   if (e) {
@@ -513,7 +615,8 @@ int mhd_step(mhd_ctx *ctx, int nsteps) {
   if (nsteps < 0) return fail(ctx, MHD_EINVAL, "nsteps must be >= 0");
   for (int i = 0; i < nsteps; ++i) {
     int e = enqueue_step(ctx->stream, ctx->p.dtype, ctx->p.kernel, ctx->p.tile, ctx->L.tw, ctx->L.th,
-                         ctx->d_run, ctx->d_tiles, ctx->ntiles, ctx->grid, ctx->iso);
+                         ctx->d_run, ctx->d_tiles, ctx->ntiles, ctx->d_sub, ctx->nsub, ctx->sub_grid,
+                         ctx->iso);
     if (e) return cuda_fail(ctx, e, "mhd_step launch");
   }
   return MHD_OK;
@@ -539,8 +642,8 @@ int mhd_step_timed(mhd_ctx *ctx, int nsteps, double *stage_ms, double *total_ms)
                           ctx->L.tw, ctx->L.th, s);
     for (int sub = 0; sub < 3 && !e; ++sub) {
       e = (int)cudaEventRecord(ev[4 * i + 1 + sub], s);
-      if (!e) e = launch_substep(ctx->p.dtype, ctx->p.kernel, ctx->p.tile, ctx->d_run, ctx->d_tiles,
-                                 ctx->ntiles, sub, ctx->grid, ctx->iso, s);
+      if (!e) e = launch_substep(ctx->p.dtype, ctx->p.kernel, ctx->p.tile, ctx->d_run, ctx->d_sub,
+                                 ctx->nsub, sub, ctx->sub_grid, ctx->iso, s);
     }
     if (e) rc = cuda_fail(ctx, e, "mhd_step_timed launch");
   }
@@ -711,8 +814,8 @@ int mhd_eval_rhs(mhd_ctx *ctx, int64_t step, double dt_forcing, void *host_rhs, 
   // substep 0 with dt = 1 leaves w = RHS; the other state buffer is
   // overwritten (it is dead between steps) and serves as staging.
   CK(ctx, launch_coeffs(ctx->p.dtype, ctx->d_run, step, 1.0, dt_forcing, par, s));
-  CK(ctx, launch_substep(ctx->p.dtype, ctx->p.kernel, ctx->p.tile, ctx->d_run, ctx->d_tiles,
-                         ctx->ntiles, 0, ctx->grid, ctx->iso, s));
+  CK(ctx, launch_substep(ctx->p.dtype, ctx->p.kernel, ctx->p.tile, ctx->d_run, ctx->d_sub,
+                         ctx->nsub, 0, ctx->sub_grid, ctx->iso, s));
   const size_t npts = (size_t)R.nx * R.ny * R.nz, hb = npts * host_esz(host_dtype);
   void *staging = R.q[par ^ 1];
   for (int f = 0; f < NF; ++f) {
@@ -790,8 +893,20 @@ int mhd_batch_create(mhd_ctx *const *runs, int nruns, mhd_batch **out) {
   int bps = 1;
   if (substep_max_grid(b->dtype, b->kernel, b->tile, &bps) != 0 || bps < 1) bps = 1;
   b->grid = std::min(b->ntiles, bps * num_sms());
+  std::vector<SubCol> cols;
+  for (int i = 0; i < nruns; ++i)
+    add_columns(&cols, i, runs[i]->p.nx, runs[i]->p.ny, runs[i]->p.nz, runs[i]->L.tw, runs[i]->L.th);
+  std::vector<Tile> sub_tiles = split_columns(cols, std::min(bps * num_sms(), GMAX), &b->sub_grid);
+  b->nsub = (int)sub_tiles.size();
+  b->d_runs = nullptr;
+  b->d_tiles = nullptr;
+  b->d_sub = nullptr;
   cudaError_t e = cudaMalloc(&b->d_runs, sizeof(RunDesc) * descs.size());
   if (e == cudaSuccess) e = cudaMalloc(&b->d_tiles, sizeof(Tile) * tiles.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_sub, sizeof(Tile) * sub_tiles.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_sub, sub_tiles.data(), sizeof(Tile) * sub_tiles.size(), cudaMemcpyHostToDevice,
+                        b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->d_runs, descs.data(), sizeof(RunDesc) * descs.size(), cudaMemcpyHostToDevice,
                         b->stream);
@@ -802,6 +917,7 @@ int mhd_batch_create(mhd_ctx *const *runs, int nruns, mhd_batch **out) {
   if (e != cudaSuccess) {
     cudaFree(b->d_runs);
     cudaFree(b->d_tiles);
+    cudaFree(b->d_sub);
     delete b;
     return fail(nullptr, MHD_ECUDA, "mhd_batch_create: %s", cudaGetErrorString(e));
   }
@@ -823,7 +939,7 @@ int mhd_batch_step(mhd_batch *b, int nsteps) {
     int le = 0;
     for (int i = 0; i < g && e == cudaSuccess && !le; ++i)
       le = enqueue_step(s, b->dtype, b->kernel, b->tile, b->tw, b->th, b->d_runs, b->d_tiles,
-                        b->ntiles, b->grid, b->iso);
+                        b->ntiles, b->d_sub, b->nsub, b->sub_grid, b->iso);
     cudaError_t e2 = cudaStreamEndCapture(s, &graph);
     if (e == cudaSuccess && !le && e2 == cudaSuccess) {
       if (cudaGraphInstantiate(&b->exec, graph, 0) == cudaSuccess) b->graph_steps = g;
@@ -841,7 +957,7 @@ int mhd_batch_step(mhd_batch *b, int nsteps) {
   }
   for (; done < nsteps; ++done) {
     int e = enqueue_step(s, b->dtype, b->kernel, b->tile, b->tw, b->th, b->d_runs, b->d_tiles,
-                         b->ntiles, b->grid, b->iso);
+                         b->ntiles, b->d_sub, b->nsub, b->sub_grid, b->iso);
     if (e) return fail(nullptr, MHD_ECUDA, "batch step launch: %s", cudaGetErrorString((cudaError_t)e));
   }
   return MHD_OK;
@@ -853,6 +969,7 @@ void mhd_batch_destroy(mhd_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   cudaFree(b->d_runs);
   cudaFree(b->d_tiles);
+  cudaFree(b->d_sub);
   delete b;
 }
 

@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(TX *TY)
 
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile tile = tiles[t];
+    if (tile.z1 <= tile.z0) continue;  // padding entry of the work split
     const RunDesc &R = runs[tile.run];
     const StepCoeffs &K = *R.coeffs;
     Coefs<T> c;

@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(32 * TY, 1)
 
   for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
     const Tile tile = tiles[t];
+    if (tile.z1 <= tile.z0) continue;  // padding entry of the work split
     const RunDesc &R = runs[tile.run];
     const StepCoeffs &K = *R.coeffs;
     StencilCoefs<T, ISO> c;
@@ -470,6 +471,7 @@ __global__ void __launch_bounds__(32 * TY, 1)
 
   for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
     const Tile tile = tiles[t];
+    if (tile.z1 <= tile.z0) continue;  // padding entry of the work split
     const RunDesc &R = runs[tile.run];
     const StepCoeffs &K = *R.coeffs;
     StencilCoefs<T, true> c;
