@@ -227,17 +227,8 @@ __global__ void __launch_bounds__(TX *TY)
           }
           if (force_at_end)
             for (int a = 0; a < 3; ++a) qn[1 + a] += dt * f[a];
-          int ix[7], iy[7], iz[7];
-          const int cx = periodic_images(x, nx, ix);
-          const int cy = periodic_images(y, ny, iy);
-          const int cz = periodic_images(z, nz, iz);
-          for (int a = 0; a < cz; ++a)
-            for (int b = 0; b < cy; ++b)
-              for (int e = 0; e < cx; ++e) {
-                const long long o = ((long long)(iz[a] + OZ) * py + (iy[b] + OY)) * px + (ix[e] + OX);
-#pragma unroll
-                for (int fld = 0; fld < NF; ++fld) qout[fld * fs + o] = qn[fld];
-              }
+          const bool near = x < RAD || x >= nx - RAD || y < RAD || y >= ny - RAD || z < RAD || z >= nz - RAD;
+          store_with_images<T, false>(qout, fs, cidx, qn, near, x, y, z, nx, ny, nz, px, py);
         }
       }
       __syncthreads();

@@ -354,24 +354,8 @@ __global__ void __launch_bounds__(32 * TY, 1)
         }
         if (force_at_end)
           for (int a = 0; a < 3; ++a) qn[1 + a] += dt * f[a];
-        if (!(edge_xy || z < RAD || z >= nz - RAD)) {
-          T *qp = qout + cidx;
-#pragma unroll
-          for (int fld = 0; fld < NF; ++fld, qp += fs) __stcs(qp, qn[fld]);
-        } else {
-          // point near a face: also write its periodic images in the ghost zones
-          int ix[7], iy[7], iz[7];
-          const int cx = periodic_images(x, nx, ix);
-          const int cy = periodic_images(y, ny, iy);
-          const int cz = periodic_images(z, nz, iz);
-          for (int a = 0; a < cz; ++a)
-            for (int b = 0; b < cy; ++b)
-              for (int e = 0; e < cx; ++e) {
-                const long long oo = ((long long)(iz[a] + OZ) * py + (iy[b] + OY)) * px + (ix[e] + OX);
-#pragma unroll
-                for (int fld = 0; fld < NF; ++fld) __stcs(qout + fld * fs + oo, qn[fld]);
-              }
-        }
+        store_with_images<T, true>(qout, fs, cidx, qn, edge_xy || z < RAD || z >= nz - RAD, x, y, z, nx, ny, nz,
+                                   px, py);
       }
       if (p >= 2 * RAD) {
         cidx += wplane;
@@ -700,23 +684,8 @@ __global__ void __launch_bounds__(32 * TY, 1)
         }
         if (force_at_end)
           for (int a = 0; a < 3; ++a) qn[1 + a] += dt * fz[a];
-        if (!(edge_xy || z < RAD || z >= nz - RAD)) {
-          T *qp = qout + cidx;
-#pragma unroll
-          for (int fld = 0; fld < NF; ++fld, qp += fs) __stcs(qp, qn[fld]);
-        } else {
-          int ix[7], iy[7], iz[7];
-          const int cx = periodic_images(x, nx, ix);
-          const int cy = periodic_images(y, ny, iy);
-          const int cz = periodic_images(z, nz, iz);
-          for (int a = 0; a < cz; ++a)
-            for (int b = 0; b < cy; ++b)
-              for (int e = 0; e < cx; ++e) {
-                const long long oo = ((long long)(iz[a] + OZ) * py + (iy[b] + OY)) * px + (ix[e] + OX);
-#pragma unroll
-                for (int fld = 0; fld < NF; ++fld) __stcs(qout + fld * fs + oo, qn[fld]);
-              }
-        }
+        store_with_images<T, true>(qout, fs, cidx, qn, edge_xy || z < RAD || z >= nz - RAD, x, y, z, nx, ny, nz,
+                                   px, py);
       }
       if (p >= 2 * RAD) {
         cidx += wplane;

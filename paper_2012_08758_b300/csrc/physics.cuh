@@ -167,4 +167,46 @@ __device__ __forceinline__ int periodic_images(int i, int n, int *out) {
   return c;
 }
 
+// Stores the new values qn of interior point (x, y, z), padded index c, and
+// -- for a point within RAD of a face (near) -- its periodic images in the
+// ghost zones (Sec. 3.1: periodic boundaries as wrapped ghost zones), so the
+// next substep finds its halo filled.  With at least 2 RAD + 1 points on
+// every axis a point has at most one image per axis (i + n below RAD, i - n
+// at or above n - RAD), so the images are the up to seven sums of those
+// shifts; smaller grids take the general enumeration.
+template <typename T, bool STREAM>
+__device__ __forceinline__ void store_with_images(T *qout, long long fs, long long c, const T qn[NF], bool near,
+                                                  int x, int y, int z, int nx, int ny, int nz, int px, int py) {
+  auto put = [&](long long o) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      if (STREAM)
+        __stcs(qout + f * fs + o, qn[f]);
+      else
+        qout[f * fs + o] = qn[f];
+    }
+  };
+  put(c);
+  if (!near) return;
+  if (nx >= 2 * RAD + 1 && ny >= 2 * RAD + 1 && nz >= 2 * RAD + 1) {
+    const long long sy = px, sz = (long long)px * py;
+    const long long dx = x < RAD ? nx : (x >= nx - RAD ? -nx : 0);
+    const long long dy = y < RAD ? ny * sy : (y >= ny - RAD ? -ny * sy : 0);
+    const long long dz = z < RAD ? nz * sz : (z >= nz - RAD ? -nz * sz : 0);
+#pragma unroll
+    for (int m = 1; m < 8; ++m) {
+      if (((m & 1) && dx == 0) || ((m & 2) && dy == 0) || ((m & 4) && dz == 0)) continue;
+      put(c + ((m & 1) ? dx : 0) + ((m & 2) ? dy : 0) + ((m & 4) ? dz : 0));
+    }
+  } else {
+    int ix[7], iy[7], iz[7];
+    const int cx = periodic_images(x, nx, ix);
+    const int cy = periodic_images(y, ny, iy);
+    const int cz = periodic_images(z, nz, iz);
+    for (int a = 0; a < cz; ++a)
+      for (int b = 0; b < cy; ++b)
+        for (int e = 0; e < cx; ++e) put(((long long)(iz[a] + OZ) * py + (iy[b] + OY)) * px + (ix[e] + OX));
+  }
+}
+
 }  // namespace mhd
