@@ -96,6 +96,8 @@ std::vector<Tile> make_tiles(int nx, int ny, int nz, int tw, int th, int target_
 // weighted by its active fraction (ragged edge tiles do the TMA and lead-plane
 // work for the full tile but compute fewer points).  The table is laid out
 // round-robin (entry c + G*j = tile j of CTA c), padded with empty tiles.
+// The weights are a cost model fitted to the measured spread of SM busy
+// times, not a derivation: 0.2 + 0.8 sqrt(active fraction).
 constexpr int GMAX = 4 * 148;   // most persistent CTAs of any variant on a B300
 constexpr double MIN_SHARE = 6.0;  // smallest remainder share, in weighted planes
 
@@ -108,7 +110,9 @@ void add_columns(std::vector<SubCol> *cols, int run, int nx, int ny, int nz, int
   for (int y0 = 0; y0 < ny; y0 += th)
     for (int x0 = 0; x0 < nx; x0 += tw) {
       const double act = (double)std::min(tw, nx - x0) * std::min(th, ny - y0) / ((double)tw * th);
-      cols->push_back(SubCol{run, x0, y0, nz, 0.15 + 0.85 * act});
+      // a partly idle tile still does the TMA and lead-plane work of the full
+      // tile, and its fewer computing warps hide latency worse
+      cols->push_back(SubCol{run, x0, y0, nz, act >= 1.0 ? 1.0 : 0.2 + 0.8 * std::sqrt(act)});
     }
 }
 
