@@ -778,6 +778,10 @@ __global__ void __launch_bounds__(32 * TY, 1)
     T ax[7], ay[7];
 #pragma unroll
     for (int k = 0; k < 7; ++k) ax[k] = ay[k] = T(0);
+    // running maximum in the working precision (exact; FP64 per point would
+    // run on B300's 1/64-rate FP64 pipe), NaN tracked apart
+    T vm = T(0);
+    bool bad = false;
     bool failed = false;
     int p = 0;
     for (; p < npl; ++p) {
@@ -814,14 +818,15 @@ __global__ void __launch_bounds__(32 * TY, 1)
         const T Bz = dx(5) - dy(4);
         const T ux = o[FIELD], uy = o[2 * FIELD], uz = o[3 * FIELD];
         const T v = sqrt(ux * ux + uy * uy + uz * uz) + sqrt(cs2 + (Bx * Bx + By * By + Bz * Bz) * exp(-o[0]));
-        const double vd = (double)v;
-        vmax = (isnan(vd) || isnan(vmax)) ? vd + vmax : fmax(vmax, vd);
+        bad |= isnan(v);
+        vm = fmax(vm, v);
       }
       if (__syncthreads_or(!ok)) {
         failed = true;
         break;
       }
     }
+    vmax = bad ? __longlong_as_double(0x7ff8000000000000ll) : (double)vm;
     if (failed) {
       if (tid == 0) {
         atomicOr(&R.clock->status, 2);

@@ -46,6 +46,11 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS) k_prologue(const RunDesc *__
       for (int s = 0; s < 4; ++s) w[a][s] = T(W1(s) * R.inv_h[a]);
     const T cs2 = T(R.cs2);
     const int x = tile.x0 + threadIdx.x, y = tile.y0 + threadIdx.y;
+    // running maximum in the working precision (a maximum is exact in any
+    // precision; FP64 per point would run on B300's 1/64-rate FP64 pipe),
+    // NaN tracked apart so that a blown-up run still reports NaN
+    T vm = T(0);
+    bool bad = false;
     if (x < R.nx && y < R.ny) {
       const T *Ax = q + 4 * fs, *Ay = q + 5 * fs, *Az = q + 6 * fs;
       for (int z = tile.z0 + (int)blockIdx.y; z < tile.z1; z += PRO_SPLIT) {
@@ -56,10 +61,11 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS) k_prologue(const RunDesc *__
         const T ux = q[fs + c], uy = q[2 * fs + c], uz = q[3 * fs + c];
         const T v = sqrt(ux * ux + uy * uy + uz * uz) +
                     sqrt(cs2 + (Bx * Bx + By * By + Bz * Bz) * exp(-q[c]));
-        const double vd = (double)v;
-        vmax = (isnan(vd) || isnan(vmax)) ? vd + vmax : fmax(vmax, vd);
+        bad |= isnan(v);
+        vm = fmax(vm, v);
       }
     }
+    vmax = bad ? __longlong_as_double(0x7ff8000000000000ll) : (double)vm;
     vmax = block_max(vmax, sh);
   }
   if (threadIdx.x == 0 && threadIdx.y == 0)
@@ -119,13 +125,14 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS) k_diag(const RunDesc *__rest
   for (int a = 0; a < 3; ++a)
     for (int s = 0; s < 4; ++s) w[a][s] = T(W1(s) * R.inv_h[a]);
   const double cs2 = R.cs2;
-  double su2 = 0, sb2 = 0, sk = 0, sm = 0, mu = 0, mb = 0, mv = 0, md = 0;
+  double su2 = 0, sb2 = 0, sk = 0, sm = 0;  // sums: FP64 accumulation
+  T mu = 0, mb = 0, mv = 0, md = 0;         // maxima: exact in any precision
   const int x = tile.x0 + threadIdx.x, y = tile.y0 + threadIdx.y;
   if (x < R.nx && y < R.ny) {
     for (int z = tile.z0; z < tile.z1; ++z) {
       const long long c = ((long long)(z + OZ) * R.py + (y + OY)) * R.px + (x + OX);
-      // per-point values in the working precision (FP64 arithmetic is slow
-      // on B300), accumulated in FP64
+      // per-point values in the working precision (FP64 arithmetic runs at
+      // 1/64 rate on B300), sums accumulated in FP64
       const T ux = q[fs + c], uy = q[2 * fs + c], uz = q[3 * fs + c];
       const T bx = B[c], by = B[fs + c], bz = B[2 * fs + c];
       const T u2 = ux * ux + uy * uy + uz * uz, b2 = bx * bx + by * by + bz * bz;
@@ -137,13 +144,13 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS) k_diag(const RunDesc *__rest
       sb2 += (double)b2;
       sk += (double)(rho * u2);
       sm += (double)rho;
-      mu = fmax(mu, (double)umag);
-      mb = fmax(mb, (double)sqrt(b2));
-      mv = fmax(mv, (double)(umag + sqrt(T(cs2) + b2 / rho)));
-      md = fmax(md, (double)fabs(div));
+      mu = fmax(mu, umag);
+      mb = fmax(mb, sqrt(b2));
+      mv = fmax(mv, umag + sqrt(T(cs2) + b2 / rho));
+      md = fmax(md, fabs(div));
     }
   }
-  const double vals[NPART] = {su2, sb2, sk, sm, mu, mb, mv, md};
+  const double vals[NPART] = {su2, sb2, sk, sm, (double)mu, (double)mb, (double)mv, (double)md};
   double red[NPART];
   for (int i = 0; i < 4; ++i) red[i] = block_sum(vals[i], sh);
   for (int i = 4; i < NPART; ++i) red[i] = block_max(vals[i], sh);
