@@ -96,8 +96,12 @@ std::vector<Tile> make_tiles(int nx, int ny, int nz, int tw, int th, int target_
 // weighted by its active fraction (ragged edge tiles do the TMA and lead-plane
 // work for the full tile but compute fewer points).  The table is laid out
 // round-robin (entry c + G*j = tile j of CTA c), padded with empty tiles.
-// The weights are a cost model fitted to the measured spread of SM busy
-// times, not a derivation: 0.2 + 0.8 sqrt(active fraction).
+// The per-plane weights are a cost model fitted to per-tile clock records of
+// the FP32 32x12 kernel at 256^3 (interior 4260 cycles per plane, tiles at an
+// x face 4864, at a y face 4636, the ragged last row of 4 active rows 3292):
+// the points within RAD of a face also store their periodic images, and a
+// partly idle tile keeps the TMA and lead-plane work of a full one.  Each CTA
+// then receives remainder work up to an equal total load.
 constexpr int GMAX = 4 * 148;   // most persistent CTAs of any variant on a B300
 constexpr double MIN_SHARE = 6.0;  // smallest remainder share, in weighted planes
 
@@ -110,9 +114,11 @@ void add_columns(std::vector<SubCol> *cols, int run, int nx, int ny, int nz, int
   for (int y0 = 0; y0 < ny; y0 += th)
     for (int x0 = 0; x0 < nx; x0 += tw) {
       const double act = (double)std::min(tw, nx - x0) * std::min(th, ny - y0) / ((double)tw * th);
-      // a partly idle tile still does the TMA and lead-plane work of the full
-      // tile, and its fewer computing warps hide latency worse
-      cols->push_back(SubCol{run, x0, y0, nz, act >= 1.0 ? 1.0 : 0.2 + 0.8 * std::sqrt(act)});
+      const bool xface = x0 < RAD || x0 + tw > nx - RAD, yface = y0 < RAD || y0 + th > ny - RAD;
+      double w = act >= 1.0 ? 1.0 : 0.565 + 0.435 * act;
+      if (xface) w *= 1.14;
+      if (yface) w *= 1.09;
+      cols->push_back(SubCol{run, x0, y0, nz, w});
     }
 }
 
@@ -123,25 +129,37 @@ std::vector<Tile> split_columns(const std::vector<SubCol> &cols, int G, int *gri
   int nzmax = 0;
   for (const SubCol &c : cols) nzmax = std::max(nzmax, c.nz);
   std::vector<size_t> full, rest;
-  for (size_t i = 0; i < cols.size(); ++i) (cols[i].w == 1.0 && cols[i].nz == nzmax ? full : rest).push_back(i);
+  for (size_t i = 0; i < cols.size(); ++i) (cols[i].nz == nzmax ? full : rest).push_back(i);
   const size_t q = full.size() / G;
+  std::vector<double> load(G, 0.0);
   for (size_t k = 0; k < q * G; ++k) {
     const SubCol &c = cols[full[k]];
     per[k % G].push_back(Tile{c.run, c.x0, c.y0, 0, c.nz, 0});
+    load[k % G] += c.w * c.nz;
   }
   for (size_t k = q * G; k < full.size(); ++k) rest.push_back(full[k]);
   std::sort(rest.begin(), rest.end());
-  // the rest, end to end, in equal weighted shares
+  // the rest, end to end: CTA g takes a contiguous share budget[g] that
+  // tops its load up to the common total (equal shares when q == 0)
   double R = 0;
   for (size_t i : rest) R += cols[i].w * cols[i].nz;
   const int Gr = rest.empty() ? 0 : (int)std::max(1.0, std::min((double)G, std::floor(R / MIN_SHARE)));
+  std::vector<double> budget(Gr, Gr ? R / Gr : 0.0);
+  if (q > 0 && Gr == G) {
+    double tot = R;
+    for (double l : load) tot += l;
+    double bsum = 0;
+    for (int g = 0; g < G; ++g) bsum += (budget[g] = std::max(0.0, tot / G - load[g]));
+    for (int g = 0; g < G; ++g) budget[g] = bsum > 0 ? budget[g] * R / bsum : R / G;
+  }
   auto plane_at = [&](double d, const SubCol &c) {
     return (int)std::min<long>(c.nz, std::max<long>(0, std::lround(d / c.w)));
   };
   size_t ci = 0;
   double S = 0;  // weighted start of column rest[ci]
+  double a = 0;
   for (int g = 0; g < Gr; ++g) {
-    const double a = R * g / Gr, b = (g + 1 == Gr) ? R : R * (g + 1) / Gr;
+    const double b = (g + 1 == Gr) ? R : a + budget[g];
     while (ci < rest.size() && S + cols[rest[ci]].w * cols[rest[ci]].nz <= a) {
       S += cols[rest[ci]].w * cols[rest[ci]].nz;
       ++ci;
@@ -154,6 +172,7 @@ std::vector<Tile> split_columns(const std::vector<SubCol> &cols, int G, int *gri
       if (z1 > z0) per[g].push_back(Tile{c.run, c.x0, c.y0, z0, z1, 0});
       Sj += W;
     }
+    a = b;
   }
   const int used = q > 0 ? G : std::max(Gr, 1);
   size_t k = 0;
