@@ -178,12 +178,13 @@ template <typename T, bool STREAM>
 __device__ __forceinline__ void store_with_images(T *qout, long long fs, long long c, const T qn[NF], bool near,
                                                   int x, int y, int z, int nx, int ny, int nz, int px, int py) {
   auto put = [&](long long o) {
+    T *p = qout + o;
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
+    for (int f = 0; f < NF; ++f, p += fs) {
       if (STREAM)
-        __stcs(qout + f * fs + o, qn[f]);
+        __stcs(p, qn[f]);
       else
-        qout[f * fs + o] = qn[f];
+        *p = qn[f];
     }
   };
   put(c);
@@ -193,11 +194,12 @@ __device__ __forceinline__ void store_with_images(T *qout, long long fs, long lo
     const long long dx = x < RAD ? nx : (x >= nx - RAD ? -nx : 0);
     const long long dy = y < RAD ? ny * sy : (y >= ny - RAD ? -ny * sy : 0);
     const long long dz = z < RAD ? nz * sz : (z >= nz - RAD ? -nz * sz : 0);
-#pragma unroll
-    for (int m = 1; m < 8; ++m) {
-      if (((m & 1) && dx == 0) || ((m & 2) && dy == 0) || ((m & 4) && dz == 0)) continue;
+    // the images are the non-empty subsets of the non-zero shifts; a
+    // rolled loop over those subsets issues only the stores that exist
+    const int mask = (dx != 0 ? 1 : 0) | (dy != 0 ? 2 : 0) | (dz != 0 ? 4 : 0);
+#pragma unroll 1
+    for (int m = mask; m != 0; m = (m - 1) & mask)
       put(c + ((m & 1) ? dx : 0) + ((m & 2) ? dy : 0) + ((m & 4) ? dz : 0));
-    }
   } else {
     int ix[7], iy[7], iz[7];
     const int cx = periodic_images(x, nx, ix);
