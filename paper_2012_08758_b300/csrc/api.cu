@@ -97,8 +97,8 @@ std::vector<Tile> make_tiles(int nx, int ny, int nz, int tw, int th, int target_
 // work for the full tile but compute fewer points).  The table is laid out
 // round-robin (entry c + G*j = tile j of CTA c), padded with empty tiles.
 // The per-plane weights are a cost model fitted to per-tile clock records of
-// the FP32 32x12 kernel at 256^3 (interior 4260 cycles per plane, tiles at an
-// x face 4864, at a y face 4636, the ragged last row of 4 active rows 3292):
+// the FP32 32x12 kernel at 256^3 (interior 4220 cycles per plane, tiles at an
+// x face 4650, at a y face 4426, the ragged last row of 4 active rows 3175):
 // the points within RAD of a face also store their periodic images, and a
 // partly idle tile keeps the TMA and lead-plane work of a full one.  Each CTA
 // then receives remainder work up to an equal total load.
@@ -116,8 +116,8 @@ void add_columns(std::vector<SubCol> *cols, int run, int nx, int ny, int nz, int
       const double act = (double)std::min(tw, nx - x0) * std::min(th, ny - y0) / ((double)tw * th);
       const bool xface = x0 < RAD || x0 + tw > nx - RAD, yface = y0 < RAD || y0 + th > ny - RAD;
       double w = act >= 1.0 ? 1.0 : 0.565 + 0.435 * act;
-      if (xface) w *= 1.14;
-      if (yface) w *= 1.09;
+      if (xface) w *= 1.10;
+      if (yface) w *= 1.05;
       cols->push_back(SubCol{run, x0, y0, nz, w});
     }
 }

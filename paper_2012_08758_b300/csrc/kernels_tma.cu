@@ -727,9 +727,12 @@ __global__ void __launch_bounds__(32 * TY, 1)
 
 // Step prologue over TMA-staged planes: max over the run's points of
 // |u| + sqrt(cs^2 + |B|^2 / rho), B = curl A with the first-derivative
-// stencil (z-derivatives of A_x, A_y from register pencils, x/y derivatives
-// from shared memory).  One CTA per tile; the last CTA of each run sets dt,
-// draws the forcing and advances the clock (finalize_step).
+// stencil.  Each plane is used only while it is the lead plane: its x/y
+// derivatives of A, |u| and 1/rho go into a three-plane register delay
+// line, and the z-derivatives of A_x, A_y come from register pencils, so
+// every shared-memory stage but the current one holds a plane in flight.
+// One CTA per tile; the last CTA of each run sets dt, draws the forcing and
+// advances the clock (finalize_step).
 // Stage count of the prologue: small enough for two CTAs per SM.
 template <typename T, int TY>
 __host__ __device__ constexpr int pro_stages() {
@@ -737,10 +740,10 @@ __host__ __device__ constexpr int pro_stages() {
 }
 
 template <typename T, int TY>
-__global__ void __launch_bounds__(32 * TY, 1)
+__global__ void __launch_bounds__(32 * TY, 2)
     k_prologue_tma(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles) {
   using SH = TmaShape<T, TY>;
-  constexpr int TX = SH::TX, SX = SH::SX, FIELD = SH::FIELD, NS = pro_stages<T, TY>(), P = NS - 4;
+  constexpr int TX = SH::TX, SX = SH::SX, FIELD = SH::FIELD, NS = pro_stages<T, TY>(), P = NS - 1;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ double sh[32 * TY];
   __shared__ int flag;
@@ -775,9 +778,15 @@ __global__ void __launch_bounds__(32 * TY, 1)
     const int x = tile.x0 + tx, y = tile.y0 + ty;
     const bool active = x < R.nx && y < R.ny;
     const int cxy = (ty + RAD) * SX + tx + 4;
-    T ax[7], ay[7];
+    // pencils of A_x, A_y over planes p-6 .. p; delay line of the lead-plane
+    // values (d_y A_z, d_x A_z, d_x A_y, d_y A_x, |u|, 1/rho) of planes p-3 .. p
+    T ax[7], ay[7], dl[4][6];
 #pragma unroll
     for (int k = 0; k < 7; ++k) ax[k] = ay[k] = T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int v = 0; v < 6; ++v) dl[k][v] = T(0);
     // running maximum in the working precision (exact; FP64 per point would
     // run on B300's 1/64-rate FP64 pipe), NaN tracked apart
     T vm = T(0);
@@ -787,37 +796,48 @@ __global__ void __launch_bounds__(32 * TY, 1)
     for (; p < npl; ++p) {
       if (tid == 0 && p + P < npl) {
         fence_proxy_async_smem();
-        issue(p + P);
+        issue(p + P);  // into the stage of plane p-1, released at the end of the last iteration
         issued = p + P + 1;
       }
       const int sl = p % NS;
       const bool ok = mbar_wait(&bars[sl], (uint32_t)((p / NS) & 1));
-      const T *lead = reinterpret_cast<const T *>(smem + sl * SH::STAGE_BYTES) + cxy;
+      const T *o = reinterpret_cast<const T *>(smem + sl * SH::STAGE_BYTES) + cxy;
+      auto dx = [&](int f) {
+        return w[0][1] * (o[f * FIELD + 1] - o[f * FIELD - 1]) + w[0][2] * (o[f * FIELD + 2] - o[f * FIELD - 2]) +
+               w[0][3] * (o[f * FIELD + 3] - o[f * FIELD - 3]);
+      };
+      auto dy = [&](int f) {
+        return w[1][1] * (o[f * FIELD + SX] - o[f * FIELD - SX]) +
+               w[1][2] * (o[f * FIELD + 2 * SX] - o[f * FIELD - 2 * SX]) +
+               w[1][3] * (o[f * FIELD + 3 * SX] - o[f * FIELD - 3 * SX]);
+      };
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
         ax[k] = ax[k + 1];
         ay[k] = ay[k + 1];
       }
-      ax[6] = lead[4 * FIELD];
-      ay[6] = lead[5 * FIELD];
-      if (p >= 2 * RAD && ok && active) {
-        const T *o = reinterpret_cast<const T *>(smem + ((p - RAD) % NS) * SH::STAGE_BYTES) + cxy;
-        auto dx = [&](int f) {
-          return w[0][1] * (o[f * FIELD + 1] - o[f * FIELD - 1]) + w[0][2] * (o[f * FIELD + 2] - o[f * FIELD - 2]) +
-                 w[0][3] * (o[f * FIELD + 3] - o[f * FIELD - 3]);
-        };
-        auto dy = [&](int f) {
-          return w[1][1] * (o[f * FIELD + SX] - o[f * FIELD - SX]) +
-                 w[1][2] * (o[f * FIELD + 2 * SX] - o[f * FIELD - 2 * SX]) +
-                 w[1][3] * (o[f * FIELD + 3 * SX] - o[f * FIELD - 3 * SX]);
-        };
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int v = 0; v < 6; ++v) dl[k][v] = dl[k + 1][v];
+      ax[6] = o[4 * FIELD];
+      ay[6] = o[5 * FIELD];
+      if (active) {
+        const T ux = o[FIELD], uy = o[2 * FIELD], uz = o[3 * FIELD];
+        dl[3][0] = dy(6);
+        dl[3][1] = dx(6);
+        dl[3][2] = dx(5);
+        dl[3][3] = dy(4);
+        dl[3][4] = sqrt(ux * ux + uy * uy + uz * uz);
+        dl[3][5] = exp(-o[0]);
+      }
+      if (p >= 2 * RAD && ok && active) {  // output plane p-3
         const T dzAx = w[2][1] * (ax[4] - ax[2]) + w[2][2] * (ax[5] - ax[1]) + w[2][3] * (ax[6] - ax[0]);
         const T dzAy = w[2][1] * (ay[4] - ay[2]) + w[2][2] * (ay[5] - ay[1]) + w[2][3] * (ay[6] - ay[0]);
-        const T Bx = dy(6) - dzAy;
-        const T By = dzAx - dx(6);
-        const T Bz = dx(5) - dy(4);
-        const T ux = o[FIELD], uy = o[2 * FIELD], uz = o[3 * FIELD];
-        const T v = sqrt(ux * ux + uy * uy + uz * uz) + sqrt(cs2 + (Bx * Bx + By * By + Bz * Bz) * exp(-o[0]));
+        const T Bx = dl[0][0] - dzAy;
+        const T By = dzAx - dl[0][1];
+        const T Bz = dl[0][2] - dl[0][3];
+        const T v = dl[0][4] + sqrt(cs2 + (Bx * Bx + By * By + Bz * Bz) * dl[0][5]);
         bad |= isnan(v);
         vm = fmax(vm, v);
       }
