@@ -105,7 +105,7 @@ struct Phase {
 };
 
 template <typename T, int TY, int NS, bool UNROLL7, bool ISO>
-__global__ void __launch_bounds__(32 * TY, 1)
+__global__ void __launch_bounds__(32 * TY, TY <= 6 ? 2 : 1)
     k_substep_tma(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles, int ntiles,
                   int substep) {
   using SH = TmaShape<T, TY>;
@@ -901,7 +901,8 @@ int occupancy_tma(int *bps) {
 
 // Tile variants of the TMA kernel: id -> (dtype, TY, stages, ring rotation
 // by 7-fold unrolling instead of register moves).
-//   FP32: 1 = 32x8/6; 2 = 32x4/6; 3 = 32x8/8; 4 = 32x12/6; 5 = 32x12/5; 6 = 32x16/5
+//   FP32: 1 = 32x8/6; 2 = 32x4/6; 3 = 32x8/8; 4 = 32x12/6; 5 = 32x12/5; 6 = 32x16/5;
+//         9 = 32x6/5 (two CTAs per SM)
 //   FP32 packed (isotropic grids; anisotropic runs fall back to the tile
 //   of the same shape above): 7 = 32x12/5; 8 = 32x8/6
 //   FP64: 1 = 32x4/6; 2 = 32x4/6 unrolled
@@ -914,10 +915,11 @@ int occupancy_tma(int *bps) {
   X(0, 4, float, 12, 6, false)      \
   X(0, 5, float, 12, 5, false)      \
   X(0, 6, float, 16, 5, false)      \
+  X(0, 9, float, 6, 5, false)       \
   X(1, 1, double, 4, 6, false)      \
   X(1, 2, double, 4, 6, true)
 
-int tma_num_tiles(int dtype) { return dtype == 0 ? 8 : 2; }
+int tma_num_tiles(int dtype) { return dtype == 0 ? 9 : 2; }
 
 template <typename T, int TY>
 int pro_smem_bytes() {
