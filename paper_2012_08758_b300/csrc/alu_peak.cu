@@ -110,11 +110,11 @@ extern "C" int mhd_alu_peak(int dtype, void *stream, double *flops, double *ms) 
   cudaStream_t s = (cudaStream_t)stream;
   switch (dtype) {
     case MHD_F32:
-      return time_peak<float>(0.999999f, 1e-7f, 32768, 1, s, flops, ms);
+      return time_peak<float>(0.999999f, 1e-7f, 8192, 1, s, flops, ms);
     case MHD_F64:
-      return time_peak<double>(0.999999, 1e-7, 512, 1, s, flops, ms);
+      return time_peak<double>(0.999999, 1e-7, 128, 1, s, flops, ms);
     case 2:
-      return time_peak<float2>(make_float2(0.999999f, 0.999998f), make_float2(1e-7f, 2e-7f), 16384, 2, s,
+      return time_peak<float2>(make_float2(0.999999f, 0.999998f), make_float2(1e-7f, 2e-7f), 4096, 2, s,
                                flops, ms);
     default:
       set_last_error("mhd_alu_peak: dtype must be MHD_F32, MHD_F64 or 2 (packed FP32 pairs)");
