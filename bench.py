@@ -597,6 +597,66 @@ def run_tables(args):
     return 0
 
 
+def run_c2(args):
+    """C2: the 256^3 FP32 workload for 2000 steps (device-timed throughput
+    and achieved HBM bandwidth of the fused substeps), and the growth rate
+    of ln B_rms over the first 300 steps in FP32 against the same 300 steps
+    in FP64 on the GPU (the FP64 path is the one pinned to the oracle; the
+    oracle itself would need hours for 256^3 x 300)."""
+    from paper_2012_08758_b300 import binding as B
+    from paper_2012_08758_b300 import inputs
+    from paper_2012_08758_b300.growth import brms_series, fit_last
+    from paper_2012_08758_b300.run import Run
+
+    n = args.n
+    q0 = inputs.seed_field_state(n, seed=0)
+    run = Run(n=n, dtype=B.MHD_F32, **WORKLOAD)
+    run.set_state(q0)
+    run.step(args.warmup)
+    run.sync()
+    stage_ms, total_ms = B.mhd_step_timed(run.ctx, 2000)
+    run.sync()
+    run.close()
+    out = {}
+    for dt in (B.MHD_F32, B.MHD_F64):
+        r = Run(n=n, dtype=dt, **WORKLOAD)
+        r.set_state(q0)
+        ts, bs = brms_series(r, 300, 10)
+        r.close()
+        out[dt] = (ts, bs, fit_last(ts, bs, 0.5))
+    la, lb = out[B.MHD_F32][2], out[B.MHD_F64][2]
+    line = {"workload": f"C2: {n}^3 FP32, " + workload_name(n, "f32") + ", 2000 steps",
+            "cell_updates_per_s": n ** 3 * 2000 / (total_ms / 1e3), "ms_per_step": total_ms / 2000,
+            "substep_gbs": BYTES_PER_CELL["f32"] * n ** 3 * 2000 / (sum(stage_ms[1:4]) / 1e3) / 1e9,
+            "lambda_f32_first_300": la, "lambda_f64_first_300": lb, "lambda_rel": abs(la - lb) / abs(lb),
+            "brms_rel_max": float(np.max(np.abs(out[B.MHD_F32][1] - out[B.MHD_F64][1]) / out[B.MHD_F64][1]))}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_cpu(args):
+    """The FP64 oracle timed on the host: one core and all cores, whole steps
+    at 64^3 and 128^3 (per-cell cost, which extrapolates to 512^3 by the
+    point count)."""
+    from oracle import oracle as O
+    from paper_2012_08758_b300 import inputs
+
+    allc = os.cpu_count() or 1
+    res = []
+    for n, cores in ((64, 1), (64, allc), (128, allc)):
+        used = O.set_threads(cores)
+        p = O.Params(nx=n, ny=n, nz=n, **WORKLOAD)
+        q = inputs.seed_field_state(n, seed=0)
+        t0 = time.perf_counter()
+        O.run(p, q, 1)
+        el = time.perf_counter() - t0
+        res.append({"n": n, "cores": used, "s_per_step": el, "cell_updates_per_s": n ** 3 / el,
+                    "ns_per_point_step": el * 1e9 / n ** 3})
+    O.set_threads(allc)
+    print(json.dumps({"workload": "FP64 oracle on the host cores, one whole step", "runs": res}), flush=True)
+    return 0
+
+
 def run_fp32vs64(args):
     """C3: the same initial state advanced in FP32 and in FP64 on the GPU;
     per-quantity FP32 error against FP64 (fields, rms values, energies,
@@ -644,7 +704,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
-    ap.add_argument("--workload", choices=["step", "batch", "serve", "fp32vs64", "paper", "spectrum", "tables"],
+    ap.add_argument("--workload", choices=["step", "batch", "serve", "fp32vs64", "paper", "spectrum", "tables",
+                                           "c2", "cpu"],
                     default="step",
                     help="step: the benchmark line; the others measure the batch (16x64^3+8x128^3), "
                          "serving and FP32-vs-FP64 configurations and the paper's timing protocol")
@@ -678,6 +739,10 @@ def main():
         return run_spectrum(args)
     if args.workload == "tables":
         return run_tables(args)
+    if args.workload == "c2":
+        return run_c2(args)
+    if args.workload == "cpu":
+        return run_cpu(args)
     return run_ours(args)
 
 
