@@ -388,7 +388,7 @@ def run_serve(args):
 
     from paper_2012_08758_b300 import binding as B
     from paper_2012_08758_b300.run import Run
-    from paper_2012_08758_b300.serving import Server, initial_state, requests_from_inputs, run_params, summarize
+    from paper_2012_08758_b300.serving import Server, requests_from_inputs, run_params, start, summarize
     from paper_2012_08758_b300.growth import brms_series, fit_last
 
     lo, hi = int(500 * args.serve_scale), int(5000 * args.serve_scale)
@@ -402,7 +402,7 @@ def run_serve(args):
     rates = {}
     for n in sorted({r.n for r in reqs}):
         rr = Run(n=n, dtype=B.MHD_F64, f0=0.02, seed=1)
-        rr.set_state(initial_state(reqs[0].__class__(0, 0, n, 100.0, 1.0, 10, 1)))
+        start(rr, reqs[0].__class__(0, 0, n, 100.0, 1.0, 10, 1))
         rr.step(1)
         st, tot = B.mhd_step_timed(rr.ctx, 3)
         rates[n] = n ** 3 * 3 / (tot / 1e3)
@@ -416,7 +416,7 @@ def run_serve(args):
         lam = {}
         for dt in (B.MHD_F32, B.MHD_F64):
             rr = Run(**run_params(r, dtype=dt))
-            rr.set_state(initial_state(r))
+            start(rr, r)
             ts, bs = brms_series(rr, r.steps, max(1, r.steps // 40))
             rr.close()
             lam[dt] = fit_last(ts, bs, 0.5)

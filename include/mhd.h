@@ -132,6 +132,19 @@ void mhd_destroy(mhd_ctx *ctx);
  * periodic ghost zones.  Synchronising. */
 int mhd_set_state(mhd_ctx *ctx, const void *host_soa, int host_dtype, double t, int64_t step);
 
+/* Sets the state to the paper's initial condition (Sec. 4) at t = 0, step 0:
+ * ln rho = 0, u = 0 and a weak delta-correlated seed field A = amp * N(0,1),
+ * independent per component and interior point, generated on the device
+ * (no host arrays): normal number n = c * nx*ny*nz + e of component c and
+ * point e = (k*ny + j)*nx + i is sqrt(-2 ln u1) cos(2 pi u2) (Box-Muller, FP64),
+ * u1 = ((SplitMix64(seed, 2n) >> 11) + 1) 2^-53, u2 = (SplitMix64(seed, 2n+1)
+ * >> 11) 2^-53, SplitMix64(key, c) being output c of the stream keyed by key
+ * (as in the forcing draw), rounded to the context's precision.  Use a seed
+ * other than the forcing seed of mhd_params for independent streams.
+ * Synchronising.  Errors: MHD_EINVAL (NULL ctx, amp < 0 or not finite),
+ * MHD_ECUDA. */
+int mhd_set_seed_field(mhd_ctx *ctx, uint64_t seed, double amp);
+
 /* Downloads the state into host_soa (7*nx*ny*nz values of host_dtype) and
  * the time and step index (either pointer may be NULL).  Synchronising;
  * returns MHD_ENONFINITE if the run has produced a non-finite time step. */

@@ -79,6 +79,7 @@ def lib():
                                                   C.c_double, C.c_double, C.c_double, vp, vp]),
             "mhd_alu_peak": (C.c_int, [C.c_int, vp, dp, dp]),
             "mhd_spectrum_shells": (C.c_int, [pp, C.POINTER(C.c_int)]),
+            "mhd_set_seed_field": (C.c_int, [vp, C.c_uint64, C.c_double]),
             "mhd_spectrum": (C.c_int, [vp, dp, C.c_int, C.POINTER(C.c_int)]),
         }
         for name, (res, args) in sig.items():
@@ -232,6 +233,11 @@ def mhd_diagnostics_noalloc(state_dev: int, dtype: int, nx: int, ny: int, nz: in
     _check(lib().mhd_diagnostics_noalloc(C.c_void_p(state_dev), int(dtype), int(nx), int(ny), int(nz),
                                          float(lx), float(ly), float(lz), float(cs),
                                          C.c_void_p(out_dev), C.c_void_p(stream or None)))
+
+
+def mhd_set_seed_field(ctx: int, seed: int, amp: float) -> None:
+    """The paper's initial state generated on the device (t = 0, step 0)."""
+    _check(lib().mhd_set_seed_field(C.c_void_p(ctx), int(seed) & 0xFFFFFFFFFFFFFFFF, float(amp)), ctx)
 
 
 def mhd_spectrum_shells(p: MhdParams) -> int:

@@ -608,6 +608,23 @@ int mhd_set_state(mhd_ctx *ctx, const void *host_soa, int host_dtype, double t, 
   return MHD_OK;
 }
 
+int mhd_set_seed_field(mhd_ctx *ctx, uint64_t seed, double amp) {
+  if (!ctx) return fail(nullptr, MHD_EINVAL, "ctx is NULL");
+  if (!(amp >= 0.0) || !std::isfinite(amp)) return fail(ctx, MHD_EINVAL, "amp must be finite and >= 0");
+  const RunDesc &R = ctx->h_run;
+  char *dst = static_cast<char *>(R.q[0]);
+  cudaStream_t s = ctx->stream;
+  CK(ctx, cudaMemsetAsync(dst, 0, (size_t)NF * R.fstride * ctx->L.esz, s));
+  CK(ctx, launch_seed_field(ctx->p.dtype, dst + (size_t)4 * R.fstride * ctx->L.esz, R.fstride, R.nx, R.ny,
+                            R.nz, R.px, R.py, seed, amp, s));
+  CK(ctx, launch_halo(ctx->p.dtype, dst, NF, R.fstride, R.nx, R.ny, R.nz, R.px, R.py, s));
+  Clock c;
+  std::memset(&c, 0, sizeof c);
+  CK(ctx, cudaMemcpyAsync(R.clock, &c, sizeof c, cudaMemcpyHostToDevice, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  return MHD_OK;
+}
+
 int mhd_get_state(mhd_ctx *ctx, void *host_soa, int host_dtype, double *t, int64_t *step) {
   if (!ctx) return fail(nullptr, MHD_EINVAL, "ctx is NULL");
   if (host_dtype != MHD_F32 && host_dtype != MHD_F64) return fail(ctx, MHD_EINVAL, "bad host_dtype");

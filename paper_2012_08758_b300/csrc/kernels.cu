@@ -14,6 +14,7 @@
 
 #include "mhd_internal.h"
 #include "physics.cuh"
+#include "step_device.cuh"
 
 namespace mhd {
 
@@ -355,6 +356,27 @@ __global__ void k_get_field(const T *src, H *dst, int nx, int ny, int nz, int px
   }
 }
 
+// The paper's initial magnetic field (Sec. 4): A = amp * N(0,1) independently
+// per component and interior point.  Normal number n = c * npts + e (component
+// c, point e = (k ny + j) nx + i) by Box-Muller from SplitMix64 outputs 2n and
+// 2n + 1 of the stream keyed by `seed` (u1 in (0, 1], u2 in [0, 1)), in FP64.
+template <typename T>
+__global__ void k_seed_field(T *A, long long fstride, int nx, int ny, int nz, int px, int py,
+                             unsigned long long seed, double amp) {
+  const long long npts = (long long)nx * ny * nz, total = 3 * npts;
+  const double TWO_PI = 6.283185307179586476925286766559;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < total;
+       n += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(n / npts);
+    const long long e = n - c * npts;
+    const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / ((long long)nx * ny));
+    const double u1 = (double)((splitmix64(seed, 2ull * (unsigned long long)n) >> 11) + 1ull) * 0x1.0p-53;
+    const double u2 = (double)(splitmix64(seed, 2ull * (unsigned long long)n + 1ull) >> 11) * 0x1.0p-53;
+    const double g = sqrt(-2.0 * log(u1)) * cos(TWO_PI * u2);
+    A[c * fstride + ((long long)(k + OZ) * py + (j + OY)) * px + (i + OX)] = T(amp * g);
+  }
+}
+
 static int conv_grid(long long total) {
   long long g = (total + 255) / 256;
   return (int)(g > 148 * 32 ? 148 * 32 : (g < 1 ? 1 : g));
@@ -371,6 +393,16 @@ int launch_set_field(int dtype, int host_dtype, const void *src, void *dst_field
     k_set_field<double, float><<<g, 256, 0, s>>>((const float *)src, (double *)dst_field, nx, ny, nz, px, py);
   else
     k_set_field<double, double><<<g, 256, 0, s>>>((const double *)src, (double *)dst_field, nx, ny, nz, px, py);
+  return (int)cudaGetLastError();
+}
+
+int launch_seed_field(int dtype, void *A, long long fstride, int nx, int ny, int nz, int px, int py,
+                      unsigned long long seed, double amp, cudaStream_t s) {
+  const int g = conv_grid(3LL * nx * ny * nz);
+  if (dtype == 0)
+    k_seed_field<float><<<g, 256, 0, s>>>((float *)A, fstride, nx, ny, nz, px, py, seed, amp);
+  else
+    k_seed_field<double><<<g, 256, 0, s>>>((double *)A, fstride, nx, ny, nz, px, py, seed, amp);
   return (int)cudaGetLastError();
 }
 

@@ -103,6 +103,9 @@ int substep_tile_shape(int dtype, int kernel, int tile, int *tx, int *ty);
 int substep_max_grid(int dtype, int kernel, int tile, int *blocks_per_sm);
 int launch_halo(int dtype, void *fields, int nfields, long long fstride, int nx, int ny, int nz,
                 int px, int py, cudaStream_t s);
+// A = amp * N(0,1) per component and interior point (counter-based, see kernels.cu)
+int launch_seed_field(int dtype, void *A, long long fstride, int nx, int ny, int nz, int px, int py,
+                      unsigned long long seed, double amp, cudaStream_t s);
 int launch_set_field(int dtype, int host_dtype, const void *src, void *dst_field, int nx, int ny,
                      int nz, int px, int py, cudaStream_t s);
 int launch_get_field(int dtype, int host_dtype, const void *src_field, void *dst, int nx, int ny,

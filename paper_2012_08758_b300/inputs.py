@@ -92,3 +92,31 @@ def serving_requests(n: int = 200, seed: int = 2025, rate: float = 1.0,
             seed=int(rng.integers(0, 2**62)),
         ))
     return out
+
+
+def _splitmix64(key: int, ctr: np.ndarray) -> np.ndarray:
+    """Output ctr of the SplitMix64 stream keyed by key (Steele, Lea & Flood
+    2014), vectorised on uint64 with wrap-around arithmetic."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(key & 0xFFFFFFFFFFFFFFFF) + (ctr + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def counter_seed_field_state(nx: int, ny: int | None = None, nz: int | None = None,
+                             seed: int = 0, amp: float = 1e-5) -> np.ndarray:
+    """The initial state that mhd_set_seed_field generates on the device,
+    built on the host from the same published generators: ln rho = 0, u = 0,
+    A = amp * N(0,1) with normal n = c * npts + e by Box-Muller from SplitMix64
+    outputs 2n, 2n + 1 of the stream keyed by seed."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    npts = nx * ny * nz
+    n = np.arange(3 * npts, dtype=np.uint64)
+    u1 = ((_splitmix64(seed, np.uint64(2) * n) >> np.uint64(11)) + np.uint64(1)).astype(np.float64) * 2.0 ** -53
+    u2 = (_splitmix64(seed, np.uint64(2) * n + np.uint64(1)) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    g = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    q = np.zeros((7, nz, ny, nx))
+    q[4:7] = amp * g.reshape(3, nz, ny, nx)
+    return q

@@ -63,6 +63,10 @@ class Run:
         assert q.shape == self.shape, (q.shape, self.shape)
         B.mhd_set_state(self.ctx, q, t, step)
 
+    def set_seed_field(self, seed: int, amp: float = 1e-5) -> None:
+        """ln rho = 0, u = 0, A = amp * N(0,1) per point, generated on the device."""
+        B.mhd_set_seed_field(self.ctx, seed, amp)
+
     def get_state(self, dtype=np.float64):
         return B.mhd_get_state(self.ctx, shape=self.shape, dtype=dtype)
 

@@ -65,9 +65,24 @@ def run_params(req: Request, urms0: float = 0.05, dtype=B.MHD_F32, **extra) -> d
     return p
 
 
+SEED_FIELD_AMP = 1e-5
+SEED_FIELD_KEY = 1 << 32  # offset of the seed-field stream from the forcing stream
+
+
+def seed_field_key(req: Request) -> int:
+    return req.seed + SEED_FIELD_KEY
+
+
 def initial_state(req: Request) -> np.ndarray:
-    """Uniform density, no flow, weak delta-correlated seed field (Sec. 4)."""
-    return inputs.seed_field_state(req.n, seed=req.seed, amp=1e-5)
+    """Uniform density, no flow, weak delta-correlated seed field (Sec. 4):
+    the host copy of what start() generates on the device."""
+    return inputs.counter_seed_field_state(req.n, seed=seed_field_key(req), amp=SEED_FIELD_AMP)
+
+
+def start(run, req: Request) -> None:
+    """Puts a run into its request's initial state, generated on the device
+    (no host arrays, no upload)."""
+    run.set_seed_field(seed_field_key(req), SEED_FIELD_AMP)
 
 
 class Server:
@@ -99,7 +114,7 @@ class Server:
         nbytes = self.footprint(req)
         run = Run(device=self.device, **run_params(req, self.urms0, self.dtype, kernel=self.kernel,
                                                     tile=self.tile))
-        run.set_state(initial_state(req))
+        start(run, req)
         b0 = run.reduce(B.MHD_BRMS)
         self.active.append([run, req, req.steps, now, [0.0], [b0], nbytes])
         self.used += nbytes

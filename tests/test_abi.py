@@ -94,3 +94,8 @@ def test_spectrum_shell_count_and_box_checks(B):
         with pytest.raises(B.MhdError) as e:
             B.mhd_spectrum_shells(B.mhd_default_params(**bad))
         assert e.value.code == B.MHD_EINVAL
+
+
+def test_seed_field_rejects_null_context(B):
+    import ctypes as C
+    assert B.lib().mhd_set_seed_field(None, C.c_uint64(1), C.c_double(1e-5)) == B.MHD_EINVAL

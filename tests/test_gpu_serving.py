@@ -17,7 +17,7 @@ def _requests():
 def test_serving_results_equal_runs_alone():
     from paper_2012_08758_b300 import binding as B
     from paper_2012_08758_b300.run import Run
-    from paper_2012_08758_b300.serving import Server, initial_state, run_params
+    from paper_2012_08758_b300.serving import Server, run_params, start
 
     reqs = _requests()
     srv = Server(chunk=10, time_scale=1.0)
@@ -25,7 +25,7 @@ def test_serving_results_equal_runs_alone():
     assert sorted(res) == [0, 1, 2, 3]
     for req in reqs:
         run = Run(**run_params(req))
-        run.set_state(initial_state(req))
+        start(run, req)
         # the server stepped this run in chunks inside changing batches; the
         # final state must be the one of an uninterrupted run
         run.step(req.steps)
@@ -68,3 +68,24 @@ def test_autotuner_returns_a_working_variant():
     assert all(v > 0 for v in best["ms"].values()) and len(best["ms"]) >= 2
     both = autotune.tune([(16, 16, 16), (24, 24, 24)], B.MHD_F32, steps=2)
     assert both["ms"]
+
+
+@pytest.mark.parametrize("dtype,tol", [(1, 1e-13), (0, 6e-8)])
+def test_device_seed_field_equals_host_generator(dtype, tol):
+    """mhd_set_seed_field against the same counter-based generator on the
+    host (SplitMix64 + Box-Muller): equal to FP64 library rounding (FP32:
+    to FP32 rounding); ln rho and u exactly zero; t = 0, step 0."""
+    from paper_2012_08758_b300 import inputs
+    from paper_2012_08758_b300.run import Run
+    nx, ny, nz, seed, amp = 20, 13, 9, 2**33 + 5, 1e-5
+    run = Run(nx=nx, ny=ny, nz=nz, dtype=dtype)
+    run.set_state(inputs.random_modes_state(nx, ny, nz, seed=1))  # overwritten below
+    run.set_seed_field(seed, amp)
+    got, t, step = run.get_state()
+    run.close()
+    want = inputs.counter_seed_field_state(nx, ny, nz, seed=seed, amp=amp)
+    assert t == 0.0 and step == 0
+    assert np.all(got[:4] == 0.0)
+    assert np.abs(got - want).max() <= tol * amp * np.abs(want[4:]).max() / amp
+    g = want[4:] / amp  # the host normals: sample statistics of N(0, 1)
+    assert abs(g.mean()) < 0.03 and abs(g.std() - 1.0) < 0.03
