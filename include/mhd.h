@@ -167,7 +167,9 @@ int mhd_step(mhd_ctx *ctx, int nsteps);
 int mhd_step_timed(mhd_ctx *ctx, int nsteps, double *stage_ms, double *total_ms);
 
 /* Reads one quantity (MHD_URMS ... MHD_VMAX) of the current state into
- * *out, accumulated in FP64 in a fixed order.  Synchronising. */
+ * *out, accumulated in FP64 in a fixed order.  MHD_BRMS (sampled every few
+ * steps by growth-rate runs) takes a single fused pass over A with the same
+ * tiles and summation order as mhd_diagnostics.  Synchronising. */
 int mhd_reduce(mhd_ctx *ctx, int kind, double *out);
 
 /* All MHD_NREDUCE quantities at once into out[MHD_NREDUCE].  Synchronising. */

@@ -725,6 +725,14 @@ int mhd_reduce(mhd_ctx *ctx, int kind, double *out) {
   if (!ctx) return fail(nullptr, MHD_EINVAL, "ctx is NULL");
   if (kind < 0 || kind >= MHD_NREDUCE) return fail(ctx, MHD_EINVAL, "unknown reduction kind %d", kind);
   if (!out) return fail(ctx, MHD_EINVAL, "out is NULL");
+  if (kind == MHD_BRMS) {  // one fused pass: no stored B, no halo, no other sums
+    CK(ctx, launch_brms(ctx->p.dtype, ctx->d_run, ctx->d_tiles, ctx->ntiles, ctx->L.tw, ctx->L.th, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(out, ctx->h_run.diag + 1, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    Clock c;
+    int rc = read_clock(ctx, &c);
+    if (rc) return rc;
+    return check_status(ctx, c);
+  }
   double all[MHD_NREDUCE];
   int rc = mhd_diagnostics(ctx, all);
   if (rc) return rc;

@@ -110,6 +110,9 @@ int launch_set_field(int dtype, int host_dtype, const void *src, void *dst_field
                      int nz, int px, int py, cudaStream_t s);
 int launch_get_field(int dtype, int host_dtype, const void *src_field, void *dst, int nx, int ny,
                      int nz, int px, int py, cudaStream_t s);
+// B_rms of the run's current state into diag[1] (curl and sum in one pass)
+int launch_brms(int dtype, const RunDesc *run_dev, const Tile *tiles, int ntiles, int tw, int th,
+                cudaStream_t s);
 // B = curl A of the run's current state into fields 0..2 of its w buffer
 // (interior points only).
 int launch_curl(int dtype, const RunDesc *run_dev, const Tile *tiles, int ntiles, int tw, int th,

@@ -184,6 +184,55 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS) k_diag(const RunDesc *__rest
   R.counter[1] = 0u;
 }
 
+// B_rms alone (the quantity sampled every step of a growth-rate run): B = curl A
+// straight from the state and sum |B|^2 in FP64, with the tiles, per-thread
+// z order, block tree and final tile order of k_diag, so the value equals the
+// B_rms of the full diagnostics without storing B or filling its halo.
+template <typename T>
+__global__ void __launch_bounds__(MAX_TILE_THREADS) k_brms(const RunDesc *__restrict__ runs,
+                                              const Tile *__restrict__ tiles) {
+  __shared__ double sh[MAX_TILE_THREADS];
+  __shared__ int flag;
+  const Tile tile = tiles[blockIdx.x];
+  const RunDesc &R = runs[tile.run];
+  const T *q = static_cast<const T *>(R.q[R.clock->step & 1]);
+  const long long fs = R.fstride, sy = R.px, sz = (long long)R.px * R.py;
+  T w[3][4];
+  for (int a = 0; a < 3; ++a)
+    for (int s = 0; s < 4; ++s) w[a][s] = T(W1(s) * R.inv_h[a]);
+  double sb2 = 0;
+  const int x = tile.x0 + threadIdx.x, y = tile.y0 + threadIdx.y;
+  if (x < R.nx && y < R.ny) {
+    const T *Ax = q + 4 * fs, *Ay = q + 5 * fs, *Az = q + 6 * fs;
+    for (int z = tile.z0; z < tile.z1; ++z) {
+      const long long c = ((long long)(z + OZ) * R.py + (y + OY)) * R.px + (x + OX);
+      const T bx = d1_at<T, 1>(Az, c, sy, w[1]) - d1_at<T, 2>(Ay, c, sz, w[2]);
+      const T by = d1_at<T, 2>(Ax, c, sz, w[2]) - d1_at<T, 0>(Az, c, 1, w[0]);
+      const T bz = d1_at<T, 0>(Ay, c, 1, w[0]) - d1_at<T, 1>(Ax, c, sy, w[1]);
+      sb2 += (double)(bx * bx + by * by + bz * bz);
+    }
+  }
+  const double red = block_sum(sb2, sh);
+  if (threadIdx.x == 0 && threadIdx.y == 0) R.partials[(long long)tile.slot * NPART + 1] = red;
+  if (!last_tile_done(&R.counter[2], R.ntiles, &flag)) return;
+  const int nthr = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+  double loc = 0;
+  for (int t = tid; t < R.ntiles; t += nthr) loc += __ldcg(&R.partials[(long long)t * NPART + 1]);
+  const double tot = block_sum(loc, sh);
+  if (tid != 0) return;
+  R.diag[1] = sqrt(tot / ((double)R.nx * R.ny * R.nz));
+  R.counter[2] = 0u;
+}
+
+int launch_brms(int dtype, const RunDesc *run_dev, const Tile *tiles, int ntiles, int tw, int th,
+                cudaStream_t s) {
+  if (dtype == 0)
+    k_brms<float><<<ntiles, dim3(tw, th), 0, s>>>(run_dev, tiles);
+  else
+    k_brms<double><<<ntiles, dim3(tw, th), 0, s>>>(run_dev, tiles);
+  return (int)cudaGetLastError();
+}
+
 int launch_curl(int dtype, const RunDesc *run_dev, const Tile *tiles, int ntiles, int tw, int th,
                 cudaStream_t s) {
   if (dtype == 0)

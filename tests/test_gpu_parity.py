@@ -302,6 +302,23 @@ def test_diagnostics_match_oracle(dtype, tol):
     run.close()
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_fused_brms_equals_full_diagnostics(dtype):
+    """mhd_reduce(B_rms) runs its own one-pass kernel; it must give the B_rms
+    of the full diagnostics (same per-point values, tiles and order)."""
+    from paper_2012_08758_b300 import binding as B
+    kw = dict(nx=37, ny=23, nz=19, dtype=dtype)
+    q = inputs.random_modes_state(37, 23, 19, seed=31, amp=0.3) + inputs.noise_state(37, 23, 19, seed=32,
+                                                                                    amp=0.05)
+    run = make_run(**kw)
+    run.set_state(q)
+    fast = run.reduce(B.MHD_BRMS)
+    full = run.diagnostics()["brms"]
+    assert fast == pytest.approx(full, rel=1e-13)
+    assert fast == pytest.approx(O.diagnostics(oracle_params(**kw), q)["brms"], rel=1e-12 if dtype == "f64" else 1e-5)
+    run.close()
+
+
 def test_state_roundtrip_is_exact():
     q = inputs.noise_state(13, 7, 5, seed=1, amp=1.0)
     run = make_run(nx=13, ny=7, nz=5, dtype="f64")
