@@ -115,11 +115,16 @@ struct StencilCoefs {
   __device__ __forceinline__ T wm(int pair, int s) const { return cm[ISO ? 0 : pair][s]; }
 };
 
+// 1/rho = exp(-ln rho): FP32 takes the hardware exponential (__expf, a few
+// ulp: far inside the FP32 error budget of the step), FP64 the library exp.
+__device__ __forceinline__ float inv_density(float lnr) { return __expf(-lnr); }
+__device__ __forceinline__ double inv_density(double lnr) { return exp(-lnr); }
+
 // dq/dt of Eqs. 1-3 at one point; f = forcing (already evaluated).
 // C provides cs2, nu, eta in the working precision.
 template <typename T, class C>
 __device__ __forceinline__ void rhs_point(const Derivs<T> &d, const C &c, const T f[3], T out[NF]) {
-  const T rho_inv = exp(-d.lnr);
+  const T rho_inv = inv_density(d.lnr);
   const T divu = d.G[0][0] + d.G[1][1] + d.G[2][2];
   const T B[3] = {d.gA[2][1] - d.gA[1][2], d.gA[0][2] - d.gA[2][0], d.gA[1][0] - d.gA[0][1]};
   // Eq. 1: D ln rho / Dt = -div u
