@@ -541,7 +541,8 @@ def run_tables(args):
     from paper_2012_08758_b300.run import Batch, Run
 
     grids = [int(g) for g in args.tables_grids.split(",")]
-    rows = [r for r in paper_tables() if r["n"] in grids]
+    etas = [float(e) for e in args.tables_eta.split(",")] if args.tables_eta else None
+    rows = [r for r in paper_tables() if r["n"] in grids and (etas is None or r["eta"] in etas)]
     kf = shell_mean_k(4.5, 5.5)
     runs, series, live = [], [], []
     for i, r in enumerate(rows):
@@ -720,6 +721,7 @@ def main():
     ap.add_argument("--tables-tmax", type=float, default=600.0)
     ap.add_argument("--tables-chunk", type=int, default=200)
     ap.add_argument("--tables-f0", type=float, default=0.029)
+    ap.add_argument("--tables-eta", default="", help="comma-separated eta values to keep (default: all rows)")
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 plane ring, 2 TMA")
     ap.add_argument("--tile", type=int, default=0, help="tile variant id (0: default)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU-baseline leg")
