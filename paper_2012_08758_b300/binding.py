@@ -80,6 +80,8 @@ def lib():
             "mhd_alu_peak": (C.c_int, [C.c_int, vp, dp, dp]),
             "mhd_spectrum_shells": (C.c_int, [pp, C.POINTER(C.c_int)]),
             "mhd_set_seed_field": (C.c_int, [vp, C.c_uint64, C.c_double]),
+            "mhd_substep_plan": (C.c_int, [pp, C.c_int, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int),
+                                           C.POINTER(C.c_int)]),
             "mhd_spectrum": (C.c_int, [vp, dp, C.c_int, C.POINTER(C.c_int)]),
         }
         for name, (res, args) in sig.items():
@@ -238,6 +240,16 @@ def mhd_diagnostics_noalloc(state_dev: int, dtype: int, nx: int, ny: int, nz: in
 def mhd_set_seed_field(ctx: int, seed: int, amp: float) -> None:
     """The paper's initial state generated on the device (t = 0, step 0)."""
     _check(lib().mhd_set_seed_field(C.c_void_p(ctx), int(seed) & 0xFFFFFFFFFFFFFFFF, float(amp)), ctx)
+
+
+def mhd_substep_plan(p: MhdParams, grid_ctas: int):
+    """(tiles as an (ntiles, 5) array of x0, y0, z0, z1, run; grid) of the
+    fused substep's work split for grid_ctas persistent CTAs."""
+    n, g = C.c_int(), C.c_int()
+    _check(lib().mhd_substep_plan(C.byref(p), int(grid_ctas), None, 0, C.byref(n), C.byref(g)))
+    buf = (C.c_int * max(1, 5 * n.value))()
+    _check(lib().mhd_substep_plan(C.byref(p), int(grid_ctas), buf, n.value, C.byref(n), C.byref(g)))
+    return np.frombuffer(buf, dtype=np.int32)[: 5 * n.value].reshape(n.value, 5).copy(), g.value
 
 
 def mhd_spectrum_shells(p: MhdParams) -> int:

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/mhd.h"
+#include "../../include/mhd_plan.h"
 #include "mhd_internal.h"
 
 using namespace mhd;
@@ -768,6 +769,25 @@ int mhd_forcing_draw(mhd_ctx *ctx, int64_t step, double *out) {
   CK(ctx, launch_forcing_draw(ctx->d_run, step, scratch, ctx->stream));
   CK(ctx, cudaMemcpyAsync(out, scratch, sizeof(double) * 13, cudaMemcpyDeviceToHost, ctx->stream));
   CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return MHD_OK;
+}
+
+int mhd_substep_plan(const mhd_params *p, int grid_ctas, int *tiles, int max_tiles, int *ntiles, int *grid) {
+  std::string why;
+  if (validate(p, &why)) return fail(nullptr, MHD_EINVAL, "%s", why.c_str());
+  if (grid_ctas < 1 || !ntiles || !grid) return fail(nullptr, MHD_EINVAL, "grid_ctas < 1 or NULL output");
+  const Layout L = make_layout(p);
+  std::vector<SubCol> cols;
+  add_columns(&cols, 0, p->nx, p->ny, p->nz, L.tw, L.th);
+  const std::vector<Tile> t = split_columns(cols, std::min(grid_ctas, GMAX), grid);
+  *ntiles = (int)t.size();
+  for (size_t i = 0; tiles && i < t.size() && (int)i < max_tiles; ++i) {
+    tiles[5 * i + 0] = t[i].x0;
+    tiles[5 * i + 1] = t[i].y0;
+    tiles[5 * i + 2] = t[i].z0;
+    tiles[5 * i + 3] = t[i].z1;
+    tiles[5 * i + 4] = t[i].run;
+  }
   return MHD_OK;
 }
 
