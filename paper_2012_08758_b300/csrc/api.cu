@@ -594,10 +594,20 @@ int mhd_set_state(mhd_ctx *ctx, const void *host_soa, int host_dtype, double t, 
   void *staging = R.w;  // dead between steps; holds one host-typed field
   cudaStream_t s = ctx->stream;
   for (int f = 0; f < NF; ++f) {
-    CK(ctx, cudaMemcpyAsync(staging, static_cast<const char *>(host_soa) + f * hb, hb,
-                            cudaMemcpyHostToDevice, s));
-    CK(ctx, launch_set_field(dt, host_dtype, staging, dst + (size_t)f * R.fstride * ctx->L.esz, R.nx,
-                             R.ny, R.nz, R.px, R.py, s));
+    char *field = dst + (size_t)f * R.fstride * ctx->L.esz;
+    const char *src = static_cast<const char *>(host_soa) + f * hb;
+    if (host_dtype == dt) {  // same precision: one strided copy into the padded interior
+      cudaMemcpy3DParms c3 = {};
+      c3.srcPtr = make_cudaPitchedPtr(const_cast<char *>(src), (size_t)R.nx * ctx->L.esz, R.nx, R.ny);
+      c3.dstPtr = make_cudaPitchedPtr(field, (size_t)R.px * ctx->L.esz, R.px, R.py);
+      c3.dstPos = make_cudaPos((size_t)OX * ctx->L.esz, OY, OZ);
+      c3.extent = make_cudaExtent((size_t)R.nx * ctx->L.esz, R.ny, R.nz);
+      c3.kind = cudaMemcpyHostToDevice;
+      CK(ctx, cudaMemcpy3DAsync(&c3, s));
+    } else {
+      CK(ctx, cudaMemcpyAsync(staging, src, hb, cudaMemcpyHostToDevice, s));
+      CK(ctx, launch_set_field(dt, host_dtype, staging, field, R.nx, R.ny, R.nz, R.px, R.py, s));
+    }
   }
   CK(ctx, launch_halo(dt, dst, NF, R.fstride, R.nx, R.ny, R.nz, R.px, R.py, s));
   Clock c;
@@ -639,10 +649,20 @@ int mhd_get_state(mhd_ctx *ctx, void *host_soa, int host_dtype, double *t, int64
     void *staging = R.w;
     cudaStream_t s = ctx->stream;
     for (int f = 0; f < NF; ++f) {
-      CK(ctx, launch_get_field(ctx->p.dtype, host_dtype, src + (size_t)f * R.fstride * ctx->L.esz,
-                               staging, R.nx, R.ny, R.nz, R.px, R.py, s));
-      CK(ctx, cudaMemcpyAsync(static_cast<char *>(host_soa) + f * hb, staging, hb,
-                              cudaMemcpyDeviceToHost, s));
+      const char *field = src + (size_t)f * R.fstride * ctx->L.esz;
+      char *out = static_cast<char *>(host_soa) + f * hb;
+      if (host_dtype == ctx->p.dtype) {  // same precision: one strided copy from the padded interior
+        cudaMemcpy3DParms c3 = {};
+        c3.srcPtr = make_cudaPitchedPtr(const_cast<char *>(field), (size_t)R.px * ctx->L.esz, R.px, R.py);
+        c3.srcPos = make_cudaPos((size_t)OX * ctx->L.esz, OY, OZ);
+        c3.dstPtr = make_cudaPitchedPtr(out, (size_t)R.nx * ctx->L.esz, R.nx, R.ny);
+        c3.extent = make_cudaExtent((size_t)R.nx * ctx->L.esz, R.ny, R.nz);
+        c3.kind = cudaMemcpyDeviceToHost;
+        CK(ctx, cudaMemcpy3DAsync(&c3, s));
+      } else {
+        CK(ctx, launch_get_field(ctx->p.dtype, host_dtype, field, staging, R.nx, R.ny, R.nz, R.px, R.py, s));
+        CK(ctx, cudaMemcpyAsync(out, staging, hb, cudaMemcpyDeviceToHost, s));
+      }
     }
     CK(ctx, cudaStreamSynchronize(s));
   }
