@@ -7,11 +7,11 @@
 // Shell sum in two passes over the half spectrum (kx >= 0, nh = nx/2 + 1
 // modes per row; modes 0 < kx < nx/2 stand for their conjugate partners
 // too and count twice):
-//   1. one warp per row (ky, kz): along a row |k| grows with kx and the
-//      shell index m = floor(|k| + 1/2) rises by at most one per step, so a
-//      row's modes form consecutive runs of equal m.  A segmented scan
-//      across the warp's lanes (fixed shuffle network) sums each run; the
-//      row's sums go to rowsum[row][m - m_min(row)].
+//   1. one thread per row (ky, kz), k_x in increasing order: along a row
+//      |k|^2 = kx^2 + ky^2 + kz^2 grows by 2 kx + 1 per step and the shell
+//      m = floor(|k| + 1/2) -- the least m >= 0 with |k|^2 <= m^2 + m, exact
+//      in integers -- rises by at most one per step, so each shell's modes
+//      of a row are consecutive; their sum goes to rowsum[row][m - m_min(row)].
 //   2. one block per shell m: the sum over rows in row order, then a fixed
 //      block tree.
 #include <cuda_runtime.h>
@@ -27,82 +27,61 @@
 namespace mhd {
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
 constexpr int SPEC_THREADS = 256;
 
-__device__ __forceinline__ int shell_of(long long k2) { return (int)floor(sqrt((double)k2) + 0.5); }
+// Least m >= 0 with k2 <= m^2 + m (= floor(sqrt(k2) + 1/2) for integer k2):
+// a single-precision square-root estimate corrected in integers.
+__device__ __forceinline__ int shell_of(long long k2) {
+  long long m = (long long)sqrtf((float)k2);
+  while (m * m + m < k2) ++m;
+  while (m > 0 && (m - 1) * (m - 1) + (m - 1) >= k2) --m;
+  return (int)m;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(SPEC_THREADS)
     k_spec_rows(const Cplx<T> *__restrict__ bh, long long odist, int nx, int ny, int nz, double norm,
                 double *__restrict__ rowsum, int2 *__restrict__ rowinfo) {
-  const int lane = threadIdx.x & 31;
-  const long long row = ((long long)blockIdx.x * SPEC_THREADS + threadIdx.x) >> 5;
+  const long long row = (long long)blockIdx.x * SPEC_THREADS + threadIdx.x;
   const long long nrows = (long long)ny * nz;
-  if (row >= nrows) return;  // warp-uniform
+  if (row >= nrows) return;
   const int nh = nx / 2 + 1;
   const int iz = (int)(row / ny), iy = (int)(row % ny);
   const long long ky = iy <= ny / 2 ? iy : iy - ny;
   const long long kz = iz <= nz / 2 ? iz : iz - nz;
   const long long kyz2 = ky * ky + kz * kz;
   const int smin = shell_of(kyz2);
-  const int smax = shell_of((long long)(nh - 1) * (nh - 1) + kyz2);
+  long long m = smin, top = (long long)smin * smin + smin;  // |k|^2 <= top inside shell m
   const Cplx<T> *r0 = bh + row * nh;
+  const Cplx<T> *r1 = r0 + odist, *r2 = r1 + odist;
   double *out = rowsum + row * nh;
-  double carry = 0.0;
-  int cshell = smin;
-  for (int base = 0; base < nh; base += 32) {
-    const int kx = base + lane;
-    const bool v = kx < nh;
-    double e = 0.0;
-    int s = INT_MAX;
-    if (v) {
-      double a2 = 0.0;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const Cplx<T> z = r0[c * odist + kx];
-        a2 += (double)z.re * (double)z.re + (double)z.im * (double)z.im;
-      }
-      const double wgt = (kx == 0 || 2 * kx == nx) ? 1.0 : 2.0;
-      e = wgt * norm * a2;
-      s = shell_of((long long)kx * kx + kyz2);
+  double acc = 0.0;
+  long long k2 = kyz2;
+  for (int kx = 0; kx < nh; ++kx) {
+    if (k2 > top) {  // the row leaves shell m (at most one shell per step)
+      out[m - smin] = acc;
+      acc = 0.0;
+      ++m;
+      top += 2 * m;
     }
-    // inclusive scan within runs of equal s (keys do not decrease across lanes)
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const double eo = __shfl_up_sync(FULL, e, d);
-      const int so = __shfl_up_sync(FULL, s, d);
-      if (lane >= d && so == s) e += eo;
-    }
-    const int s0 = __shfl_sync(FULL, s, 0);
-    const int last = min(31, nh - 1 - base);
-    const int slast = __shfl_sync(FULL, s, last);
-    if (base > 0) {
-      if (s0 != cshell) {
-        if (lane == 0) out[cshell - smin] = carry;  // the carried run ended at the boundary
-      } else if (s == cshell) {
-        e += carry;  // the first run continues the carried one
-      }
-    }
-    const int snext = __shfl_down_sync(FULL, s, 1);
-    const bool end = v && (lane == last || snext != s);
-    if (end && s != slast) out[s - smin] = e;
-    carry = __shfl_sync(FULL, e, last);
-    cshell = slast;
+    const Cplx<T> a = r0[kx], b = r1[kx], c = r2[kx];
+    const T a2 = a.re * a.re + a.im * a.im + b.re * b.re + b.im * b.im + c.re * c.re + c.im * c.im;
+    acc += ((kx == 0 || 2 * kx == nx) ? norm : 2.0 * norm) * (double)a2;
+    k2 += 2 * kx + 1;
   }
-  if (lane == 0) {
-    out[cshell - smin] = carry;
-    rowinfo[row] = make_int2(smin, smax);
-  }
+  out[m - smin] = acc;
+  rowinfo[row] = make_int2(smin, (int)m);
 }
 
-__global__ void __launch_bounds__(SPEC_THREADS)
+constexpr int SHELL_THREADS = 1024;
+
+__global__ void __launch_bounds__(SHELL_THREADS)
     k_spec_shells(const double *__restrict__ rowsum, const int2 *__restrict__ rowinfo, long long nrows,
                   int nh, double *__restrict__ out) {
-  __shared__ double sh[SPEC_THREADS];
+  __shared__ double sh[SHELL_THREADS];
   const int s = blockIdx.x;
   double acc = 0.0;
-  for (long long r = threadIdx.x; r < nrows; r += SPEC_THREADS) {
+  for (long long r = threadIdx.x; r < nrows; r += SHELL_THREADS) {
     const int2 mm = rowinfo[r];
     if (s >= mm.x && s <= mm.y) acc += rowsum[r * nh + (s - mm.x)];
   }
@@ -131,7 +110,7 @@ int launch_spectrum_bins(int dtype, const void *bh, long long odist, int nx, int
   double *rowsum = reinterpret_cast<double *>(p);
   size_t off = (size_t)(nrows * nh * 8 + 15) / 16 * 16;
   int2 *rowinfo = reinterpret_cast<int2 *>(p + off);
-  const long long blocks = (nrows * 32 + SPEC_THREADS - 1) / SPEC_THREADS;
+  const long long blocks = (nrows + SPEC_THREADS - 1) / SPEC_THREADS;
   if (dtype == 0)
     k_spec_rows<float><<<(unsigned)blocks, SPEC_THREADS, 0, s>>>(static_cast<const Cplx<float> *>(bh), odist,
                                                                  nx, ny, nz, norm, rowsum, rowinfo);
@@ -140,7 +119,7 @@ int launch_spectrum_bins(int dtype, const void *bh, long long odist, int nx, int
                                                                   nx, ny, nz, norm, rowsum, rowinfo);
   int e = (int)cudaGetLastError();
   if (e) return e;
-  k_spec_shells<<<spectrum_nshells(nx, ny, nz), SPEC_THREADS, 0, s>>>(rowsum, rowinfo, nrows, (int)nh,
+  k_spec_shells<<<spectrum_nshells(nx, ny, nz), SHELL_THREADS, 0, s>>>(rowsum, rowinfo, nrows, (int)nh,
                                                                      shells_out);
   return (int)cudaGetLastError();
 }
