@@ -374,6 +374,8 @@ int read_clock(mhd_ctx *ctx, Clock *c) {
 }
 
 int check_status(mhd_ctx *ctx, const Clock &c) {
+  if (c.status & 2)
+    return fail(ctx, MHD_ETIMEOUT, "a bounded wait for a TMA plane copy gave up by step %lld", c.step);
   if (c.status & 1)
     return fail(ctx, MHD_ENONFINITE, "non-finite time step at step %lld (run blew up)", c.step);
   return MHD_OK;

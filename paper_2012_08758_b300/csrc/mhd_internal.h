@@ -23,7 +23,8 @@ struct Clock {
   double t;
   double dt_last;
   long long step;
-  int status;   // bit 0: the time-step reduction saw a non-finite value
+  int status;   // bit 0: the time-step reduction saw a non-finite value;
+                // bit 1: a bounded wait for a TMA copy gave up
   int pad;
 };
 
