@@ -63,6 +63,32 @@ class Run:
         assert q.shape == self.shape, (q.shape, self.shape)
         B.mhd_set_state(self.ctx, q, t, step)
 
+    def params_dict(self) -> dict:
+        return {name: getattr(self.params, name) for name, _ in self.params._fields_}
+
+    def checkpoint(self, path: str) -> None:
+        """Writes the state (in the working precision, so a restore is exact),
+        t, the step index and the parameters to an .npz file.  The forcing's
+        random numbers are counter-based (seed, step), so no generator state
+        is needed: a restored run continues bit for bit."""
+        wp = np.float32 if self.params.dtype == B.MHD_F32 else np.float64
+        q, t, step = self.get_state(dtype=wp)
+        kinds = dict(B.MhdParams._fields_)
+        params = {}
+        for name, value in self.params_dict().items():
+            dt = np.uint64 if kinds[name] is B.C.c_uint64 else (np.int64 if kinds[name] is B.C.c_int else np.float64)
+            params["param_" + name] = np.asarray(value, dtype=dt)
+        np.savez(path, q=q, t=np.float64(t), step=np.int64(step), **params)
+
+    @classmethod
+    def restore(cls, path: str, device=None, stream=None) -> "Run":
+        """A new Run with the parameters, state, t and step of a checkpoint."""
+        d = np.load(path)
+        p = {key[len("param_"):]: d[key].item() for key in d.files if key.startswith("param_")}
+        r = cls(device=device, stream=stream, **p)
+        r.set_state(d["q"], float(d["t"]), int(d["step"]))
+        return r
+
     def set_seed_field(self, seed: int, amp: float = 1e-5) -> None:
         """ln rho = 0, u = 0, A = amp * N(0,1) per point, generated on the device."""
         B.mhd_set_seed_field(self.ctx, seed, amp)

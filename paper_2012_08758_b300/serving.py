@@ -9,7 +9,9 @@ over the combined tile table, replayed from a CUDA graph) in chunks; after
 each chunk it samples B_rms of every run, retires runs whose budget is spent
 (result: growth rate of ln B_rms, final diagnostics, latency) and admits
 runs that arrived meanwhile.  A run's result does not depend on what it was
-batched with.
+batched with.  A run that blows up (non-finite time step: the paper's
+under-resolved runs "crash early") or is cancelled is retired with that
+status at the next chunk boundary and frees its slot; the others go on.
 
 Physics parameters (Sec. 4): L = 2 pi, c_s = 1, f0 = 0.02, forcing shell
 2.5 <= |k| <= 3.5 (k_f = 3.13), nu = eta = u_rms0 / (Re_M k_f) with u_rms0 the
@@ -51,6 +53,7 @@ class Result:
     diagnostics: dict
     t: list = field(repr=False, default_factory=list)
     brms: list = field(repr=False, default_factory=list)
+    status: str = "ok"
 
     @property
     def latency(self) -> float:
@@ -88,7 +91,7 @@ def start(run, req: Request) -> None:
 class Server:
     def __init__(self, device=None, budget_bytes: float = 150e9, max_active: int = 64,
                  chunk: int = 50, urms0: float = 0.05, dtype=B.MHD_F32, kernel: int = 0, tile: int = 0,
-                 time_scale: float = 1.0, window: float = 0.5):
+                 time_scale: float = 1.0, window: float = 0.5, run_factory=None, batch_factory=None):
         self.device = device
         self.budget = budget_bytes
         self.max_active = max_active
@@ -102,6 +105,27 @@ class Server:
         self.active = []              # [Run, Request, remaining, admitted, ts, bs, nbytes]
         self.results: list[Result] = []
         self.stepped_cells = 0
+        self.cancelled: set[int] = set()
+        # constructors of runs and batches (the GPU Run and Batch unless given)
+        self._run_factory = run_factory
+        self._batch_factory = batch_factory
+
+    def cancel(self, request_id: int) -> None:
+        """Drops a queued request, or retires an active one at the next chunk
+        boundary with status "cancelled"."""
+        self.cancelled.add(request_id)
+
+    def _make_run(self, **params):
+        if self._run_factory is not None:
+            return self._run_factory(**params)
+        from .run import Run
+        return Run(device=self.device, **params)
+
+    def _make_batch(self, runs):
+        if self._batch_factory is not None:
+            return self._batch_factory(runs)
+        from .run import Batch
+        return Batch(runs)
 
     def footprint(self, req: Request) -> int:
         p = B.mhd_default_params(**run_params(req, self.urms0, self.dtype, kernel=self.kernel,
@@ -109,30 +133,25 @@ class Server:
         return B.mhd_workspace_bytes(p) + 256
 
     def _admit(self, req: Request, now: float) -> None:
-        from .run import Run
-
         nbytes = self.footprint(req)
-        run = Run(device=self.device, **run_params(req, self.urms0, self.dtype, kernel=self.kernel,
-                                                    tile=self.tile))
+        run = self._make_run(**run_params(req, self.urms0, self.dtype, kernel=self.kernel, tile=self.tile))
         start(run, req)
         b0 = run.reduce(B.MHD_BRMS)
         self.active.append([run, req, req.steps, now, [0.0], [b0], nbytes])
         self.used += nbytes
 
-    def _retire(self, entry, now: float) -> None:
+    def _retire(self, entry, now: float, status: str = "ok") -> None:
         run, req, _, admitted, ts, bs, nbytes = entry
-        diag = run.diagnostics()
-        lam = fit_last(ts, bs, self.window) if len(ts) > 2 else float("nan")
+        diag = run.diagnostics() if status == "ok" else {}
+        lam = fit_last(ts, bs, self.window) if status == "ok" and len(ts) > 2 else float("nan")
         self.results.append(Result(req.id, req.n, req.steps, req.arrival, admitted, now, lam, diag,
-                                   list(ts), list(bs)))
+                                   list(ts), list(bs), status))
         run.close()
         self.used -= nbytes
 
     def serve(self, requests, realtime: bool = True) -> list[Result]:
         """Serves all requests; arrival times are honoured in wall time (scaled
         by time_scale) when realtime is True, otherwise all arrive at once."""
-        from .run import Batch
-
         pending = sorted(requests, key=lambda r: r.arrival)
         queue: list[Request] = []
         t0 = time.perf_counter()
@@ -143,6 +162,9 @@ class Server:
             while pending and (not realtime or pending[0].arrival * self.time_scale <= tn):
                 r = pending.pop(0)
                 queue.append(r)
+            if self.cancelled:
+                queue = [r for r in queue if r.id not in self.cancelled]
+                pending = [r for r in pending if r.id not in self.cancelled]
             while queue and len(self.active) < self.max_active:
                 need = self.footprint(queue[0])
                 if self.used + need > self.budget and self.active:
@@ -158,22 +180,31 @@ class Server:
             if ids != batch_ids:
                 if batch is not None:
                     batch.close()
-                batch = Batch([e[0] for e in self.active])
+                batch = self._make_batch([e[0] for e in self.active])
                 batch_ids = ids
             k = min(self.chunk, min(e[2] for e in self.active))
             batch.step(k)
+            ended = []
             for e in self.active:
                 e[2] -= k
-                tt, _, _ = e[0].time()
-                e[4].append(tt)
-                e[5].append(e[0].reduce(B.MHD_BRMS))
                 self.stepped_cells += k * e[0].cells
-            done = [e for e in self.active if e[2] == 0]
-            if done:
+                try:
+                    tt, _, _ = e[0].time()
+                    b = e[0].reduce(B.MHD_BRMS)
+                except B.MhdError as err:  # blew up: retire it, keep the others
+                    ended.append((e, f"failed: {err}"))
+                    continue
+                e[4].append(tt)
+                e[5].append(b)
+                if e[1].id in self.cancelled:
+                    ended.append((e, "cancelled"))
+                elif e[2] == 0:
+                    ended.append((e, "ok"))
+            if ended:
                 tn = now()
-                for e in done:
+                for e, status in ended:
                     self.active.remove(e)
-                    self._retire(e, tn)
+                    self._retire(e, tn, status)
         if batch is not None:
             batch.close()
         return self.results
@@ -183,6 +214,7 @@ def summarize(results, wall: float, stepped_cells: int) -> dict:
     lat = np.array([r.latency for r in results])
     return {
         "requests": len(results),
+        "failed": sum(1 for r in results if r.status != "ok"),
         "p50_latency_s": float(np.percentile(lat, 50)),
         "p99_latency_s": float(np.percentile(lat, 99)),
         "cell_updates_per_s": stepped_cells / wall,
