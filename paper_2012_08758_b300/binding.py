@@ -80,6 +80,7 @@ def lib():
             "mhd_alu_peak": (C.c_int, [C.c_int, vp, dp, dp]),
             "mhd_spectrum_shells": (C.c_int, [pp, C.POINTER(C.c_int)]),
             "mhd_set_seed_field": (C.c_int, [vp, C.c_uint64, C.c_double]),
+            "mhd_padding_check": (C.c_int, [vp, C.POINTER(C.c_longlong)]),
             "mhd_substep_plan": (C.c_int, [pp, C.c_int, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int),
                                            C.POINTER(C.c_int)]),
             "mhd_spectrum": (C.c_int, [vp, dp, C.c_int, C.POINTER(C.c_int)]),
@@ -250,6 +251,13 @@ def mhd_substep_plan(p: MhdParams, grid_ctas: int):
     buf = (C.c_int * max(1, 5 * n.value))()
     _check(lib().mhd_substep_plan(C.byref(p), int(grid_ctas), buf, n.value, C.byref(n), C.byref(g)))
     return np.frombuffer(buf, dtype=np.int32)[: 5 * n.value].reshape(n.value, 5).copy(), g.value
+
+
+def mhd_padding_check(ctx: int) -> int:
+    """Words of the state buffers' padding columns that are not NaN (0: intact)."""
+    n = C.c_longlong()
+    _check(lib().mhd_padding_check(C.c_void_p(ctx), C.byref(n)), ctx)
+    return n.value
 
 
 def mhd_spectrum_shells(p: MhdParams) -> int:

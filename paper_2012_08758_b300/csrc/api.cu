@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/mhd.h"
+#include "../../include/mhd_check.h"
 #include "../../include/mhd_plan.h"
 #include "mhd_internal.h"
 
@@ -312,6 +313,12 @@ Layout make_layout(const mhd_params *p_in) {
 
 }  // namespace
 
+namespace mhd {
+// padding canaries (kernels.cu)
+int launch_padding_check(int dtype, const void *q, int nf, long long fstride, int nx, int px, int py, int pz,
+                         unsigned long long *bad, cudaStream_t s);
+}  // namespace mhd
+
 struct mhd_ctx {
   mhd_params p;
   cudaStream_t stream;
@@ -556,6 +563,14 @@ int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t worksp
   cudaStream_t s = ctx->stream;
   int e = prepare_substep(p->dtype, p->kernel, p->tile);
   if (!e) e = (int)cudaMemsetAsync(ws, 0, L.total, s);
+  // state buffers and RK register: all NaN (0xFF bytes), then the zero state at
+  // the interior and ghost points of q[0]; the alignment padding keeps its NaN
+  // canaries (mhd_padding_check)
+  if (!e) e = (int)cudaMemsetAsync(ws + L.q[0], 0xFF, L.w + (size_t)NF * L.fstride * L.esz - L.q[0], s);
+  if (!e)
+    e = launch_seed_field(p->dtype, ws + L.q[0] + (size_t)4 * L.fstride * L.esz, L.fstride, p->nx, p->ny, p->nz,
+                          L.px, L.py, 0ull, 0.0, s);
+  if (!e) e = launch_halo(p->dtype, ws + L.q[0], NF, L.fstride, p->nx, p->ny, p->nz, L.px, L.py, s);
   for (int a = 0; a < 3 && !e; ++a)
     e = (int)cudaMemcpyAsync(ws + L.roots[a], roots[a].data(), roots[a].size(), cudaMemcpyHostToDevice, s);
   if (!e && L.nk)
@@ -627,7 +642,6 @@ int mhd_set_seed_field(mhd_ctx *ctx, uint64_t seed, double amp) {
   const RunDesc &R = ctx->h_run;
   char *dst = static_cast<char *>(R.q[0]);
   cudaStream_t s = ctx->stream;
-  CK(ctx, cudaMemsetAsync(dst, 0, (size_t)NF * R.fstride * ctx->L.esz, s));
   CK(ctx, launch_seed_field(ctx->p.dtype, dst + (size_t)4 * R.fstride * ctx->L.esz, R.fstride, R.nx, R.ny,
                             R.nz, R.px, R.py, seed, amp, s));
   CK(ctx, launch_halo(ctx->p.dtype, dst, NF, R.fstride, R.nx, R.ny, R.nz, R.px, R.py, s));
@@ -791,6 +805,22 @@ int mhd_forcing_draw(mhd_ctx *ctx, int64_t step, double *out) {
   CK(ctx, launch_forcing_draw(ctx->d_run, step, scratch, ctx->stream));
   CK(ctx, cudaMemcpyAsync(out, scratch, sizeof(double) * 13, cudaMemcpyDeviceToHost, ctx->stream));
   CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return MHD_OK;
+}
+
+int mhd_padding_check(mhd_ctx *ctx, long long *bad) {
+  if (!ctx) return fail(nullptr, MHD_EINVAL, "ctx is NULL");
+  if (!bad) return fail(ctx, MHD_EINVAL, "bad is NULL");
+  const RunDesc &R = ctx->h_run;
+  unsigned long long *cnt = reinterpret_cast<unsigned long long *>(ctx->ws + ctx->L.scratch);
+  cudaStream_t s = ctx->stream;
+  CK(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+  for (int b = 0; b < 2; ++b)
+    CK(ctx, launch_padding_check(ctx->p.dtype, R.q[b], NF, R.fstride, R.nx, R.px, R.py, R.pz, cnt, s));
+  unsigned long long h = 0;
+  CK(ctx, cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  *bad = (long long)h;
   return MHD_OK;
 }
 

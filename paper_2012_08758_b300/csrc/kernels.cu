@@ -356,14 +356,23 @@ __global__ void k_get_field(const T *src, H *dst, int nx, int ny, int nz, int px
   }
 }
 
-// The paper's initial magnetic field (Sec. 4): A = amp * N(0,1) independently
-// per component and interior point.  Normal number n = c * npts + e (component
-// c, point e = (k ny + j) nx + i) by Box-Muller from SplitMix64 outputs 2n and
-// 2n + 1 of the stream keyed by `seed` (u1 in (0, 1], u2 in [0, 1)), in FP64.
+// The paper's initial state (Sec. 4) at the interior points: ln rho = 0,
+// u = 0 and A = amp * N(0,1) independently per component and point.  A points
+// to field 4 of a state buffer; fields 0..3 are the NF - 3 fields before it.
+// Normal number n = c * npts + e (component c, point e = (k ny + j) nx + i)
+// by Box-Muller from SplitMix64 outputs 2n and 2n + 1 of the stream keyed by
+// `seed` (u1 in (0, 1], u2 in [0, 1)), in FP64.  Only interior points are
+// written, so the alignment padding keeps whatever it holds.
 template <typename T>
 __global__ void k_seed_field(T *A, long long fstride, int nx, int ny, int nz, int px, int py,
                              unsigned long long seed, double amp) {
   const long long npts = (long long)nx * ny * nz, total = 3 * npts;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < npts;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / ((long long)nx * ny));
+    const long long o = ((long long)(k + OZ) * py + (j + OY)) * px + (i + OX);
+    for (int f = 0; f < 4; ++f) A[(f - 4) * fstride + o] = T(0);
+  }
   const double TWO_PI = 6.283185307179586476925286766559;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < total;
        n += (long long)gridDim.x * blockDim.x) {
@@ -375,6 +384,28 @@ __global__ void k_seed_field(T *A, long long fstride, int nx, int ny, int nz, in
     const double g = sqrt(-2.0 * log(u1)) * cos(TWO_PI * u2);
     A[c * fstride + ((long long)(k + OZ) * py + (j + OY)) * px + (i + OX)] = T(amp * g);
   }
+}
+
+// Canary check of the alignment padding: counts the words of x-columns 0 and
+// nx + OX + RAD .. px - 1 of nf fields that are not NaN.  No kernel reads or
+// writes these columns; they are filled with NaN when a context is created.
+template <typename T>
+__global__ void k_padding_check(const T *q, int nf, long long fstride, int nx, int px, int py, int pz,
+                                unsigned long long *bad) {
+  const int first = nx + OX + RAD, ncols = 1 + (px - first);
+  const long long rows = (long long)nf * py * pz, total = rows * ncols;
+  unsigned long long cnt = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e % ncols);
+    const long long r = e / ncols;
+    const int f = (int)(r / ((long long)py * pz));
+    const long long row = r - (long long)f * py * pz;
+    const int x = c == 0 ? 0 : first + c - 1;
+    const T v = q[f * fstride + row * px + x];
+    cnt += isnan(v) ? 0ull : 1ull;
+  }
+  if (cnt) atomicAdd(bad, cnt);
 }
 
 static int conv_grid(long long total) {
@@ -403,6 +434,16 @@ int launch_seed_field(int dtype, void *A, long long fstride, int nx, int ny, int
     k_seed_field<float><<<g, 256, 0, s>>>((float *)A, fstride, nx, ny, nz, px, py, seed, amp);
   else
     k_seed_field<double><<<g, 256, 0, s>>>((double *)A, fstride, nx, ny, nz, px, py, seed, amp);
+  return (int)cudaGetLastError();
+}
+
+int launch_padding_check(int dtype, const void *q, int nf, long long fstride, int nx, int px, int py, int pz,
+                         unsigned long long *bad, cudaStream_t s) {
+  const int g = conv_grid((long long)nf * py * pz * (1 + px - (nx + OX + RAD)));
+  if (dtype == 0)
+    k_padding_check<float><<<g, 256, 0, s>>>((const float *)q, nf, fstride, nx, px, py, pz, bad);
+  else
+    k_padding_check<double><<<g, 256, 0, s>>>((const double *)q, nf, fstride, nx, px, py, pz, bad);
   return (int)cudaGetLastError();
 }
 

@@ -135,3 +135,9 @@ def test_substep_plan_covers_every_point_once(B, shape, grid, tile):
     # which the plan weights by their lower cost; faces weigh up to 1.16x
     if nx * ny * nz >= 128 ** 3 and nx % tw == 0 and ny % th == 0:
         assert planes.max() <= 1.15 * planes.mean()
+
+
+def test_padding_check_rejects_null(B):
+    import ctypes as C
+    n = C.c_longlong()
+    assert B.lib().mhd_padding_check(None, C.byref(n)) == B.MHD_EINVAL

@@ -359,6 +359,43 @@ def test_checkpoint_resume_is_bit_for_bit(dtype, tmp_path):
     b.close()
 
 
+@pytest.mark.parametrize("kernel,tile", [(2, 0), (1, 0), (2, 2), (2, 9)])
+@pytest.mark.parametrize("shape,dtype", [((32, 32, 32), "f32"), ((37, 23, 11), "f64"), ((12, 9, 1), "f32"),
+                                         ((16, 1, 1), "f64"), ((40, 8, 20), "f32")])
+def test_padding_canaries_survive_every_entry_point(shape, dtype, kernel, tile):
+    """The alignment padding of both state buffers holds NaN from creation on:
+    no kernel of any entry point (uploads, seed field, steps with forcing and
+    upwinding, RHS evaluation, diagnostics, B_rms, spectrum, batch steps,
+    downloads) writes there, and since every result stays finite none reads it."""
+    from paper_2012_08758_b300 import binding as B
+    from paper_2012_08758_b300.run import Batch
+    if dtype == "f64" and tile > 2:
+        pytest.skip("FP32 tile")
+    nx, ny, nz = shape
+    kw = dict(nx=nx, ny=ny, nz=nz, nu=0.01, eta=0.01, f0=0.05, sigma=1.0, kmin=1.0, kmax=2.0, seed=4,
+              dtype=dtype, kernel=kernel, tile=tile, upwind=1)
+    run = make_run(**kw)
+    assert B.mhd_padding_check(run.ctx) == 0
+    run.set_state(inputs.random_modes_state(nx, ny, nz, seed=5, amp=0.2))
+    run.step(3)
+    run.eval_rhs(step=3, dt_forcing=0.01)
+    d = run.diagnostics()
+    assert np.isfinite(run.reduce(B.MHD_BRMS)) and all(np.isfinite(v) for v in d.values())
+    if nx >= 2:
+        assert np.all(np.isfinite(run.spectrum()))
+    run.set_seed_field(7, 1e-3)
+    other = make_run(**kw)
+    other.set_state(inputs.random_modes_state(nx, ny, nz, seed=6, amp=0.2), step=1)
+    b = Batch([run, other])
+    b.step(4)
+    b.close()
+    for r in (run, other):
+        q, _, _ = r.get_state()
+        assert np.all(np.isfinite(q))
+        assert B.mhd_padding_check(r.ctx) == 0
+        r.close()
+
+
 def test_batch_is_bitwise_identical_to_alone():
     from paper_2012_08758_b300.run import Batch
     cfgs = [dict(nx=32, ny=32, nz=32, f0=0.02, sigma=1.0, seed=1, nu=4e-3, eta=4e-3),
