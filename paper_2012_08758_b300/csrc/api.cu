@@ -945,10 +945,12 @@ int mhd_eval_rhs(mhd_ctx *ctx, int64_t step, double dt_forcing, void *host_rhs, 
     CK(ctx, cudaMemcpyAsync(static_cast<char *>(host_rhs) + f * hb, staging, hb,
                             cudaMemcpyDeviceToHost, s));
   }
+  // the staging buffer held the other parity's state, which is dead between
+  // steps (the next substep rewrites its interior and ghost zones): refill it
+  // with NaN so the padding canaries hold again.  The step constants were
+  // overwritten too; the next prologue rewrites them.
+  CK(ctx, cudaMemsetAsync(staging, 0xFF, (size_t)NF * R.fstride * ctx->L.esz, s));
   CK(ctx, cudaStreamSynchronize(s));
-  // the staging buffer held the other parity's state: rebuild nothing (it is
-  // dead), but the step constants were overwritten; the next prologue
-  // rewrites them.
   return MHD_OK;
 }
 
