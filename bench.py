@@ -552,7 +552,7 @@ def run_tables(args):
     etas = [float(e) for e in args.tables_eta.split(",")] if args.tables_eta else None
     rows = [r for r in paper_tables() if r["n"] in grids and (etas is None or r["eta"] in etas)]
     kf = shell_mean_k(4.5, 5.5)
-    runs, series, live = [], [], []
+    runs, series, spectra, live = [], [], [], []
     for i, r in enumerate(rows):
         run = Run(n=r["n"], nu=r["eta"], eta=r["eta"], f0=args.tables_f0, kmin=4.5, kmax=5.5, sigma=r["sigma"],
                   seed=1000 + i, upwind=1, cfl=0.4)
@@ -560,6 +560,7 @@ def run_tables(args):
         d = run.diagnostics()
         runs.append(run)
         series.append([(0.0, d["brms"], d["urms"])])
+        spectra.append([run.spectrum()] if args.tables_spectra else [])
         live.append(i)
     status = ["ok"] * len(rows)
     t0 = time.perf_counter()
@@ -580,6 +581,8 @@ def run_tables(args):
                 continue
             t = runs[i].time()[0]
             series[i].append((t, d["brms"], d["urms"]))
+            if args.tables_spectra:
+                spectra[i].append(runs[i].spectrum())
             if t >= args.tables_tmax:
                 done.append(i)
         if done:
@@ -600,6 +603,9 @@ def run_tables(args):
         if status[i] == "ok" and m.sum() >= 3:
             res.update(lambda_=growth_rate(ts[m], bs[m]), rem=float(us[m].mean() / (r["eta"] * kf)),
                        window=[float(ts[m][0]), float(ts[m][-1])])
+            if args.tables_spectra:
+                E = np.array(spectra[i])[m]
+                res["lambda_k"] = {k: 0.5 * growth_rate(ts[m], E[:, k]) for k in (1, 5, 9) if k < E.shape[1]}
         out.append(res)
     print(json.dumps({"workload": f"growth rates at the setup of Tables 1-2, grids {grids}, t <= {args.tables_tmax}",
                       "f0": args.tables_f0, "k_f": kf, "steps": steps, "wall_s": wall, "rows": out}), flush=True)
@@ -730,6 +736,8 @@ def main():
     ap.add_argument("--tables-chunk", type=int, default=200)
     ap.add_argument("--tables-f0", type=float, default=0.029)
     ap.add_argument("--tables-eta", default="", help="comma-separated eta values to keep (default: all rows)")
+    ap.add_argument("--tables-spectra", action="store_true",
+                    help="also sample E_B(k) and fit the growth rates of channels k = 1, 5, 9 (Sec. 5)")
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 plane ring, 2 TMA")
     ap.add_argument("--tile", type=int, default=0, help="tile variant id (0: default)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU-baseline leg")
