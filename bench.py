@@ -550,12 +550,13 @@ def run_tables(args):
 
     grids = [int(g) for g in args.tables_grids.split(",")]
     etas = [float(e) for e in args.tables_eta.split(",")] if args.tables_eta else None
-    rows = [r for r in paper_tables() if r["n"] in grids and (etas is None or r["eta"] in etas)]
+    rows = [dict(r, realisation=s) for r in paper_tables() if r["n"] in grids and (etas is None or r["eta"] in etas)
+            for s in range(args.tables_seeds)]
     kf = shell_mean_k(4.5, 5.5)
     runs, series, spectra, live = [], [], [], []
     for i, r in enumerate(rows):
         run = Run(n=r["n"], nu=r["eta"], eta=r["eta"], f0=args.tables_f0, kmin=4.5, kmax=5.5, sigma=r["sigma"],
-                  seed=1000 + i, upwind=1, cfl=0.4)
+                  seed=1000 + i + 7919 * r["realisation"], upwind=1, cfl=0.4)
         run.set_state(inputs.seed_field_state(r["n"], seed=i, amp=1e-5))
         d = run.diagnostics()
         runs.append(run)
@@ -599,7 +600,7 @@ def run_tables(args):
         if len(sat):
             m &= ts < ts[sat[0]]
         res = dict(sigma=r["sigma"], n=r["n"], eta=r["eta"], lambda_paper=r["lam"], rem_paper=r["rem"],
-                   status=status[i], t_end=float(ts[-1]))
+                   realisation=r["realisation"], status=status[i], t_end=float(ts[-1]))
         if status[i] == "ok" and m.sum() >= 3:
             res.update(lambda_=growth_rate(ts[m], bs[m]), rem=float(us[m].mean() / (r["eta"] * kf)),
                        window=[float(ts[m][0]), float(ts[m][-1])])
@@ -736,6 +737,7 @@ def main():
     ap.add_argument("--tables-chunk", type=int, default=200)
     ap.add_argument("--tables-f0", type=float, default=0.029)
     ap.add_argument("--tables-eta", default="", help="comma-separated eta values to keep (default: all rows)")
+    ap.add_argument("--tables-seeds", type=int, default=1, help="forcing realisations per table row")
     ap.add_argument("--tables-spectra", action="store_true",
                     help="also sample E_B(k) and fit the growth rates of channels k = 1, 5, 9 (Sec. 5)")
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 plane ring, 2 TMA")
