@@ -189,7 +189,7 @@ def run_reference(args):
         return 0
     # the oracle's cost per point does not depend on the grid, so each step is
     # a bounded sample: whole steps of the 64^3 version of the same workload
-    cb = cpu_baseline(seconds=max(5.0, 2.0 * args.steps), n=64)
+    cb = cpu_baseline(seconds=min(60.0, max(5.0, 0.1 * args.steps)), n=64)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * args.n ** 3 / cb["value"], "higher_is_better": True, "scaling": "weak",
