@@ -556,7 +556,7 @@ def run_tables(args):
     runs, series, spectra, live = [], [], [], []
     for i, r in enumerate(rows):
         run = Run(n=r["n"], nu=r["eta"], eta=r["eta"], f0=args.tables_f0, kmin=4.5, kmax=5.5, sigma=r["sigma"],
-                  seed=1000 + i + 7919 * r["realisation"], upwind=1, cfl=0.4)
+                  seed=1000 + i + 7919 * r["realisation"], upwind=args.tables_upwind, cfl=0.4)
         run.set_state(inputs.seed_field_state(r["n"], seed=i, amp=1e-5))
         d = run.diagnostics()
         runs.append(run)
@@ -601,6 +601,8 @@ def run_tables(args):
             m &= ts < ts[sat[0]]
         res = dict(sigma=r["sigma"], n=r["n"], eta=r["eta"], lambda_paper=r["lam"], rem_paper=r["rem"],
                    realisation=r["realisation"], status=status[i], t_end=float(ts[-1]))
+        if args.tables_series:
+            res["series"] = {"t": ts.tolist(), "brms": bs.tolist(), "urms": us.tolist()}
         if status[i] == "ok" and m.sum() >= 3:
             res.update(lambda_=growth_rate(ts[m], bs[m]), rem=float(us[m].mean() / (r["eta"] * kf)),
                        window=[float(ts[m][0]), float(ts[m][-1])])
@@ -738,6 +740,8 @@ def main():
     ap.add_argument("--tables-f0", type=float, default=0.029)
     ap.add_argument("--tables-eta", default="", help="comma-separated eta values to keep (default: all rows)")
     ap.add_argument("--tables-seeds", type=int, default=1, help="forcing realisations per table row")
+    ap.add_argument("--tables-series", action="store_true", help="include the (t, B_rms, u_rms) samples")
+    ap.add_argument("--tables-upwind", type=int, default=1, help="upwinding of the continuity equation (0/1)")
     ap.add_argument("--tables-spectra", action="store_true",
                     help="also sample E_B(k) and fit the growth rates of channels k = 1, 5, 9 (Sec. 5)")
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 plane ring, 2 TMA")
