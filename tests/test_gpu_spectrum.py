@@ -89,3 +89,21 @@ def test_channel_growth_rates_fp32_gpu_match_fp64_oracle():
     for k in top:
         lam_o = 0.5 * O.growth_rate(t_o[half:], e_o[half:, k])
         assert abs(lam_g[k] - lam_o) <= 0.01 * abs(lam_o) + 1e-6, (k, lam_g[k], lam_o)
+
+
+@pytest.mark.slow
+def test_full_size_256_spectrum_matches_oracle():
+    """The bench workload's grid (256^3, FP32): every shell against the FP64
+    oracle's spectrum of the same state (the oracle's curl and numpy FFT take
+    a few seconds), within 1e-5 of the total magnetic energy."""
+    n = 256
+    kw = dict(nx=n, ny=n, nz=n, dtype="f32")
+    q = inputs.random_modes_state(n, n, n, seed=40, amp=0.2, kmax=8, nmodes=12) + \
+        inputs.noise_state(n, n, n, seed=41, amp=1e-3)
+    run = make_run(**kw)
+    run.set_state(q)
+    got = run.spectrum()
+    run.close()
+    want = O.spectrum(oracle_params(**kw), q)
+    assert got.shape == want.shape == (223,)
+    assert np.abs(got - want).max() <= 1e-5 * want.sum()
