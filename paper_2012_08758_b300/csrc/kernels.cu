@@ -379,9 +379,12 @@ __global__ void k_seed_field(T *A, long long fstride, int nx, int ny, int nz, in
     const int c = (int)(n / npts);
     const long long e = n - c * npts;
     const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / ((long long)nx * ny));
-    const double u1 = (double)((splitmix64(seed, 2ull * (unsigned long long)n) >> 11) + 1ull) * 0x1.0p-53;
-    const double u2 = (double)(splitmix64(seed, 2ull * (unsigned long long)n + 1ull) >> 11) * 0x1.0p-53;
-    const double g = sqrt(-2.0 * log(u1)) * cos(TWO_PI * u2);
+    double g = 0.0;
+    if (amp != 0.0) {  // the zero state (context creation) needs no random numbers
+      const double u1 = (double)((splitmix64(seed, 2ull * (unsigned long long)n) >> 11) + 1ull) * 0x1.0p-53;
+      const double u2 = (double)(splitmix64(seed, 2ull * (unsigned long long)n + 1ull) >> 11) * 0x1.0p-53;
+      g = sqrt(-2.0 * log(u1)) * cos(TWO_PI * u2);
+    }
     A[c * fstride + ((long long)(k + OZ) * py + (j + OY)) * px + (i + OX)] = T(amp * g);
   }
 }
