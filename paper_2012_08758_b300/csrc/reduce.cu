@@ -108,31 +108,16 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS) k_curl(const RunDesc *__rest
   for (int a = 0; a < 3; ++a)
     for (int s = 0; s < 4; ++s) w[a][s] = T(W1(s) * R.inv_h[a]);
   const int x = tile.x0 + threadIdx.x, y = tile.y0 + threadIdx.y;
-  if (x >= R.nx || y >= R.ny || tile.z1 <= tile.z0) return;
+  if (x >= R.nx || y >= R.ny) return;
   const T *Ax = q + 4 * fs, *Ay = q + 5 * fs, *Az = q + 6 * fs;
-  // z-pencils of A_x, A_y (planes z-3 .. z+3): each plane is loaded once
-  long long c = ((long long)(tile.z0 + OZ) * R.py + (y + OY)) * R.px + (x + OX);
-  T ax[7], ay[7];
-#pragma unroll
-  for (int k = 0; k < 7; ++k) {
-    ax[k] = Ax[c + (k - 3) * sz];
-    ay[k] = Ay[c + (k - 3) * sz];
-  }
-  for (int z = tile.z0; z < tile.z1; ++z, c += sz) {
-    const T dzAy = d1_vals(ay[4], ay[2], ay[5], ay[1], ay[6], ay[0], w[2]);
-    const T dzAx = d1_vals(ax[4], ax[2], ax[5], ax[1], ax[6], ax[0], w[2]);
-    B[c] = d1_at<T, 1>(Az, c, sy, w[1]) - dzAy;
-    B[fs + c] = dzAx - d1_at<T, 0>(Az, c, 1, w[0]);
+  // z-neighbours come from L1 (the block sweeps its tile along z); register
+  // pencils of A_x, A_y measured 2.4x slower here: at 92 registers only one
+  // 12-warp block fits an SM instead of four
+  for (int z = tile.z0; z < tile.z1; ++z) {
+    const long long c = ((long long)(z + OZ) * R.py + (y + OY)) * R.px + (x + OX);
+    B[c] = d1_at<T, 1>(Az, c, sy, w[1]) - d1_at<T, 2>(Ay, c, sz, w[2]);
+    B[fs + c] = d1_at<T, 2>(Ax, c, sz, w[2]) - d1_at<T, 0>(Az, c, 1, w[0]);
     B[2 * fs + c] = d1_at<T, 0>(Ay, c, 1, w[0]) - d1_at<T, 1>(Ax, c, sy, w[1]);
-    if (z + 1 < tile.z1) {  // plane z + 4 (at most the last ghost plane, z1 + 2)
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        ax[k] = ax[k + 1];
-        ay[k] = ay[k + 1];
-      }
-      ax[6] = Ax[c + 4 * sz];
-      ay[6] = Ay[c + 4 * sz];
-    }
   }
 }
 
