@@ -10,6 +10,7 @@
 #include "../../include/mhd.h"
 #include "mhd_internal.h"
 #include "physics.cuh"
+#include "step_device.cuh"
 
 namespace mhd {
 namespace {
@@ -135,14 +136,8 @@ __global__ void __launch_bounds__(NA_THREADS)
   const double vals[NPART] = {su2, sb2, sk, sm, mu, mb, mv, md};
   const int t = threadIdx.x;
   for (int v = 0; v < NPART; ++v) {
-    __syncthreads();
-    sh[t] = vals[v];
-    __syncthreads();
-    for (int s = NA_THREADS / 2; s > 0; s >>= 1) {
-      if (t < s) sh[t] = v < 4 ? sh[t] + sh[t + s] : fmax(sh[t], sh[t + s]);
-      __syncthreads();
-    }
-    if (t == 0) scratch[NA_HEADER + (long long)blockIdx.x * NPART + v] = __double_as_longlong(sh[0]);
+    const double r = v < 4 ? block_sum(vals[v], sh) : block_max(vals[v], sh);
+    if (t == 0) scratch[NA_HEADER + (long long)blockIdx.x * NPART + v] = __double_as_longlong(r);
   }
   __threadfence();
   __syncthreads();

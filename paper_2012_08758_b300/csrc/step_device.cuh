@@ -99,43 +99,58 @@ __device__ __forceinline__ void make_coeffs(const RunDesc &R, long long draw_ste
 }
 
 // ---------------------------------------------------------------------------
-// Block reduction helpers (fixed tree order: deterministic).
+// Block reduction helpers (fixed order: deterministic).
 // ---------------------------------------------------------------------------
-// Any block size: the entries above the largest power of two p2 <= n are
-// folded onto the first ones, then a halving tree; the order is fixed.
-__device__ __forceinline__ double block_sum(double v, double *sh) {
-  const int n = blockDim.x * blockDim.y, t = threadIdx.y * blockDim.x + threadIdx.x;
-  int p2 = 1;
-  while (2 * p2 <= n) p2 *= 2;
-  __syncthreads();
-  sh[t] = v;
-  __syncthreads();
-  if (t < n - p2) sh[t] += sh[t + p2];
-  __syncthreads();
-  for (int s = p2 / 2; s > 0; s >>= 1) {
-    if (t < s) sh[t] += sh[t + s];
-    __syncthreads();
-  }
-  return sh[0];
-}
-
+// A butterfly of warp shuffles inside each warp, the warp results through
+// shared memory, then the same butterfly in the first warp.  Every lane of a
+// butterfly ends with the same value (both combining operations are
+// commutative), and the order is fixed, so the result is bitwise
+// reproducible.  Blocks are whole warps (every launch uses 32 x TY, 256 or
+// 1024 threads); sh holds at least one double per warp.
 __device__ __forceinline__ double nan_max(double a, double b) {
   return (isnan(a) || isnan(b)) ? (a + b) : fmax(a, b);
 }
 
-__device__ __forceinline__ double block_max(double v, double *sh) {
-  const int n = blockDim.x * blockDim.y, t = threadIdx.y * blockDim.x + threadIdx.x;
-  int p2 = 1;
-  while (2 * p2 <= n) p2 *= 2;
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = nan_max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+  const int nw = (blockDim.x * blockDim.y) >> 5, t = threadIdx.y * blockDim.x + threadIdx.x;
+  v = warp_sum(v);
+  __syncthreads();  // sh[0] may still be read after the previous call
+  if ((t & 31) == 0) sh[t >> 5] = v;
   __syncthreads();
-  sh[t] = v;
-  __syncthreads();
-  if (t < n - p2) sh[t] = nan_max(sh[t], sh[t + p2]);
-  __syncthreads();
-  for (int s = p2 / 2; s > 0; s >>= 1) {
-    if (t < s) sh[t] = nan_max(sh[t], sh[t + s]);
-    __syncthreads();
+  if (t < 32) {
+    const double w = warp_sum(t < nw ? sh[t] : 0.0);
+    __syncwarp();
+    if (t == 0) sh[0] = w;
   }
+  __syncthreads();
+  return sh[0];
+}
+
+// Maximum with NaN kept (a non-finite partial poisons the result).
+__device__ __forceinline__ double block_max(double v, double *sh) {
+  const int nw = (blockDim.x * blockDim.y) >> 5, t = threadIdx.y * blockDim.x + threadIdx.x;
+  v = warp_max(v);
+  __syncthreads();
+  if ((t & 31) == 0) sh[t >> 5] = v;
+  __syncthreads();
+  if (t < 32) {
+    const double w = warp_max(t < nw ? sh[t] : -INFINITY);
+    __syncwarp();
+    if (t == 0) sh[0] = w;
+  }
+  __syncthreads();
   return sh[0];
 }
 
