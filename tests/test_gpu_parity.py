@@ -288,8 +288,12 @@ def test_full_size_256_sampled_rhs_and_beltrami():
 # --------------------------------------------------------------------------
 # Diagnostics, state transfer, batching, determinism, failure detection
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-5)])
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-14), ("f32", 1e-5)])
 def test_diagnostics_match_oracle(dtype, tol):
+    """Volume means and maxima against the oracle.  In FP64 the per-point
+    values round like the oracle's and the fixed-order FP64 sums (per-thread
+    z sums, warp butterflies, tile partials) stay within a few ulp of its
+    pairwise sums: 1e-14 relative (measured worst 4e-16 over five grids)."""
     kw = dict(nx=30, ny=20, nz=18, dtype=dtype)
     q = inputs.random_modes_state(30, 20, 18, seed=6, amp=0.4)
     run = make_run(**kw)
@@ -315,7 +319,7 @@ def test_fused_brms_equals_full_diagnostics(dtype):
     fast = run.reduce(B.MHD_BRMS)
     full = run.diagnostics()["brms"]
     assert fast == pytest.approx(full, rel=1e-13)
-    assert fast == pytest.approx(O.diagnostics(oracle_params(**kw), q)["brms"], rel=1e-12 if dtype == "f64" else 1e-5)
+    assert fast == pytest.approx(O.diagnostics(oracle_params(**kw), q)["brms"], rel=1e-14 if dtype == "f64" else 1e-5)
     run.close()
 
 
