@@ -29,6 +29,7 @@ namespace {
 
 constexpr size_t ALIGN = 256;
 constexpr int TARGET_CTAS = 2 * 2 * 148;  // ~two waves of two CTAs per SM on 148 SMs
+constexpr int RESIDENT_CTAS = 2 * 148;     // reduction blocks resident at once (two per SM)
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Byte offsets of every region of a context's device workspace.
@@ -72,13 +73,26 @@ int num_sms() {
 
 // Tiles of one run: TX x TY columns, z split into chunks so that the launch
 // covers the GPU with a couple of waves; chunks of at least 8 planes keep the
-// re-read z-halo (6 planes per chunk) small.
+// re-read z-halo (6 planes per chunk) small.  Among the splits into nch0 ..
+// 2 nch0 + 2 chunks (nch0 from the target CTA count) the one with the least
+// estimated time is taken: whole waves of RESIDENT_CTAS blocks times the
+// planes a block reads (chunk + 6), so the last wave is not left mostly idle.
 std::vector<Tile> make_tiles(int nx, int ny, int nz, int tw, int th, int target_ctas) {
   const int ntx = (nx + tw - 1) / tw, nty = (ny + th - 1) / th;
-  const int ncol = ntx * nty;
-  int nch = std::max(1, (target_ctas + ncol - 1) / ncol);
-  int chunk = std::max(8, (nz + nch - 1) / nch);
-  chunk = std::min(chunk, nz);
+  const long long ncol = (long long)ntx * nty;
+  const int nch0 = (int)std::max(1LL, (target_ctas + ncol - 1) / ncol);
+  auto chunk_of = [&](int nch) { return std::min(nz, std::max(8, (nz + nch - 1) / nch)); };
+  int chunk = chunk_of(nch0);
+  long long best = -1;
+  for (int nch = nch0; nch <= 2 * nch0 + 2; ++nch) {
+    const int c = chunk_of(nch);
+    const long long tiles = ncol * ((nz + c - 1) / c);
+    const long long cost = (tiles + RESIDENT_CTAS - 1) / RESIDENT_CTAS * (c + 2 * RAD);
+    if (best < 0 || cost < best) {
+      best = cost;
+      chunk = c;
+    }
+  }
   std::vector<Tile> t;
   int slot = 0;
   for (int z0 = 0; z0 < nz; z0 += chunk)
