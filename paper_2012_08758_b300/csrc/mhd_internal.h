@@ -44,6 +44,7 @@ struct StepCoeffs {
 // Everything a kernel needs to know about one run, resident in device memory.
 struct RunDesc {
   CUtensorMap tmap[2];      // TMA maps of q[0], q[1]: 4-D (x, y, z, field), box of one z-plane
+  CUtensorMap tmapA[2];     // the same maps with a box of the three A fields only
   int nx, ny, nz;
   int px, py, pz;           // padded extents; px is the row pitch
   long long fstride;        // elements per field (px * py * pz)
@@ -114,6 +115,8 @@ int launch_get_field(int dtype, int host_dtype, const void *src_field, void *dst
 // B_rms of the run's current state into diag[1] (curl and sum in one pass)
 int launch_brms(int dtype, const RunDesc *run_dev, const Tile *tiles, int ntiles, int tw, int th,
                 cudaStream_t s);
+// TMA variant of launch_brms for runs on the TMA kernel (same tiles and order).
+int tma_launch_brms(int dtype, int tile, const RunDesc *run_dev, const Tile *tiles, int ntiles, cudaStream_t s);
 // B = curl A of the run's current state into fields 0..2 of its w buffer
 // (interior points only).
 int launch_curl(int dtype, const RunDesc *run_dev, const Tile *tiles, int ntiles, int tw, int th,

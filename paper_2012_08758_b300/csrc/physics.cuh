@@ -153,6 +153,14 @@ __device__ __forceinline__ void rhs_point(const Derivs<T> &d, const C &c, const 
   }
 }
 
+// First derivative from the samples at offsets +-1, +-2, +-3 with the
+// weights w[1..3] of one axis (one expression shared by every reduction, so
+// they all see bit-identical B).
+template <typename T>
+__device__ __forceinline__ T d1_vals(T p1, T m1, T p2, T m2, T p3, T m3, const T *w) {
+  return w[1] * (p1 - m1) + w[2] * (p2 - m2) + w[3] * (p3 - m3);
+}
+
 // Complex product helpers for the forcing phase.
 template <typename T>
 struct Cplx {

@@ -14,13 +14,6 @@
 
 namespace mhd {
 
-// First derivative from the samples at offsets +-1, +-2, +-3 (one expression
-// shared by every reduction, so they all see bit-identical B).
-template <typename T>
-__device__ __forceinline__ T d1_vals(T p1, T m1, T p2, T m2, T p3, T m3, const T *w) {
-  return w[1] * (p1 - m1) + w[2] * (p2 - m2) + w[3] * (p3 - m3);
-}
-
 template <typename T, int AX>
 __device__ __forceinline__ T d1_at(const T *f, long long c, long long stride, const T *w) {
   return d1_vals(f[c + stride], f[c - stride], f[c + 2 * stride], f[c - 2 * stride], f[c + 3 * stride],
