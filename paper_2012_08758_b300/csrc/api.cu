@@ -259,10 +259,9 @@ EncodeTiledFn encode_fn() {
 }
 
 // 4-D map of one state buffer: (x: px, y: py, z: pz, field: 7), box = one
-// z-plane of a (tw+8) x (th+6) tile of `nbox` consecutive fields (all seven,
-// or the three A fields for the B_rms reduction).
+// z-plane of a (tw+8) x (th+6) tile of all seven fields.
 int encode_state_map(CUtensorMap *m, void *base, size_t esz, int px, int py, int pz, int tw, int th,
-                     std::string *why, int nbox = NF) {
+                     std::string *why) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) {
     *why = "cuTensorMapEncodeTiled is not available from the driver";
@@ -271,7 +270,7 @@ int encode_state_map(CUtensorMap *m, void *base, size_t esz, int px, int py, int
   const cuuint64_t dims[4] = {(cuuint64_t)px, (cuuint64_t)py, (cuuint64_t)pz, (cuuint64_t)NF};
   const cuuint64_t strides[3] = {(cuuint64_t)px * esz, (cuuint64_t)px * py * esz,
                                  (cuuint64_t)px * py * pz * esz};
-  const cuuint32_t box[4] = {(cuuint32_t)(tw + 8), (cuuint32_t)(th + 2 * RAD), 1u, (cuuint32_t)nbox};
+  const cuuint32_t box[4] = {(cuuint32_t)(tw + 8), (cuuint32_t)(th + 2 * RAD), 1u, (cuuint32_t)NF};
   const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
   CUresult r = fn(m, esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, base,
                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -529,8 +528,7 @@ int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t worksp
   if (p->kernel == MHD_KERNEL_TMA) {
     std::string why;
     for (int b = 0; b < 2; ++b)
-      if (encode_state_map(&R.tmap[b], R.q[b], L.esz, L.px, L.py, L.pz, L.tw, L.th, &why) ||
-          encode_state_map(&R.tmapA[b], R.q[b], L.esz, L.px, L.py, L.pz, L.tw, L.th, &why, 3)) {
+      if (encode_state_map(&R.tmap[b], R.q[b], L.esz, L.px, L.py, L.pz, L.tw, L.th, &why)) {
         fail(ctx, MHD_ECUDA, "%s", why.c_str());
         return cleanup(MHD_ECUDA);
       }
@@ -779,8 +777,10 @@ int mhd_reduce(mhd_ctx *ctx, int kind, double *out) {
   if (kind < 0 || kind >= MHD_NREDUCE) return fail(ctx, MHD_EINVAL, "unknown reduction kind %d", kind);
   if (!out) return fail(ctx, MHD_EINVAL, "out is NULL");
   if (kind == MHD_BRMS) {  // one fused pass: no stored B, no halo, no other sums
+    // TMA runs: the prologue sweep in B_rms mode, which also caches the CFL
+    // maximum of this state, so the next step's prologue sweeps nothing
     if (ctx->p.kernel == MHD_KERNEL_TMA)
-      CK(ctx, tma_launch_brms(ctx->p.dtype, ctx->p.tile, ctx->d_run, ctx->d_tiles, ctx->ntiles, ctx->stream));
+      CK(ctx, tma_launch_prologue(ctx->p.dtype, ctx->p.tile, ctx->d_run, ctx->d_tiles, ctx->ntiles, ctx->stream, 1));
     else
       CK(ctx, launch_brms(ctx->p.dtype, ctx->d_run, ctx->d_tiles, ctx->ntiles, ctx->L.tw, ctx->L.th, ctx->stream));
     CK(ctx, cudaMemcpyAsync(out, ctx->h_run.diag + 1, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));

@@ -739,7 +739,12 @@ __host__ __device__ constexpr int pro_stages() {
   return TmaShape<T, TY>::STAGE_BYTES * 6 <= 110 * 1024 ? 6 : 5;
 }
 
-template <typename T, int TY>
+// MODE 0: the step prologue.  MODE 1: the same sweep as a B_rms reduction of
+// the current state (|B|^2 summed in FP64 per point, in the tile, thread-z,
+// block and tile order of every other B_rms reduction); its CFL maximum is
+// kept in the clock, tagged with the step, and the prologue of that step
+// takes it instead of sweeping the state again.
+template <typename T, int TY, int MODE>
 __global__ void __launch_bounds__(32 * TY, 2)
     k_prologue_tma(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles) {
   using SH = TmaShape<T, TY>;
@@ -752,8 +757,9 @@ __global__ void __launch_bounds__(32 * TY, 2)
   const Tile tile = tiles[blockIdx.x];
   const RunDesc &R = runs[tile.run];
   const long long step = R.clock->step;
-  double vmax = 0.0;
-  if (R.dt_fixed <= 0.0) {
+  const bool cached = MODE == 0 && R.clock->cache_tag == step + 1;
+  double vmax = 0.0, sb2 = 0.0;
+  if (MODE == 1 || (R.dt_fixed <= 0.0 && !cached)) {
     if (tid == 0) {
       for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
       mbar_fence_init();
@@ -803,13 +809,12 @@ __global__ void __launch_bounds__(32 * TY, 2)
       const bool ok = mbar_wait(&bars[sl], (uint32_t)((p / NS) & 1));
       const T *o = reinterpret_cast<const T *>(smem + sl * SH::STAGE_BYTES) + cxy;
       auto dx = [&](int f) {
-        return w[0][1] * (o[f * FIELD + 1] - o[f * FIELD - 1]) + w[0][2] * (o[f * FIELD + 2] - o[f * FIELD - 2]) +
-               w[0][3] * (o[f * FIELD + 3] - o[f * FIELD - 3]);
+        const T *r = o + f * FIELD;
+        return d1_vals(r[1], r[-1], r[2], r[-2], r[3], r[-3], w[0]);
       };
       auto dy = [&](int f) {
-        return w[1][1] * (o[f * FIELD + SX] - o[f * FIELD - SX]) +
-               w[1][2] * (o[f * FIELD + 2 * SX] - o[f * FIELD - 2 * SX]) +
-               w[1][3] * (o[f * FIELD + 3 * SX] - o[f * FIELD - 3 * SX]);
+        const T *r = o + f * FIELD;
+        return d1_vals(r[SX], r[-SX], r[2 * SX], r[-2 * SX], r[3 * SX], r[-3 * SX], w[1]);
       };
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
@@ -832,14 +837,16 @@ __global__ void __launch_bounds__(32 * TY, 2)
         dl[3][5] = exp(-o[0]);
       }
       if (p >= 2 * RAD && ok && active) {  // output plane p-3
-        const T dzAx = w[2][1] * (ax[4] - ax[2]) + w[2][2] * (ax[5] - ax[1]) + w[2][3] * (ax[6] - ax[0]);
-        const T dzAy = w[2][1] * (ay[4] - ay[2]) + w[2][2] * (ay[5] - ay[1]) + w[2][3] * (ay[6] - ay[0]);
+        const T dzAx = d1_vals(ax[4], ax[2], ax[5], ax[1], ax[6], ax[0], w[2]);
+        const T dzAy = d1_vals(ay[4], ay[2], ay[5], ay[1], ay[6], ay[0], w[2]);
         const T Bx = dl[0][0] - dzAy;
         const T By = dzAx - dl[0][1];
         const T Bz = dl[0][2] - dl[0][3];
-        const T v = dl[0][4] + sqrt(cs2 + (Bx * Bx + By * By + Bz * Bz) * dl[0][5]);
+        const T b2 = norm2_rn(Bx, By, Bz);
+        const T v = dl[0][4] + sqrt(cs2 + b2 * dl[0][5]);
         bad |= isnan(v);
         vm = fmax(vm, v);
+        if constexpr (MODE == 1) sb2 += (double)b2;
       }
       if (__syncthreads_or(!ok)) {
         failed = true;
@@ -853,144 +860,38 @@ __global__ void __launch_bounds__(32 * TY, 2)
         for (int q = p; q < issued; ++q) mbar_wait(&bars[q % NS], (uint32_t)((q / NS) & 1));
       }
       vmax = __longlong_as_double(0x7ff8000000000000ll);  // NaN: the step is marked bad
+      sb2 = vmax;
     }
     vmax = block_max(vmax, sh);
+  }
+  if constexpr (MODE == 1) {
+    const double red = block_sum(sb2, sh);
+    if (tid == 0) {
+      R.partials[(long long)tile.slot * NPART] = vmax;
+      R.partials[(long long)tile.slot * NPART + 1] = red;
+    }
+    if (!last_tile_done(&R.counter[2], R.ntiles, &flag)) return;
+    // the CFL maximum as finalize_step would form it, and the |B|^2 sum
+    const int nthr = 32 * TY;
+    double v = 0.0, sum = 0.0;
+    for (int t = tid; t < R.ntiles; t += nthr) {
+      const double pm = __ldcg(&R.partials[(long long)t * NPART]);
+      v = isfinite(pm) ? fmax(v, pm) : __longlong_as_double(0x7ff8000000000000ll);
+      if (!isfinite(pm)) break;
+    }
+    for (int t = tid; t < R.ntiles; t += nthr) sum += __ldcg(&R.partials[(long long)t * NPART + 1]);
+    v = block_max(v, sh);
+    sum = block_sum(sum, sh);
+    if (tid != 0) return;
+    R.diag[1] = sqrt(sum / ((double)R.nx * R.ny * R.nz));
+    R.clock->cache_vmax = v;
+    R.clock->cache_tag = step + 1;
+    R.counter[2] = 0u;
+    return;
   }
   if (tid == 0) R.partials[(long long)tile.slot * NPART] = vmax;
   if (!last_tile_done(&R.counter[0], R.ntiles, &flag)) return;
   finalize_step(R, step, 1, sh);
-}
-
-// ---------------------------------------------------------------------------
-// B_rms reduction, TMA variant (runs on the TMA kernel): B = curl A with the
-// first-derivative stencil and |B|^2 summed in FP64, with the tiles,
-// per-point expression, per-thread z order, block reduction and tile order
-// of k_brms, so it returns the same value.  Only the three A fields are
-// staged: each z-plane of A_x, A_y, A_z (with x/y halos) arrives by one TMA
-// copy, up to NS-1 planes ahead; the x/y derivatives are taken while a plane
-// is the lead plane and wait three planes in registers for the
-// z-derivatives of A_x, A_y, which come from register pencils.
-// ---------------------------------------------------------------------------
-constexpr int BRMS_STAGES = 8;
-
-template <typename T, int TY>
-__host__ __device__ constexpr int brms_stage_bytes() {
-  return (3 * TmaShape<T, TY>::FIELD * (int)sizeof(T) + 127) / 128 * 128;
-}
-
-template <typename T, int TY>
-__global__ void __launch_bounds__(32 * TY, 2)
-    k_brms_tma(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles) {
-  using SH = TmaShape<T, TY>;
-  constexpr int TX = SH::TX, SX = SH::SX, FIELD = SH::FIELD, NS = BRMS_STAGES, P = NS - 1;
-  constexpr int STAGE = brms_stage_bytes<T, TY>();
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ double sh[32 * TY];
-  __shared__ int flag;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * STAGE);
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-  const Tile tile = tiles[blockIdx.x];
-  const RunDesc &R = runs[tile.run];
-  if (tid == 0) {
-    for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
-    mbar_fence_init();
-  }
-  __syncthreads();
-  const CUtensorMap *map = &R.tmapA[R.clock->step & 1];
-  const int npl = (tile.z1 - tile.z0) + 2 * RAD;  // planes z0-3 .. z1+2
-  auto issue = [&](int p) {
-    const int sl = p % NS;
-    mbar_arrive_expect_tx(&bars[sl], (uint32_t)(3 * FIELD * sizeof(T)));
-    tma_load_4d(smem + sl * STAGE, map, &bars[sl], tile.x0, tile.y0, tile.z0 + p, 4);
-  };
-  int issued = 0;
-  if (tid == 0) {
-    issued = npl < P ? npl : P;
-    for (int p = 0; p < issued; ++p) issue(p);
-  }
-  T w[3][4];
-  for (int a = 0; a < 3; ++a)
-    for (int s = 0; s < 4; ++s) w[a][s] = T(W1(s) * R.inv_h[a]);
-  const int x = tile.x0 + tx, y = tile.y0 + ty;
-  const bool active = x < R.nx && y < R.ny;
-  const int cxy = (ty + RAD) * SX + tx + 4;
-  // pencils of A_x, A_y over planes p-6 .. p; delay line of the lead-plane
-  // derivatives (d_y A_z, d_x A_z, d_x A_y, d_y A_x) of planes p-3 .. p
-  T ax[7], ay[7], dl[4][4];
-#pragma unroll
-  for (int k = 0; k < 7; ++k) ax[k] = ay[k] = T(0);
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) dl[k][v] = T(0);
-  double sb2 = 0.0;
-  bool failed = false;
-  int p = 0;
-  for (; p < npl; ++p) {
-    if (tid == 0 && p + P < npl) {
-      fence_proxy_async_smem();
-      issue(p + P);  // into the stage of plane p-1, released at the end of the last iteration
-      issued = p + P + 1;
-    }
-    const int sl = p % NS;
-    const bool ok = mbar_wait(&bars[sl], (uint32_t)((p / NS) & 1));
-    // stage fields: 0 = A_x, 1 = A_y, 2 = A_z
-    const T *o = reinterpret_cast<const T *>(smem + sl * STAGE) + cxy;
-    auto dx = [&](int f) {
-      const T *r = o + f * FIELD;
-      return d1_vals(r[1], r[-1], r[2], r[-2], r[3], r[-3], w[0]);
-    };
-    auto dy = [&](int f) {
-      const T *r = o + f * FIELD;
-      return d1_vals(r[SX], r[-SX], r[2 * SX], r[-2 * SX], r[3 * SX], r[-3 * SX], w[1]);
-    };
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      ax[k] = ax[k + 1];
-      ay[k] = ay[k + 1];
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) dl[k][v] = dl[k + 1][v];
-    ax[6] = o[0];
-    ay[6] = o[FIELD];
-    if (active) {
-      dl[3][0] = dy(2);
-      dl[3][1] = dx(2);
-      dl[3][2] = dx(1);
-      dl[3][3] = dy(0);
-    }
-    if (p >= 2 * RAD && ok && active) {  // output plane p-3
-      const T dzAx = d1_vals(ax[4], ax[2], ax[5], ax[1], ax[6], ax[0], w[2]);
-      const T dzAy = d1_vals(ay[4], ay[2], ay[5], ay[1], ay[6], ay[0], w[2]);
-      const T bx = dl[0][0] - dzAy;
-      const T by = dzAx - dl[0][1];
-      const T bz = dl[0][2] - dl[0][3];
-      sb2 += (double)(bx * bx + by * by + bz * bz);
-    }
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
-  }
-  if (failed) {
-    if (tid == 0) {
-      atomicOr(&R.clock->status, 2);
-      for (int q = p; q < issued; ++q) mbar_wait(&bars[q % NS], (uint32_t)((q / NS) & 1));
-    }
-    sb2 = __longlong_as_double(0x7ff8000000000000ll);  // NaN: the value is marked bad
-  }
-  const double red = block_sum(sb2, sh);
-  if (tid == 0) R.partials[(long long)tile.slot * NPART + 1] = red;
-  if (!last_tile_done(&R.counter[2], R.ntiles, &flag)) return;
-  const int nthr = blockDim.x * blockDim.y;
-  double loc = 0;
-  for (int t = tid; t < R.ntiles; t += nthr) loc += __ldcg(&R.partials[(long long)t * NPART + 1]);
-  const double tot = block_sum(loc, sh);
-  if (tid != 0) return;
-  R.diag[1] = sqrt(tot / ((double)R.nx * R.ny * R.nz));
-  R.counter[2] = 0u;
 }
 
 namespace {
@@ -1054,11 +955,6 @@ int occupancy_tma(int *bps) {
 int tma_num_tiles(int dtype) { return dtype == 0 ? 9 : 2; }
 
 template <typename T, int TY>
-int brms_smem_bytes() {
-  return BRMS_STAGES * brms_stage_bytes<T, TY>() + BRMS_STAGES * 8;
-}
-
-template <typename T, int TY>
 int pro_smem_bytes() {
   return pro_stages<T, TY>() * TmaShape<T, TY>::STAGE_BYTES + pro_stages<T, TY>() * 8;
 }
@@ -1096,11 +992,11 @@ int tma_prepare(int dtype, int tile) {
   if (dtype == DT && tile == ID) {                                                                       \
     int e = prepare_tma<T, TY, NS, U>();                                                                 \
     if (!e)                                                                                              \
-      e = (int)cudaFuncSetAttribute(k_prologue_tma<T, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                    pro_smem_bytes<T, TY>());                                            \
-    if (!e)                                                                                              \
-      e = (int)cudaFuncSetAttribute(k_brms_tma<T, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                                    brms_smem_bytes<T, TY>());                                           \
+      e = (int)cudaFuncSetAttribute(k_prologue_tma<T, TY, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                    pro_smem_bytes<T, TY>());                                               \
+    if (!e)                                                                                                 \
+      e = (int)cudaFuncSetAttribute(k_prologue_tma<T, TY, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                    pro_smem_bytes<T, TY>());                                               \
     return e;                                                                                            \
   }
   MHD_TMA_VARIANTS(X)
@@ -1123,32 +1019,19 @@ int tma_occupancy(int dtype, int tile, int *bps) {
 }
 
 int tma_launch_prologue(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles,
-                        cudaStream_t s) {
+                        cudaStream_t s, int mode) {
   if (ntiles <= 0) return 0;
 #define X(ID, SC, TY, NS) \
-  if (dtype == 0 && tile == ID) return tma_launch_prologue(0, SC, runs, tiles, ntiles, s);
+  if (dtype == 0 && tile == ID) return tma_launch_prologue(0, SC, runs, tiles, ntiles, s, mode);
   MHD_PACKED_VARIANTS(X)
 #undef X
 #define X(DT, ID, T, TY, NS, U)                                                                       \
   if (dtype == DT && tile == ID) {                                                                    \
-    k_prologue_tma<T, TY><<<ntiles, dim3(32, TY), pro_smem_bytes<T, TY>(), s>>>(runs, tiles);         \
+    if (mode == 1)                                                                                    \
+      k_prologue_tma<T, TY, 1><<<ntiles, dim3(32, TY), pro_smem_bytes<T, TY>(), s>>>(runs, tiles);    \
+    else                                                                                              \
+      k_prologue_tma<T, TY, 0><<<ntiles, dim3(32, TY), pro_smem_bytes<T, TY>(), s>>>(runs, tiles);    \
     return (int)cudaGetLastError();                                                                   \
-  }
-  MHD_TMA_VARIANTS(X)
-#undef X
-  return (int)cudaErrorInvalidValue;
-}
-
-int tma_launch_brms(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles, cudaStream_t s) {
-  if (ntiles <= 0) return 0;
-#define X(ID, SC, TY, NS) \
-  if (dtype == 0 && tile == ID) return tma_launch_brms(0, SC, runs, tiles, ntiles, s);
-  MHD_PACKED_VARIANTS(X)
-#undef X
-#define X(DT, ID, T, TY, NS, U)                                                                 \
-  if (dtype == DT && tile == ID) {                                                              \
-    k_brms_tma<T, TY><<<ntiles, dim3(32, TY), brms_smem_bytes<T, TY>(), s>>>(runs, tiles);      \
-    return (int)cudaGetLastError();                                                             \
   }
   MHD_TMA_VARIANTS(X)
 #undef X

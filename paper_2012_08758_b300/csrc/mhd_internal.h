@@ -26,6 +26,11 @@ struct Clock {
   int status;   // bit 0: the time-step reduction saw a non-finite value;
                 // bit 1: a bounded wait for a TMA copy gave up
   int pad;
+  // The CFL maximum of the state at the start of step cache_tag - 1, taken by
+  // a B_rms reduction of that state (the same sweep); 0 = nothing cached.
+  // Every write of the state zeroes the clock, and with it the tag.
+  long long cache_tag;
+  double cache_vmax;
 };
 
 // Per-step constants written by the prologue and read by every substep of
@@ -44,7 +49,6 @@ struct StepCoeffs {
 // Everything a kernel needs to know about one run, resident in device memory.
 struct RunDesc {
   CUtensorMap tmap[2];      // TMA maps of q[0], q[1]: 4-D (x, y, z, field), box of one z-plane
-  CUtensorMap tmapA[2];     // the same maps with a box of the three A fields only
   int nx, ny, nz;
   int px, py, pz;           // padded extents; px is the row pitch
   long long fstride;        // elements per field (px * py * pz)
@@ -97,8 +101,11 @@ int tma_num_tiles(int dtype);
 int tma_tile_shape(int dtype, int tile, int *tx, int *ty);
 int tma_prepare(int dtype, int tile);
 int tma_occupancy(int dtype, int tile, int *bps);
+// mode 0: the step prologue (takes the cached CFL maximum when the clock
+// holds one for this step); mode 1: B_rms of the current state into diag[1],
+// caching the CFL maximum of the same sweep for the next step's prologue.
 int tma_launch_prologue(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles,
-                        cudaStream_t s);
+                        cudaStream_t s, int mode = 0);
 int tma_launch(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles, int substep,
                int grid, int iso, cudaStream_t s);
 int substep_tile_shape(int dtype, int kernel, int tile, int *tx, int *ty);
@@ -115,8 +122,6 @@ int launch_get_field(int dtype, int host_dtype, const void *src_field, void *dst
 // B_rms of the run's current state into diag[1] (curl and sum in one pass)
 int launch_brms(int dtype, const RunDesc *run_dev, const Tile *tiles, int ntiles, int tw, int th,
                 cudaStream_t s);
-// TMA variant of launch_brms for runs on the TMA kernel (same tiles and order).
-int tma_launch_brms(int dtype, int tile, const RunDesc *run_dev, const Tile *tiles, int ntiles, cudaStream_t s);
 // B = curl A of the run's current state into fields 0..2 of its w buffer
 // (interior points only).
 int launch_curl(int dtype, const RunDesc *run_dev, const Tile *tiles, int ntiles, int tw, int th,

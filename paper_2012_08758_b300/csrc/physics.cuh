@@ -153,12 +153,24 @@ __device__ __forceinline__ void rhs_point(const Derivs<T> &d, const C &c, const 
   }
 }
 
+// Round-to-nearest operations the compiler may not fuse or reorder: every
+// kernel that evaluates them gets the same bits.
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // First derivative from the samples at offsets +-1, +-2, +-3 with the
-// weights w[1..3] of one axis (one expression shared by every reduction, so
-// they all see bit-identical B).
+// weights w[1..3] of one axis, and |B|^2, in one fixed sequence of roundings
+// shared by every reduction (dt prologue, diagnostics, B_rms, curl), so they
+// all see bit-identical B.
 template <typename T>
 __device__ __forceinline__ T d1_vals(T p1, T m1, T p2, T m2, T p3, T m3, const T *w) {
-  return w[1] * (p1 - m1) + w[2] * (p2 - m2) + w[3] * (p3 - m3);
+  return fma_rn(w[3], p3 - m3, fma_rn(w[2], p2 - m2, mul_rn(w[1], p1 - m1)));
+}
+template <typename T>
+__device__ __forceinline__ T norm2_rn(T bx, T by, T bz) {
+  return fma_rn(bz, bz, fma_rn(by, by, mul_rn(bx, bx)));
 }
 
 // Complex product helpers for the forcing phase.

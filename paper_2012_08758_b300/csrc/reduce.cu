@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS) k_prologue(const RunDesc *__
         const T Bz = d1_at<T, 0>(Ay, c, 1, w[0]) - d1_at<T, 1>(Ax, c, sy, w[1]);
         const T ux = q[fs + c], uy = q[2 * fs + c], uz = q[3 * fs + c];
         const T v = sqrt(ux * ux + uy * uy + uz * uz) +
-                    sqrt(cs2 + (Bx * Bx + By * By + Bz * Bz) * exp(-q[c]));
+                    sqrt(cs2 + norm2_rn(Bx, By, Bz) * exp(-q[c]));
         bad |= isnan(v);
         vm = fmax(vm, v);
       }
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS) k_diag(const RunDesc *__rest
       // 1/64 rate on B300), sums accumulated in FP64
       const T ux = q[fs + c], uy = q[2 * fs + c], uz = q[3 * fs + c];
       const T bx = B[c], by = B[fs + c], bz = B[2 * fs + c];
-      const T u2 = ux * ux + uy * uy + uz * uz, b2 = bx * bx + by * by + bz * bz;
+      const T u2 = ux * ux + uy * uy + uz * uz, b2 = norm2_rn(bx, by, bz);
       const T rho = exp(q[c]);
       const T div = d1_at<T, 0>(B, c, 1, w[0]) + d1_at<T, 1>(B + fs, c, sy, w[1]) +
                     d1_at<T, 2>(B + 2 * fs, c, sz, w[2]);
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS) k_brms(const RunDesc *__rest
       const T bx = d1_at<T, 1>(Az, c, sy, w[1]) - d1_at<T, 2>(Ay, c, sz, w[2]);
       const T by = d1_at<T, 2>(Ax, c, sz, w[2]) - d1_at<T, 0>(Az, c, 1, w[0]);
       const T bz = d1_at<T, 0>(Ay, c, 1, w[0]) - d1_at<T, 1>(Ax, c, sy, w[1]);
-      sb2 += (double)(bx * bx + by * by + bz * bz);
+      sb2 += (double)norm2_rn(bx, by, bz);
     }
   }
   const double red = block_sum(sb2, sh);

@@ -175,7 +175,9 @@ __device__ __forceinline__ bool last_tile_done(unsigned int *counter, int ntiles
 __device__ __forceinline__ void finalize_step(const RunDesc &R, long long step, int nsub, double *sh) {
   const int nthr = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
   double v = 0.0;
-  if (R.dt_fixed <= 0.0) {
+  if (R.dt_fixed <= 0.0 && R.clock->cache_tag == step + 1) {
+    v = R.clock->cache_vmax;  // taken by a B_rms reduction of this very state
+  } else if (R.dt_fixed <= 0.0) {
     const int n = R.ntiles * nsub;
     for (int i = tid; i < n; i += nthr) {
       const double p = __ldcg(&R.partials[(long long)(i / nsub) * NPART + (i % nsub)]);

@@ -323,6 +323,60 @@ def test_fused_brms_equals_full_diagnostics(dtype):
     run.close()
 
 
+@pytest.mark.parametrize("kernel,tile", [(2, 0), (1, 0)])
+def test_brms_sampling_leaves_the_run_unchanged(kernel, tile):
+    """Sampling B_rms after every step (the TMA runs cache the CFL maximum of
+    that sweep for the next step's prologue) gives bit-for-bit the run that
+    is never sampled, and each sample equals the full diagnostics' B_rms."""
+    from paper_2012_08758_b300 import binding as B
+    kw = dict(nx=40, ny=24, nz=20, nu=5e-3, eta=5e-3, f0=0.05, sigma=1.0, kmin=1.0, kmax=2.0, seed=9,
+              dtype="f32", kernel=kernel, tile=tile)
+    q0 = inputs.random_modes_state(40, 24, 20, seed=14, amp=0.3)
+    a, b = make_run(**kw), make_run(**kw)
+    a.set_state(q0)
+    b.set_state(q0)
+    for _ in range(6):
+        a.step(1)
+        b.step(1)
+        fast = a.reduce(B.MHD_BRMS)
+        assert fast == pytest.approx(a.diagnostics()["brms"], rel=1e-13)
+    qa, ta, sa = a.get_state()
+    qb, tb, sb = b.get_state()
+    assert sa == sb == 6 and ta == tb and np.array_equal(qa, qb)
+    a.close()
+    b.close()
+
+
+def test_state_write_after_brms_drops_the_cached_maximum():
+    """A B_rms reduction caches the CFL maximum of the current state; writing
+    a new state (faster flow, same step number) must not reuse it: the next
+    step takes the dt of the new state, as a fresh run does."""
+    from paper_2012_08758_b300 import binding as B
+    kw = dict(nx=24, ny=24, nz=24, nu=5e-3, eta=5e-3, f0=0.0, dtype="f32")
+    slow = inputs.random_modes_state(24, 24, 24, seed=15, amp=0.05)
+    fast = inputs.random_modes_state(24, 24, 24, seed=16, amp=0.6)
+    a, b = make_run(**kw), make_run(**kw)
+    a.set_state(slow)
+    a.reduce(B.MHD_BRMS)
+    a.set_state(fast)
+    b.set_state(fast)
+    a.step(1)
+    b.step(1)
+    (qa, ta, _), (qb, tb, _) = a.get_state(), b.get_state()
+    assert ta == tb and np.array_equal(qa, qb)
+    a.set_seed_field(3, 1e-3)  # the device initial condition is a state write too
+    b.set_seed_field(3, 1e-3)
+    a.reduce(B.MHD_BRMS)
+    a.set_state(fast)
+    b.set_state(fast)
+    a.step(2)
+    b.step(2)
+    (qa, ta, _), (qb, tb, _) = a.get_state(), b.get_state()
+    assert ta == tb and np.array_equal(qa, qb)
+    a.close()
+    b.close()
+
+
 def test_state_roundtrip_is_exact():
     q = inputs.noise_state(13, 7, 5, seed=1, amp=1.0)
     run = make_run(nx=13, ny=7, nz=5, dtype="f64")
