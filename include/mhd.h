@@ -195,6 +195,22 @@ int mhd_forcing_draw(mhd_ctx *ctx, int64_t step, double *out);
  * change the state.  Synchronising. */
 int mhd_eval_rhs(mhd_ctx *ctx, int64_t step, double dt_forcing, void *host_rhs, int host_dtype);
 
+/* The same right-hand side at npts listed grid points only, for grids whose
+ * full dq/dt is too large to bring to the host (the whole field is still
+ * evaluated on the device; only the listed values are copied back).
+ *   ijk       host array of 3*npts ints: (i, j, k) of each point,
+ *             0 <= i < nx, 0 <= j < ny, 0 <= k < nz (caller-owned).
+ *   host_out  host array of 7*npts doubles (caller-owned): point-major,
+ *             host_out[7*n + f] = dq_f/dt at point n, fields in state order.
+ * 1 <= npts <= MHD_EVAL_AT_MAX_POINTS, and the list and values must fit the
+ * context's spare state buffer (12 + 56 bytes per point against 7 padded
+ * fields: any npts up to a third of the grid's points).  Does not change the
+ * state.  Synchronising.  Errors: MHD_EINVAL (NULL pointers, npts out of
+ * range, a point outside the grid), MHD_ECUDA. */
+enum { MHD_EVAL_AT_MAX_POINTS = 1 << 16 };
+int mhd_eval_rhs_at(mhd_ctx *ctx, int64_t step, double dt_forcing, int npts, const int *ijk,
+                    double *host_out);
+
 /* ---- magnetic energy spectrum (Sec. 5, power spectra) ----------------------
  * E_B(m) for shells m = 0 .. nshells-1 of the current state:
  *   B = curl A with the first-derivative stencil (the B of mhd_diagnostics),

@@ -71,6 +71,7 @@ def lib():
             "mhd_sync": (C.c_int, [vp]),
             "mhd_forcing_draw": (C.c_int, [vp, i64, dp]),
             "mhd_eval_rhs": (C.c_int, [vp, i64, C.c_double, vp, C.c_int]),
+            "mhd_eval_rhs_at": (C.c_int, [vp, i64, C.c_double, C.c_int, vp, vp]),
             "mhd_last_error": (C.c_char_p, [vp]),
             "mhd_batch_create": (C.c_int, [C.POINTER(vp), C.c_int, C.POINTER(vp)]),
             "mhd_batch_step": (C.c_int, [vp, C.c_int]),
@@ -203,6 +204,16 @@ def mhd_eval_rhs(ctx: int, shape, step: int = 0, dt_forcing: float = 0.0, dtype=
     out = np.empty(shape, dtype=dtype)
     _check(lib().mhd_eval_rhs(C.c_void_p(ctx), int(step), float(dt_forcing),
                               out.ctypes.data_as(C.c_void_p), _host(out)), C.c_void_p(ctx))
+    return out
+
+
+def mhd_eval_rhs_at(ctx: int, points, step: int = 0, dt_forcing: float = 0.0) -> np.ndarray:
+    """dq/dt at the listed (i, j, k) points: array (len(points), 7)."""
+    ijk = np.ascontiguousarray(np.asarray(points, dtype=np.int32).reshape(-1, 3))
+    out = np.empty((len(ijk), 7))
+    _check(lib().mhd_eval_rhs_at(C.c_void_p(ctx), int(step), float(dt_forcing), len(ijk),
+                                 ijk.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p)),
+           C.c_void_p(ctx))
     return out
 
 

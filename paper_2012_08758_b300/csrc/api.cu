@@ -973,6 +973,42 @@ int mhd_eval_rhs(mhd_ctx *ctx, int64_t step, double dt_forcing, void *host_rhs, 
   return MHD_OK;
 }
 
+int mhd_eval_rhs_at(mhd_ctx *ctx, int64_t step, double dt_forcing, int npts, const int *ijk, double *host_out) {
+  if (!ctx) return fail(nullptr, MHD_EINVAL, "ctx is NULL");
+  if (!ijk || !host_out) return fail(ctx, MHD_EINVAL, "ijk and host_out must be non-NULL");
+  if (npts < 1 || npts > MHD_EVAL_AT_MAX_POINTS)
+    return fail(ctx, MHD_EINVAL, "npts must be in [1, %d]", (int)MHD_EVAL_AT_MAX_POINTS);
+  if (step < 0) return fail(ctx, MHD_EINVAL, "step must be >= 0");
+  const RunDesc &R = ctx->h_run;
+  for (int n = 0; n < npts; ++n)
+    if (ijk[3 * n] < 0 || ijk[3 * n] >= R.nx || ijk[3 * n + 1] < 0 || ijk[3 * n + 1] >= R.ny ||
+        ijk[3 * n + 2] < 0 || ijk[3 * n + 2] >= R.nz)
+      return fail(ctx, MHD_EINVAL, "point %d (%d, %d, %d) is outside the grid", n, ijk[3 * n], ijk[3 * n + 1],
+                  ijk[3 * n + 2]);
+  Clock c;
+  int rc = read_clock(ctx, &c);
+  if (rc) return rc;
+  const int par = (int)(c.step & 1);
+  cudaStream_t s = ctx->stream;
+  // as mhd_eval_rhs: substep 0 with dt = 1 leaves w = RHS; the dead state
+  // buffer holds the point list and the gathered values, then is re-poisoned
+  char *staging = static_cast<char *>(R.q[par ^ 1]);
+  const size_t ijk_bytes = align_up((size_t)3 * npts * sizeof(int), ALIGN);
+  if (ijk_bytes + (size_t)NF * npts * sizeof(double) > (size_t)NF * R.fstride * ctx->L.esz)
+    return fail(ctx, MHD_EINVAL, "%d points do not fit this grid's staging buffer", npts);
+  CK(ctx, launch_coeffs(ctx->p.dtype, ctx->d_run, step, 1.0, dt_forcing, par, s));
+  CK(ctx, launch_substep(ctx->p.dtype, ctx->p.kernel, ctx->p.tile, ctx->d_run, ctx->d_sub,
+                         ctx->nsub, 0, ctx->sub_grid, ctx->iso, s));
+  int *d_ijk = reinterpret_cast<int *>(staging);
+  double *d_out = reinterpret_cast<double *>(staging + ijk_bytes);
+  CK(ctx, cudaMemcpyAsync(d_ijk, ijk, (size_t)3 * npts * sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(ctx, launch_gather_points(ctx->p.dtype, R.w, R.fstride, R.px, R.py, d_ijk, npts, d_out, s));
+  CK(ctx, cudaMemcpyAsync(host_out, d_out, (size_t)NF * npts * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(ctx, cudaMemsetAsync(staging, 0xFF, (size_t)NF * R.fstride * ctx->L.esz, s));
+  CK(ctx, cudaStreamSynchronize(s));
+  return MHD_OK;
+}
+
 const char *mhd_last_error(const mhd_ctx *ctx) {
   if (ctx) return ctx->err.c_str();
   return g_err.c_str();

@@ -346,6 +346,26 @@ __global__ void k_set_field(const H *src, T *dst, int nx, int ny, int nz, int px
   }
 }
 
+template <typename T>
+__global__ void k_gather_points(const T *q, long long fstride, int px, int py, const int *ijk, int npts,
+                                double *out) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= npts) return;
+  const long long c = ((long long)(ijk[3 * n + 2] + OZ) * py + (ijk[3 * n + 1] + OY)) * px + (ijk[3 * n] + OX);
+  for (int f = 0; f < NF; ++f) out[(long long)NF * n + f] = (double)q[f * fstride + c];
+}
+
+int launch_gather_points(int dtype, const void *q, long long fstride, int px, int py, const int *ijk, int npts,
+                         double *out, cudaStream_t s) {
+  const int grid = (npts + 255) / 256;
+  if (dtype == 0)
+    k_gather_points<float><<<grid, 256, 0, s>>>(static_cast<const float *>(q), fstride, px, py, ijk, npts, out);
+  else
+    k_gather_points<double><<<grid, 256, 0, s>>>(static_cast<const double *>(q), fstride, px, py, ijk, npts,
+                                                  out);
+  return (int)cudaGetLastError();
+}
+
 template <typename T, typename H>
 __global__ void k_get_field(const T *src, H *dst, int nx, int ny, int nz, int px, int py) {
   const long long total = (long long)nx * ny * nz;

@@ -117,6 +117,9 @@ int launch_seed_field(int dtype, void *A, long long fstride, int nx, int ny, int
                       unsigned long long seed, double amp, cudaStream_t s);
 int launch_set_field(int dtype, int host_dtype, const void *src, void *dst_field, int nx, int ny,
                      int nz, int px, int py, cudaStream_t s);
+// out[7 n + f] = field f of the NF-field array q at padded point of ijk[3n ..]
+int launch_gather_points(int dtype, const void *q, long long fstride, int px, int py, const int *ijk, int npts,
+                         double *out, cudaStream_t s);
 int launch_get_field(int dtype, int host_dtype, const void *src_field, void *dst, int nx, int ny,
                      int nz, int px, int py, cudaStream_t s);
 // B_rms of the run's current state into diag[1] (curl and sum in one pass)

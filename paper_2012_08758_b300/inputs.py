@@ -113,10 +113,26 @@ def counter_seed_field_state(nx: int, ny: int | None = None, nz: int | None = No
     ny = nx if ny is None else ny
     nz = nx if nz is None else nz
     npts = nx * ny * nz
-    n = np.arange(3 * npts, dtype=np.uint64)
-    u1 = ((_splitmix64(seed, np.uint64(2) * n) >> np.uint64(11)) + np.uint64(1)).astype(np.float64) * 2.0 ** -53
-    u2 = (_splitmix64(seed, np.uint64(2) * n + np.uint64(1)) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
-    g = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    g = _counter_normals(seed, np.arange(3 * npts, dtype=np.uint64))
     q = np.zeros((7, nz, ny, nx))
     q[4:7] = amp * g.reshape(3, nz, ny, nx)
     return q
+
+
+def _counter_normals(seed: int, n: np.ndarray) -> np.ndarray:
+    """Normal number n of the seed-field stream: Box-Muller of SplitMix64
+    outputs 2n and 2n + 1 (53-bit uniforms, the first shifted off zero)."""
+    n = n.astype(np.uint64)
+    u1 = ((_splitmix64(seed, np.uint64(2) * n) >> np.uint64(11)) + np.uint64(1)).astype(np.float64) * 2.0 ** -53
+    u2 = (_splitmix64(seed, np.uint64(2) * n + np.uint64(1)) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+
+def counter_seed_field_at(nx: int, ny: int, nz: int, i, j, k, seed: int = 0, amp: float = 1e-5) -> np.ndarray:
+    """A = (A_x, A_y, A_z) of the device seed field (counter_seed_field_state)
+    at grid points (i, j, k), periodic indexes allowed: array (3, len(i)).
+    Lets a test rebuild any neighbourhood of a grid too large for the host."""
+    i, j, k = (np.asarray(v, dtype=np.int64) for v in (i, j, k))
+    e = ((k % nz) * ny + (j % ny)) * nx + (i % nx)
+    npts = nx * ny * nz
+    return np.stack([amp * _counter_normals(seed, c * npts + e) for c in range(3)])

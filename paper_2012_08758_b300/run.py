@@ -121,6 +121,10 @@ class Run:
     def eval_rhs(self, step: int = 0, dt_forcing: float = 0.0, dtype=np.float64):
         return B.mhd_eval_rhs(self.ctx, self.shape, step, dt_forcing, dtype)
 
+    def eval_rhs_at(self, points, step: int = 0, dt_forcing: float = 0.0) -> np.ndarray:
+        """dq/dt at the listed (i, j, k) points only: array (len(points), 7)."""
+        return B.mhd_eval_rhs_at(self.ctx, points, step, dt_forcing)
+
     def close(self) -> None:
         if getattr(self, "ctx", None):
             B.mhd_destroy(self.ctx)
