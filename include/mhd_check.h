@@ -22,6 +22,19 @@ extern "C" {
  * Synchronising.  Errors: MHD_EINVAL (NULL argument), MHD_ECUDA. */
 int mhd_padding_check(mhd_ctx *ctx, long long *bad);
 
+/* Self-test of the bounded waits: one CTA waits, with the bounded mbarrier
+ * wait every TMA kernel uses (its poll count cut by a known factor), on an
+ * mbarrier that nothing arrives on (no copy is issued: a flag that nothing
+ * sets).  The wait must give up and the kernel must report it as the kernels
+ * do (status bit 1) and return, leaving the context usable.
+ * stream: cudaStream_t (NULL: legacy stream).  *seconds (may be NULL)
+ * receives the time the wait took, *kernel_bound_seconds (may be NULL) that
+ * time scaled to the kernels' own poll count: how long a TMA kernel waits for
+ * a copy before it gives up.  Returns MHD_ETIMEOUT when the wait gave up (the
+ * expected outcome), MHD_OK if it completed, MHD_ECUDA on a CUDA error.
+ * Synchronising. */
+int mhd_wait_selftest(void *stream, double *seconds, double *kernel_bound_seconds);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,7 @@ _BINDING_NAMES = {
     "mhd_batch_create", "mhd_batch_step", "mhd_batch_destroy", "MHD_F32", "MHD_F64",
     "REDUCE_NAMES", "MHD_URMS", "MHD_BRMS", "MHD_UMAX", "MHD_BMAX", "MHD_EKIN", "MHD_EMAG",
     "MHD_DIVB_MAX", "MHD_MASS", "MHD_VMAX", "MHD_NREDUCE", "MHD_KERNEL_AUTO", "MHD_KERNEL_SMEM",
-    "MHD_KERNEL_TMA", "mhd_diagnostics_noalloc", "MHD_NOALLOC_MAX_POINTS", "mhd_alu_peak", "MHD_F32X2", "mhd_spectrum", "mhd_spectrum_shells", "mhd_set_seed_field", "mhd_substep_plan", "mhd_padding_check",
+    "MHD_KERNEL_TMA", "mhd_diagnostics_noalloc", "MHD_NOALLOC_MAX_POINTS", "mhd_alu_peak", "MHD_F32X2", "mhd_spectrum", "mhd_spectrum_shells", "mhd_set_seed_field", "mhd_substep_plan", "mhd_padding_check", "mhd_wait_selftest",
 }
 
 

@@ -82,6 +82,7 @@ def lib():
             "mhd_spectrum_shells": (C.c_int, [pp, C.POINTER(C.c_int)]),
             "mhd_set_seed_field": (C.c_int, [vp, C.c_uint64, C.c_double]),
             "mhd_padding_check": (C.c_int, [vp, C.POINTER(C.c_longlong)]),
+            "mhd_wait_selftest": (C.c_int, [vp, dp, dp]),
             "mhd_substep_plan": (C.c_int, [pp, C.c_int, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int),
                                            C.POINTER(C.c_int)]),
             "mhd_spectrum": (C.c_int, [vp, dp, C.c_int, C.POINTER(C.c_int)]),
@@ -262,6 +263,15 @@ def mhd_substep_plan(p: MhdParams, grid_ctas: int):
     buf = (C.c_int * max(1, 5 * n.value))()
     _check(lib().mhd_substep_plan(C.byref(p), int(grid_ctas), buf, n.value, C.byref(n), C.byref(g)))
     return np.frombuffer(buf, dtype=np.int32)[: 5 * n.value].reshape(n.value, 5).copy(), g.value
+
+
+def mhd_wait_selftest(stream: int = 0):
+    """Runs the bounded-wait self-test: (return code, seconds the cut-down wait
+    took, the kernels' own bound in seconds); MHD_ETIMEOUT is the expected
+    code (the wait gave up and reported it)."""
+    sec, bound = C.c_double(-1.0), C.c_double(-1.0)
+    rc = lib().mhd_wait_selftest(C.c_void_p(stream), C.byref(sec), C.byref(bound))
+    return rc, sec.value, bound.value
 
 
 def mhd_padding_check(ctx: int) -> int:

@@ -843,6 +843,33 @@ int mhd_padding_check(mhd_ctx *ctx, long long *bad) {
   return MHD_OK;
 }
 
+int mhd_wait_selftest(void *stream, double *seconds, double *kernel_bound_seconds) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int *d = nullptr;
+  int h = -1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(d, 0xFF, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  double scale = 0.0;
+  if (e == cudaSuccess) e = (cudaError_t)launch_wait_selftest(d, s, &scale);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (d) cudaFree(d);
+  if (e != cudaSuccess) return fail(nullptr, MHD_ECUDA, "mhd_wait_selftest: %s", cudaGetErrorString(e));
+  if (seconds) *seconds = ms * 1e-3;
+  if (kernel_bound_seconds) *kernel_bound_seconds = ms * 1e-3 * scale;
+  if (h == 2) return fail(nullptr, MHD_ETIMEOUT, "the bounded wait gave up after %.3f s (expected)", ms * 1e-3);
+  return MHD_OK;
+}
+
 int mhd_substep_plan(const mhd_params *p, int grid_ctas, int *tiles, int max_tiles, int *ntiles, int *grid) {
   std::string why;
   if (validate(p, &why)) return fail(nullptr, MHD_EINVAL, "%s", why.c_str());

@@ -64,12 +64,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: gives up after MAX_TRIES polls (each poll may suspend the
-// thread for a short, hardware-defined time), well under a few seconds.
-constexpr uint32_t MAX_TRIES = 1u << 20;
+// Bounded wait: gives up after TRIES polls.  Each poll may suspend the
+// thread for a hardware-defined time, measured by the self-test at about
+// 8 us on B300, so the kernels' 2^17 polls give up after about a second.
+constexpr uint32_t MAX_TRIES = 1u << 17;
 
+template <uint32_t TRIES = MAX_TRIES>
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  for (uint32_t i = 0; i < MAX_TRIES; ++i)
+  for (uint32_t i = 0; i < TRIES; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -98,6 +100,28 @@ struct TmaShape {
 };
 
 }  // namespace
+
+// One thread waits with the bounded wait, cut to SELFTEST_TRIES polls, on an
+// mbarrier that nothing arrives on; out[0] = 2 (status bit 1) when it gave
+// up, 0 if it completed.  The kernels' own bound is MAX_TRIES polls, so the
+// time of this wait times MAX_TRIES / SELFTEST_TRIES is theirs.
+constexpr uint32_t SELFTEST_TRIES = 1u << 10;
+
+__global__ void k_wait_selftest(int *out) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) out[0] = mbar_wait<SELFTEST_TRIES>(&bar, 0) ? 0 : 2;
+}
+
+int launch_wait_selftest(int *out, cudaStream_t s, double *scale) {
+  k_wait_selftest<<<1, 32, 0, s>>>(out);
+  if (scale) *scale = (double)MAX_TRIES / SELFTEST_TRIES;
+  return (int)cudaGetLastError();
+}
 
 template <int V>
 struct Phase {

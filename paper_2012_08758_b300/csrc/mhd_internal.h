@@ -97,6 +97,9 @@ int launch_substep(int dtype, int kernel, int tile, const RunDesc *runs, const T
                    int ntiles, int substep, int grid, int iso, cudaStream_t s);
 int prepare_substep(int dtype, int kernel, int tile);
 // TMA variant (kernels_tma.cu); tile ids start at 1
+// Bounded-wait self-test kernel (mhd_wait_selftest): out[0] = 2 on give-up;
+// *scale = the kernels' poll bound over the self-test's.
+int launch_wait_selftest(int *out, cudaStream_t s, double *scale);
 int tma_num_tiles(int dtype);
 int tma_tile_shape(int dtype, int tile, int *tx, int *ty);
 int tma_prepare(int dtype, int tile);

@@ -564,6 +564,29 @@ def test_zero_steps_is_a_noop():
     r.close()
 
 
+def test_bounded_wait_gives_up_and_leaves_the_gpu_usable():
+    """Failure detection of the device waits without a fault: the self-test
+    kernel waits, with the bounded mbarrier wait of every TMA kernel (poll
+    count cut 1024-fold), on an mbarrier that nothing arrives on.  The wait
+    must give up and report status bit 1 (MHD_ETIMEOUT), the kernels' own
+    bound scaled from it must stay within a few seconds (about 1 s on B300), and afterwards the GPU runs
+    forced steps that still match the oracle."""
+    from paper_2012_08758_b300 import binding as B
+    rc, seconds, bound = B.mhd_wait_selftest()
+    assert rc == B.MHD_ETIMEOUT, (rc, B.mhd_last_error())
+    assert 0.0 < seconds < 0.5 and 0.0 < bound < 5.0, (seconds, bound)
+    kw = dict(C1, dtype="f64")
+    q0 = inputs.random_modes_state(32, seed=2, amp=0.2)
+    run = make_run(**kw)
+    run.set_state(q0)
+    run.step(2)
+    got, _, _ = run.get_state()
+    q = q0.copy()
+    O.run(oracle_params(**kw), q, 2)
+    assert rel_linf_state(got, q).max() < 1e-12
+    run.close()
+
+
 def test_blow_up_is_reported_not_hidden():
     """A NaN planted in the host-side upload makes the dt reduction
     non-finite; the next synchronising call reports it."""
