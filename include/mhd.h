@@ -167,9 +167,13 @@ int mhd_step(mhd_ctx *ctx, int nsteps);
 int mhd_step_timed(mhd_ctx *ctx, int nsteps, double *stage_ms, double *total_ms);
 
 /* Reads one quantity (MHD_URMS ... MHD_VMAX) of the current state into
- * *out, accumulated in FP64 in a fixed order.  MHD_BRMS (sampled every few
- * steps by growth-rate runs) takes a single fused pass over A with the same
- * tiles and summation order as mhd_diagnostics.  Synchronising. */
+ * *out, accumulated in FP64 in a fixed order.  MHD_BRMS (sampled after every
+ * step by growth-rate runs) takes a single fused pass with the same per-point
+ * B, tiles and summation order as mhd_diagnostics.  On the TMA kernel that
+ * pass is the time-step sweep of the next step's prologue: its CFL maximum is
+ * kept on the device and that prologue reuses it instead of sweeping again
+ * (results are bit-for-bit those of a run that is never sampled; any write of
+ * the state discards the kept value).  Synchronising. */
 int mhd_reduce(mhd_ctx *ctx, int kind, double *out);
 
 /* All MHD_NREDUCE quantities at once into out[MHD_NREDUCE].  Synchronising. */
