@@ -405,6 +405,26 @@ def test_state_write_after_brms_drops_the_cached_maximum():
     b.close()
 
 
+@pytest.mark.parametrize("kernel,tile", KERNELS)
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_ideal_mhd_step_parity(dtype, tol, kernel, tile):
+    """nu = eta = 0 (ideal MHD): the diffusive time-step limit drops out
+    (dt from the CFL speed alone) and the viscous and resistive terms vanish;
+    five forced steps against the oracle."""
+    kw = dict(nx=28, ny=24, nz=20, nu=0.0, eta=0.0, f0=0.05, sigma=1.0, kmin=1.0, kmax=2.0, seed=21,
+              dtype=dtype, kernel=kernel, tile=tile)
+    q0 = inputs.random_modes_state(28, 24, 20, seed=31, amp=0.2)
+    run = make_run(**kw)
+    run.set_state(q0)
+    run.step(5)
+    got, t, _ = run.get_state()
+    q = q0.copy()
+    t_o, _ = O.run(oracle_params(**kw), q, 5)
+    assert abs(t - t_o) <= (1e-13 if dtype == "f64" else 1e-6) * t_o
+    assert rel_linf_state(got, q).max() < tol
+    run.close()
+
+
 def test_state_roundtrip_is_exact():
     q = inputs.noise_state(13, 7, 5, seed=1, amp=1.0)
     run = make_run(nx=13, ny=7, nz=5, dtype="f64")
