@@ -128,14 +128,19 @@ struct Phase {
   static constexpr int value = V;
 };
 
-template <typename T, int TY, int NS, bool UNROLL7, bool ISO>
+template <typename T, int TY, int NS, bool UNROLL7, bool ISO, int BAR>
 __global__ void __launch_bounds__(32 * TY, TY <= 6 ? 2 : 1)
     k_substep_tma(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles, int ntiles,
                   int substep) {
   using SH = TmaShape<T, TY>;
   constexpr int TX = SH::TX, SX = SH::SX, FIELD = SH::FIELD;
-  constexpr int P = NS - 4;  // prefetch distance in planes
+  // Prefetch distance in planes.  The CTA synchronises after every BAR-th
+  // plane (and after a tile's last one); a stage is refilled NS - P planes
+  // after it was the lead plane, i.e. NS - P - 3 planes after it was last read
+  // as the output plane, which must be at least BAR planes.
+  constexpr int P = NS - 3 - BAR;
   static_assert(P >= 1, "need at least one plane of prefetch");
+  static_assert(BAR >= 1 && BAR <= 4, "one to four planes between barriers");
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * SH::STAGE_BYTES);
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -147,7 +152,7 @@ __global__ void __launch_bounds__(32 * TY, TY <= 6 ? 2 : 1)
   __syncthreads();
 
   unsigned long long G = 0;  // planes issued by this CTA before the current tile
-  bool failed = false;
+  bool failed = false, waits_ok = true;
   int fail_run = -1, fail_p = 0, issued_hi = 0;
 
   for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
@@ -395,10 +400,24 @@ __global__ void __launch_bounds__(32 * TY, TY <= 6 ? 2 : 1)
         slot = 0;
         phase ^= 1u;
       }
-      if (__syncthreads_or(!ok)) {
-        failed = true;
-        fail_run = tile.run;
-        fail_p = p;
+      if constexpr (BAR == 1) {
+        if (__syncthreads_or(!ok)) {
+          failed = true;
+          fail_run = tile.run;
+          fail_p = p;
+        }
+      } else {
+        // a wait that gave up between barriers is remembered and caught at
+        // the next one; the clean-up then waits again from the earliest
+        // plane it could concern
+        waits_ok &= ok;
+        if (p % BAR == BAR - 1 || p == npl - 1) {
+          if (__syncthreads_or(!waits_ok)) {
+            failed = true;
+            fail_run = tile.run;
+            fail_p = p >= BAR - 1 ? p - (BAR - 1) : 0;
+          }
+        }
       }
     };
 
@@ -925,58 +944,62 @@ int tma_smem_bytes() {
   return NS * TmaShape<T, TY>::STAGE_BYTES + NS * 8;
 }
 
-template <typename T, int TY, int NS, bool U>
+template <typename T, int TY, int NS, bool U, int BR>
 int prepare_tma() {
-  int e = (int)cudaFuncSetAttribute(k_substep_tma<T, TY, NS, U, false>,
+  int e = (int)cudaFuncSetAttribute(k_substep_tma<T, TY, NS, U, false, BR>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, tma_smem_bytes<T, TY, NS, U>());
   if (!e)
-    e = (int)cudaFuncSetAttribute(k_substep_tma<T, TY, NS, U, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  tma_smem_bytes<T, TY, NS, U>());
+    e = (int)cudaFuncSetAttribute(k_substep_tma<T, TY, NS, U, true, BR>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, tma_smem_bytes<T, TY, NS, U>());
   return e;
 }
 
-template <typename T, int TY, int NS, bool U>
+template <typename T, int TY, int NS, bool U, int BR>
 int launch_tma(const RunDesc *runs, const Tile *tiles, int ntiles, int substep, int grid, bool iso,
                cudaStream_t s) {
   if (grid <= 0 || grid > ntiles) grid = ntiles;
   if (grid == 0) return 0;
   const int smem = tma_smem_bytes<T, TY, NS, U>();
   if (iso)
-    k_substep_tma<T, TY, NS, U, true><<<grid, dim3(32, TY), smem, s>>>(runs, tiles, ntiles, substep);
+    k_substep_tma<T, TY, NS, U, true, BR><<<grid, dim3(32, TY), smem, s>>>(runs, tiles, ntiles, substep);
   else
-    k_substep_tma<T, TY, NS, U, false><<<grid, dim3(32, TY), smem, s>>>(runs, tiles, ntiles, substep);
+    k_substep_tma<T, TY, NS, U, false, BR><<<grid, dim3(32, TY), smem, s>>>(runs, tiles, ntiles, substep);
   return (int)cudaGetLastError();
 }
 
-template <typename T, int TY, int NS, bool U>
+template <typename T, int TY, int NS, bool U, int BR>
 int occupancy_tma(int *bps) {
-  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_substep_tma<T, TY, NS, U, true>, 32 * TY,
+  return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_substep_tma<T, TY, NS, U, true, BR>, 32 * TY,
                                                             tma_smem_bytes<T, TY, NS, U>());
 }
 
 }  // namespace
 
 // Tile variants of the TMA kernel: id -> (dtype, TY, stages, ring rotation
-// by 7-fold unrolling instead of register moves).
+// by 7-fold unrolling instead of register moves, planes between barriers).
 //   FP32: 1 = 32x8/6; 2 = 32x4/6; 3 = 32x8/8; 4 = 32x12/6; 5 = 32x12/5; 6 = 32x16/5;
-//         9 = 32x6/5 (two CTAs per SM)
+//         9 = 32x6/5 (two CTAs per SM); 10, 11, 12 = 32x12 with 6, 7, 8 stages
+//         and a barrier every second, third, fourth plane
 //   FP32 packed (isotropic grids; anisotropic runs fall back to the tile
 //   of the same shape above): 7 = 32x12/5; 8 = 32x8/6
 //   FP64: 1 = 32x4/6; 2 = 32x4/6 unrolled
 // (the unrolled FP32 variants measured 1.7x slower on B300: the 7-fold body
 // overflows the instruction cache)
-#define MHD_TMA_VARIANTS(X)         \
-  X(0, 1, float, 8, 6, false)       \
-  X(0, 2, float, 4, 6, false)       \
-  X(0, 3, float, 8, 8, false)       \
-  X(0, 4, float, 12, 6, false)      \
-  X(0, 5, float, 12, 5, false)      \
-  X(0, 6, float, 16, 5, false)      \
-  X(0, 9, float, 6, 5, false)       \
-  X(1, 1, double, 4, 6, false)      \
-  X(1, 2, double, 4, 6, true)
+#define MHD_TMA_VARIANTS(X)            \
+  X(0, 1, float, 8, 6, false, 1)       \
+  X(0, 2, float, 4, 6, false, 1)       \
+  X(0, 3, float, 8, 8, false, 1)       \
+  X(0, 4, float, 12, 6, false, 1)      \
+  X(0, 5, float, 12, 5, false, 1)      \
+  X(0, 6, float, 16, 5, false, 1)      \
+  X(0, 9, float, 6, 5, false, 1)       \
+  X(0, 10, float, 12, 6, false, 2)     \
+  X(0, 11, float, 12, 7, false, 3)     \
+  X(0, 12, float, 12, 8, false, 4)     \
+  X(1, 1, double, 4, 6, false, 1)      \
+  X(1, 2, double, 4, 6, true, 1)
 
-int tma_num_tiles(int dtype) { return dtype == 0 ? 9 : 2; }
+int tma_num_tiles(int dtype) { return dtype == 0 ? 12 : 2; }
 
 template <typename T, int TY>
 int pro_smem_bytes() {
@@ -996,7 +1019,7 @@ int tma_tile_shape(int dtype, int tile, int *tx, int *ty) {
   if (dtype == 0 && tile == ID) { *ty = TY; return 0; }
   MHD_PACKED_VARIANTS(X)
 #undef X
-#define X(DT, ID, T, TY, NS, U) \
+#define X(DT, ID, T, TY, NS, U, BR) \
   if (dtype == DT && tile == ID) { *ty = TY; return 0; }
   MHD_TMA_VARIANTS(X)
 #undef X
@@ -1012,9 +1035,9 @@ int tma_prepare(int dtype, int tile) {
   }
   MHD_PACKED_VARIANTS(X)
 #undef X
-#define X(DT, ID, T, TY, NS, U)                                                                          \
+#define X(DT, ID, T, TY, NS, U, BR)                                                                          \
   if (dtype == DT && tile == ID) {                                                                       \
-    int e = prepare_tma<T, TY, NS, U>();                                                                 \
+    int e = prepare_tma<T, TY, NS, U, BR>();                                                                 \
     if (!e)                                                                                              \
       e = (int)cudaFuncSetAttribute(k_prologue_tma<T, TY, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                     pro_smem_bytes<T, TY>());                                               \
@@ -1035,8 +1058,8 @@ int tma_occupancy(int dtype, int tile, int *bps) {
                                                               tma_smem_bytes<float, TY, NS, false>());
   MHD_PACKED_VARIANTS(X)
 #undef X
-#define X(DT, ID, T, TY, NS, U) \
-  if (dtype == DT && tile == ID) return occupancy_tma<T, TY, NS, U>(bps);
+#define X(DT, ID, T, TY, NS, U, BR) \
+  if (dtype == DT && tile == ID) return occupancy_tma<T, TY, NS, U, BR>(bps);
   MHD_TMA_VARIANTS(X)
 #undef X
   return (int)cudaErrorInvalidValue;
@@ -1049,7 +1072,7 @@ int tma_launch_prologue(int dtype, int tile, const RunDesc *runs, const Tile *ti
   if (dtype == 0 && tile == ID) return tma_launch_prologue(0, SC, runs, tiles, ntiles, s, mode);
   MHD_PACKED_VARIANTS(X)
 #undef X
-#define X(DT, ID, T, TY, NS, U)                                                                       \
+#define X(DT, ID, T, TY, NS, U, BR)                                                                       \
   if (dtype == DT && tile == ID) {                                                                    \
     if (mode == 1)                                                                                    \
       k_prologue_tma<T, TY, 1><<<ntiles, dim3(32, TY), pro_smem_bytes<T, TY>(), s>>>(runs, tiles);    \
@@ -1075,8 +1098,8 @@ int tma_launch(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int 
   }
   MHD_PACKED_VARIANTS(X)
 #undef X
-#define X(DT, ID, T, TY, NS, U) \
-  if (dtype == DT && tile == ID) return launch_tma<T, TY, NS, U>(runs, tiles, ntiles, substep, grid, iso != 0, s);
+#define X(DT, ID, T, TY, NS, U, BR) \
+  if (dtype == DT && tile == ID) return launch_tma<T, TY, NS, U, BR>(runs, tiles, ntiles, substep, grid, iso != 0, s);
   MHD_TMA_VARIANTS(X)
 #undef X
   return (int)cudaErrorInvalidValue;
