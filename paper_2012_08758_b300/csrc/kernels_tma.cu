@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(32 * TY, TY <= 6 ? 2 : 1)
   // as the output plane, which must be at least BAR planes.
   constexpr int P = NS - 3 - BAR;
   static_assert(P >= 1, "need at least one plane of prefetch");
-  static_assert(BAR >= 1 && BAR <= 4, "one to four planes between barriers");
+  static_assert(BAR >= 1 && BAR <= 8, "one to eight planes between barriers");
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * SH::STAGE_BYTES);
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -978,8 +978,10 @@ int occupancy_tma(int *bps) {
 // Tile variants of the TMA kernel: id -> (dtype, TY, stages, ring rotation
 // by 7-fold unrolling instead of register moves, planes between barriers).
 //   FP32: 1 = 32x8/6; 2 = 32x4/6; 3 = 32x8/8; 4 = 32x12/6; 5 = 32x12/5; 6 = 32x16/5;
-//         9 = 32x6/5 (two CTAs per SM); 10, 11, 12 = 32x12 with 6, 7, 8 stages
-//         and a barrier every second, third, fourth plane
+//         9 = 32x6/5 (two CTAs per SM); 10 .. 14 = 32x12 with 6 .. 10 stages
+//         and a barrier every 2nd .. 6th plane (one plane of prefetch);
+//         15, 16 = 32x12 with 9, 10 stages, a barrier every 4th, 5th plane
+//         and two planes of prefetch
 //   FP32 packed (isotropic grids; anisotropic runs fall back to the tile
 //   of the same shape above): 7 = 32x12/5; 8 = 32x8/6
 //   FP64: 1 = 32x4/6; 2 = 32x4/6 unrolled
@@ -996,10 +998,14 @@ int occupancy_tma(int *bps) {
   X(0, 10, float, 12, 6, false, 2)     \
   X(0, 11, float, 12, 7, false, 3)     \
   X(0, 12, float, 12, 8, false, 4)     \
+  X(0, 13, float, 12, 9, false, 5)     \
+  X(0, 14, float, 12, 10, false, 6)    \
+  X(0, 15, float, 12, 9, false, 4)     \
+  X(0, 16, float, 12, 10, false, 5)    \
   X(1, 1, double, 4, 6, false, 1)      \
   X(1, 2, double, 4, 6, true, 1)
 
-int tma_num_tiles(int dtype) { return dtype == 0 ? 12 : 2; }
+int tma_num_tiles(int dtype) { return dtype == 0 ? 16 : 2; }
 
 template <typename T, int TY>
 int pro_smem_bytes() {
