@@ -68,11 +68,20 @@ def test_workspace_bytes_scale_with_grid(B):
     assert 1.9 < dbl / big < 2.01 and big > small
 
 
+@pytest.mark.parametrize("dtype,tiles", [(0, range(0, 17)), (1, range(0, 3))])
+def test_every_tile_variant_is_accepted(B, dtype, tiles):
+    """FP32 TMA tiles 1-16 (shapes, stage counts, barrier spacings, packed
+    pairs) and FP64 tiles 1-2, and 0 for the default, are valid parameters."""
+    for t in tiles:
+        assert B.mhd_workspace_bytes(B.mhd_default_params(nx=40, ny=24, nz=16, kernel=2, tile=t, dtype=dtype)) > 0
+
+
 @pytest.mark.parametrize("bad,msg", [
     (dict(nx=0), "nx"), (dict(cs=0.0), "cs"), (dict(nu=-1.0), "nu"),
     (dict(f0=0.1, kmin=0.0), "shell"), (dict(f0=0.1, kmin=0.2, kmax=0.5), "no integer"),
     (dict(f0=0.1, sigma=1.5), "sigma"), (dict(dtype=7), "dtype"), (dict(forcing_mode=3), "forcing_mode"), (dict(upwind=2), "upwind"),
     (dict(cfl=0.0), "cfl"), (dict(kernel=99), "kernel"),
+    (dict(kernel=2, tile=17), "tile"), (dict(kernel=2, tile=6, dtype=1), "tile"), (dict(kernel=1, tile=3), "tile"),
 ])
 def test_invalid_parameters_are_rejected(B, bad, msg):
     with pytest.raises(B.MhdError) as e:
