@@ -984,7 +984,8 @@ int occupancy_tma(int *bps) {
 //         and two planes of prefetch
 //   FP32 packed (isotropic grids; anisotropic runs fall back to the tile
 //   of the same shape above): 7 = 32x12/5; 8 = 32x8/6
-//   FP64: 1 = 32x4/6; 2 = 32x4/6 unrolled
+//   FP64: 1 = 32x4/6; 2 = 32x4/6 unrolled; 3 = 32x8/6; 4 = 32x8/7 with a barrier every
+//         second plane
 // (the unrolled FP32 variants measured 1.7x slower on B300: the 7-fold body
 // overflows the instruction cache)
 #define MHD_TMA_VARIANTS(X)            \
@@ -1003,9 +1004,11 @@ int occupancy_tma(int *bps) {
   X(0, 15, float, 12, 9, false, 4)     \
   X(0, 16, float, 12, 10, false, 5)    \
   X(1, 1, double, 4, 6, false, 1)      \
-  X(1, 2, double, 4, 6, true, 1)
+  X(1, 2, double, 4, 6, true, 1)       \
+  X(1, 3, double, 8, 6, false, 1)      \
+  X(1, 4, double, 8, 7, false, 2)
 
-int tma_num_tiles(int dtype) { return dtype == 0 ? 16 : 2; }
+int tma_num_tiles(int dtype) { return dtype == 0 ? 16 : 4; }
 
 template <typename T, int TY>
 int pro_smem_bytes() {

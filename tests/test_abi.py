@@ -68,10 +68,10 @@ def test_workspace_bytes_scale_with_grid(B):
     assert 1.9 < dbl / big < 2.01 and big > small
 
 
-@pytest.mark.parametrize("dtype,tiles", [(0, range(0, 17)), (1, range(0, 3))])
+@pytest.mark.parametrize("dtype,tiles", [(0, range(0, 17)), (1, range(0, 5))])
 def test_every_tile_variant_is_accepted(B, dtype, tiles):
     """FP32 TMA tiles 1-16 (shapes, stage counts, barrier spacings, packed
-    pairs) and FP64 tiles 1-2, and 0 for the default, are valid parameters."""
+    pairs) and FP64 tiles 1-4, and 0 for the default, are valid parameters."""
     for t in tiles:
         assert B.mhd_workspace_bytes(B.mhd_default_params(nx=40, ny=24, nz=16, kernel=2, tile=t, dtype=dtype)) > 0
 

@@ -168,6 +168,23 @@ def test_every_tma_tile_fp32_step_parity(kernel, tile):
     run.close()
 
 
+@pytest.mark.parametrize("tile", [1, 2, 3, 4])
+def test_every_fp64_tma_tile_step_parity(tile):
+    """Each FP64 tile variant of the TMA kernel: ragged grid, 4 forced steps,
+    1e-12 of the oracle."""
+    kw = dict(nx=45, ny=37, nz=29, nu=0.01, eta=0.01, f0=0.05, sigma=1.0, kmin=1.0, kmax=2.0,
+              seed=4, dtype="f64", kernel=2, tile=tile)
+    q0 = inputs.random_modes_state(45, 37, 29, seed=12, amp=0.2)
+    run = make_run(**kw)
+    run.set_state(q0)
+    run.step(4)
+    got, _, _ = run.get_state()
+    run.close()
+    q = q0.copy()
+    O.run(oracle_params(**kw), q, 4)
+    assert rel_linf_state(got, q).max() < 1e-12
+
+
 SCALAR_TMA_TILES = [1, 2, 3, 4, 5, 6, 9, 10, 11, 12, 13, 14, 15, 16]
 
 
