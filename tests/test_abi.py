@@ -115,7 +115,7 @@ def test_seed_field_rejects_null_context(B):
 @pytest.mark.parametrize("shape,grid", [((256, 256, 256), 148), ((512, 512, 512), 148), ((64, 64, 64), 148),
                                         ((37, 23, 11), 148), ((1, 1, 1), 148), ((45, 37, 29), 444),
                                         ((256, 96, 40), 296), ((300, 200, 100), 148), ((256, 240, 128), 148)])
-@pytest.mark.parametrize("tile", [0, 2, 4])
+@pytest.mark.parametrize("tile", [0, 2, 4, 5, 9, 16])
 def test_substep_plan_covers_every_point_once(B, shape, grid, tile):
     """The work split of the fused substep: every (x-y tile, z) of the grid
     exactly once, table rectangular over the CTAs it uses, whole columns
@@ -125,7 +125,7 @@ def test_substep_plan_covers_every_point_once(B, shape, grid, tile):
     tiles, g = B.mhd_substep_plan(p, grid)
     assert 1 <= g <= grid and len(tiles) % g == 0
     tw = 32
-    th = {0: 12, 2: 4, 4: 12}[tile]
+    th = {0: 12, 2: 4, 4: 12, 5: 12, 9: 6, 16: 12}[tile]
     seen = {}
     for x0, y0, z0, z1, run in tiles:
         assert run == 0
