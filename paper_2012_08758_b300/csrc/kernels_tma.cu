@@ -7,8 +7,10 @@
 //  * a CTA owns a 32 x TY column and sweeps it along z;
 //  * every z-plane of all seven fields (with 3-point x/y halos) is brought
 //    into shared memory by one cp.async.bulk.tensor (TMA) copy, issued
-//    P = NS-4 planes ahead and completed on an mbarrier, so the memory
-//    system always has planes in flight while the SM computes;
+//    P = NS-3-BAR planes ahead and completed on an mbarrier, so the memory
+//    system always has planes in flight while the SM computes; the CTA
+//    synchronises only after every BAR-th plane, so its warps may drift
+//    apart by up to BAR planes;
 //  * each thread keeps its seven z-values of every field in registers (a
 //    pencil), so z-derivatives need no shared-memory traffic;
 //  * the mixed derivatives in the x-z and y-z planes are accumulated in
