@@ -30,3 +30,13 @@ def test_bench_rejects_too_few_warmup_steps():
     r = subprocess.run([sys.executable, "bench.py", "--warmup", "2"], cwd=ROOT, capture_output=True, text=True,
                        timeout=120)
     assert r.returncode != 0 and "warmup" in r.stderr
+
+
+def test_committed_ncu_records_match_the_kernel_sources():
+    """The DRAM-traffic and flop records under profiles/ were taken from the
+    current kernel sources: a change to the substep kernel voids them (the
+    bench line then reports traffic null) until they are captured again."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.ncu_traffic(256, "f32") is not None
+    assert bench.ncu_flops("f32") is not None and bench.ncu_flops("f64") is not None
