@@ -1,8 +1,8 @@
 """Mutation check of the oracle's pins: each case plants one plausible
 mistake (a dropped factor, a wrong sign, a transposed operand, a wrong
-index) in a scratch copy of the oracle's C source, builds it with gcc in a
-temporary folder and runs the pin suite against it; every mutant must fail.
-CPU only; the committed oracle is never modified."""
+index) in a scratch copy of the oracle's C source (built with gcc in a
+temporary folder) or of its Python side, and runs the pin suite against it;
+every mutant must fail.  CPU only; the committed oracle is never modified."""
 import os
 import subprocess
 import sys
@@ -60,4 +60,59 @@ def test_pins_reject_mutant(name, tmp_path):
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py")],
                        env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} survived the pins"
+
+
+# Mistakes planted in the Python side of the oracle (the spectrum's shells
+# and normalisation, the growth-rate fit), run against the same pins with
+# the committed C library.
+PY_SRC = os.path.join(ROOT, "oracle", "oracle.py")
+PY_MUTANTS = {
+    "shell_floor_not_nearest": ("np.floor(np.sqrt(K2) + 0.5)", "np.floor(np.sqrt(K2))"),
+    "spectrum_half_dropped": ("return 0.5 * np.bincount", "return 1.0 * np.bincount"),
+    "spectrum_norm_once": ("/ float(n) ** 2", "/ float(n)"),
+    "spectrum_drops_kx": (" + kx[None, None, :] ** 2", ""),
+    "growth_fit_intercept": ("np.polyfit(t, y, 1)[0]", "np.polyfit(t, y, 1)[1]"),
+    "growth_fit_no_log": ("y = np.log(np.asarray(brms, dtype=np.float64))",
+                          "y = np.asarray(brms, dtype=np.float64)"),
+}
+
+
+def _run_pins_with_python_oracle(tmp_path, src):
+    """Pins against a scratch package `oracle` whose oracle.py is `src`
+    (the committed C library loaded through ORACLE_LIB_OVERRIDE)."""
+    from oracle import oracle as O
+    lib = O.build()
+    import shutil
+    pkg = tmp_path / "root"
+    (pkg / "oracle").mkdir(parents=True)
+    (pkg / "oracle" / "__init__.py").write_text("")
+    (pkg / "oracle" / "oracle.py").write_text(src)
+    # the pins and their helpers, copied so that their root (put first on
+    # sys.path by the copied conftest) is the scratch one
+    tests = pkg / "tests"
+    tests.mkdir()
+    for f in ("__init__.py", "conftest.py", "states.py", "test_oracle_pins.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), tests / f)
+    shutil.copytree(os.path.join(ROOT, "tests", "golden"), tests / "golden")
+    env = dict(os.environ, ORACLE_LIB_OVERRIDE=lib,
+               PYTHONPATH=os.pathsep.join([str(pkg), ROOT, os.environ.get("PYTHONPATH", "")]))
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                           str(tests / "test_oracle_pins.py")],
+                          env=env, cwd=str(pkg), capture_output=True, text=True, timeout=600)
+
+
+def test_python_mutation_harness_passes_the_unmodified_oracle(tmp_path):
+    """Control: the harness itself (scratch package, library override) lets
+    the committed oracle pass, so a failing mutant fails for its mistake."""
+    r = _run_pins_with_python_oracle(tmp_path, open(PY_SRC).read())
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_pins_reject_python_mutant(name, tmp_path):
+    before, after = PY_MUTANTS[name]
+    src = open(PY_SRC).read()
+    assert src.count(before) == 1, f"mutation site not unique/found: {name}"
+    r = _run_pins_with_python_oracle(tmp_path, src.replace(before, after))
     assert r.returncode != 0, f"mutant {name} survived the pins"
