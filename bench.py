@@ -1,13 +1,16 @@
 #!/usr/bin/env python
 """Benchmark of one forced isothermal MHD time step on a B300.
 
-Workload (N=1): 256^3 periodic box, FP32 fields and arithmetic, helical
-forcing (sigma = 1, shell 2.5 <= |k| <= 3.5, k_f ~ 3.13, f0 = 0.02),
-nu = eta = 1.6e-4 (Re_M ~ 100 for u_rms ~ 0.05), CFL time step (0.4).  A
-step = device time-step reduction + forcing draw + three fused RHS/RK3-2N
-substeps, all of it inside the timed region.  Inputs are synthetic (seeded
-weak-field initial condition of Sec. 4) and larger than L2 (1.5 GB of
-state), so no L2 flush is needed between steps.
+Workload (N=1 line): 512^3 periodic box, FP32 fields and arithmetic,
+helical forcing (sigma = 1, shell 2.5 <= |k| <= 3.5, k_f ~ 3.13, f0 = 0.02),
+nu = eta = 6.4e-5 (Re_M ~ 250 for u_rms ~ 0.05), CFL time step (0.4), the
+paper's weak-seed-field initial condition (Sec. 4) generated on the device.
+A step = device time-step reduction + forcing draw + three fused RHS/RK3-2N
+substeps, all of it inside the timed region.  Inputs are larger than L2
+(11.7 GB of state), so no L2 flush is needed between steps.  The same line
+carries the FP64 step on the same workload, the batched ensemble (16 x 64^3
++ 8 x 128^3) against one-at-a-time stepping, and the continuous-batching
+serving loop's p50/p99 latency.
 
 Prints ONE JSON line.  --impl reference times the FP64 CPU oracle on the
 host cores instead (a deliberately slow baseline, not a target)."""
@@ -32,12 +35,31 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-updates/s & %HBM roofline, FP32 vs FP64; batched p50/p99 job latency"
 UNIT = "cell-updates/s"
 BYTES_PER_CELL = {"f32": 70 * 4, "f64": 70 * 8}  # algorithmic: 70 values per cell-update
-WORKLOAD = dict(f0=0.02, sigma=1.0, kmin=2.5, kmax=3.5, nu=1.6e-4, eta=1.6e-4, cfl=0.4, seed=1)
+KF = 3.134           # mean |k| of the 98-vector shell 2.5 <= |k| <= 3.5
+URMS0 = 0.05         # rms velocity estimate of the f0 = 0.02 forced flow
+SEED_AMP = 1e-5      # seed-field amplitude (Sec. 4)
+
+
+def re_m(n):
+    """Magnetic Reynolds number of the n^3 single-run workload: ~250 at 512^3
+    (the at-scale configuration), ~100 otherwise (the 256^3 configuration)."""
+    return 250.0 if n >= 512 else 100.0
+
+
+def workload(n):
+    nu = URMS0 / (re_m(n) * KF)
+    return dict(f0=0.02, sigma=1.0, kmin=2.5, kmax=3.5, nu=nu, eta=nu, cfl=0.4, seed=1)
+
+
+# kept for the other workloads (C2 at 256^3, spectra, CPU timings)
+WORKLOAD = workload(256)
 
 
 def workload_name(n, dtype):
+    w = workload(n)
     return (f"{n}^3 forced isothermal MHD step ({dtype.upper()}): helical sigma=1, shell [2.5,3.5] "
-            f"(k_f~3.13), f0=0.02, nu=eta=1.6e-4 (Re_M~100), CFL 0.4, seed-field initial state")
+            f"(k_f~3.13), f0=0.02, nu=eta={w['nu']:.2g} (Re_M~{re_m(n):.0f}), CFL 0.4, seed field 1e-5 "
+            f"(Sec. 4) generated on the device")
 
 
 def measured_peaks():
@@ -147,14 +169,15 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def cpu_baseline(seconds=12.0, n=64):
-    """The FP64 oracle, as it stands, on the host cores: cell-updates/s on
-    whole steps of an n^3 sample of the same workload."""
+def _oracle_steps(n, cores, seconds, max_steps=200):
+    """Whole FP64 oracle steps of the n^3 version of the workload on `cores`
+    host threads (host-tuned build): (steps, seconds, threads used)."""
     from oracle import oracle as O
     from paper_2012_08758_b300 import inputs
 
-    cores = O.set_threads(os.cpu_count() or 1)
-    p = O.Params(nx=n, ny=n, nz=n, **WORKLOAD)
+    O.use_native()
+    used = O.set_threads(cores)
+    p = O.Params(nx=n, ny=n, nz=n, **workload(n))
     q = inputs.seed_field_state(n, seed=0)
     O.run(p, q, 1)  # warm-up
     steps, t0 = 0, time.perf_counter()
@@ -162,11 +185,26 @@ def cpu_baseline(seconds=12.0, n=64):
         O.run(p, q, 1, step0=1 + steps)
         steps += 1
         el = time.perf_counter() - t0
-        if el > seconds or steps >= 200:
+        if el > seconds or steps >= max_steps:
             break
-    return {"value": n ** 3 * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} full steps of the {n}^3 version of the workload (FP64 oracle, "
-                      f"OpenMP over z-planes), {el:.1f} s"}
+    return steps, el, used
+
+
+def cpu_baseline(seconds=12.0, n=64, one_core_seconds=8.0):
+    """The FP64 oracle, as it stands (gcc -O3 -march=native, ISO C11, OpenMP
+    over z-planes), on the host cores: cell-updates/s on whole steps of an n^3
+    sample of the same workload (its cost per point does not depend on the
+    grid), on all cores and on one core."""
+    allc = os.cpu_count() or 1
+    steps, el, used = _oracle_steps(n, allc, seconds)
+    s1, e1, _ = _oracle_steps(n, 1, one_core_seconds)
+    from oracle import oracle as O
+    O.set_threads(allc)
+    return {"value": n ** 3 * steps / el, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"{steps} whole steps of the {n}^3 version of the workload (FP64 oracle, gcc -O3 "
+                      f"-march=native, OpenMP over z-planes), {el:.1f} s",
+            "one_core": {"value": n ** 3 * s1 / e1, "cores": 1,
+                         "sample": f"{s1} whole {n}^3 steps on one thread, {e1:.1f} s"}}
 
 
 def dist_setup():
@@ -184,25 +222,43 @@ def step_config(n, dtype, world):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores (there is no
+    upstream code).  Each step is a bounded sample of the workload -- one
+    whole oracle step of its 64^3 version (the cost per point does not depend
+    on the grid) -- W untimed and K timed, so value, ms_per_step and the
+    wall time are all this run's own."""
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
-    # the oracle's cost per point does not depend on the grid, so each step is
-    # a bounded sample: whole steps of the 64^3 version of the same workload
-    cb = cpu_baseline(seconds=min(60.0, max(5.0, 0.1 * args.steps)), n=64)
-    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+    from oracle import oracle as O
+    from paper_2012_08758_b300 import inputs
+
+    ns = 64
+    O.use_native()
+    cores = O.set_threads(os.cpu_count() or 1)
+    p = O.Params(nx=ns, ny=ns, nz=ns, **workload(args.n))
+    q = inputs.seed_field_state(ns, seed=0)
+    O.run(p, q, args.warmup)
+    t0 = time.perf_counter()
+    O.run(p, q, args.steps, step0=args.warmup)
+    el = time.perf_counter() - t0
+    value = ns ** 3 * args.steps / el
+    sample = (f"each step: one whole step of the {ns}^3 version of the workload (FP64 oracle, gcc -O3 "
+              f"-march=native, OpenMP over z-planes, {cores} threads); {args.warmup} untimed + "
+              f"{args.steps} timed steps, {el:.1f} s")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * args.n ** 3 / cb["value"], "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": step_config(args.n, args.dtype, world),
-            "cpu_baseline": cb,
-            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "sample": {"grid": ns, "cells_per_step": ns ** 3, "note": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
 def run_ours(args):
-    import numpy as np
     import torch
 
     world, rank, local = dist_setup()
@@ -212,16 +268,20 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     from paper_2012_08758_b300 import binding as B
-    from paper_2012_08758_b300 import inputs
+    from paper_2012_08758_b300.replicas import replica_seed
     from paper_2012_08758_b300.run import Run
 
     n, dtype = args.n, args.dtype
     cells = n ** 3
+    wl = workload(n)
     run = Run(n=n, device=dev, dtype=B.MHD_F32 if dtype == "f32" else B.MHD_F64, kernel=args.kernel,
-              tile=args.tile, **dict(WORKLOAD, seed=WORKLOAD["seed"] + rank))
-    from paper_2012_08758_b300.replicas import replica_seed
-    q0 = inputs.seed_field_state(n, seed=replica_seed(0, rank))
-    run.set_state(q0)
+              tile=args.tile, **dict(wl, seed=wl["seed"] + rank))
+    seed_key = replica_seed(0, rank)
+    run.set_seed_field(seed_key, SEED_AMP)  # the paper's initial condition, on the device
+    # host copy of the initial state (pinned), for the end-to-end leg
+    hdt = torch.float32 if dtype == "f32" else torch.float64
+    host_in = torch.empty((7, n, n, n), dtype=hdt).pin_memory().numpy()
+    B.mhd_get_state(run.ctx, host_in)
     run.step(args.warmup)
     run.sync()
 
@@ -245,19 +305,20 @@ def run_ours(args):
     achieved = bpc * cells * args.steps / (sub_ms / 1e3) / 1e9
     peak, peak_src = measured_peaks()
     traffic = ncu_traffic(n, dtype)
+    step_gbs = bpc * cells * args.steps / (total_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": "k_substep (fused RHS + RK3-2N), 3 launches per step",
             "algorithmic_bytes_per_cell_update": bpc, "peak_source": peak_src,
+            "traffic_over_algorithmic": None if traffic is None else traffic / (bpc / 3 * cells),
+            "whole_step": {"achieved": step_gbs, "frac": step_gbs / peak,
+                           "note": "the same algorithmic bytes over the whole step (prologue included)"},
             "stage_ms_per_step": {"prologue": stage_ms[0] / args.steps,
                                   "substep1": stage_ms[1] / args.steps,
                                   "substep2": stage_ms[2] / args.steps,
                                   "substep3": stage_ms[3] / args.steps}}
 
     # --- end to end through the public API with host buffers ---
-    pinned = torch.empty(q0.shape, dtype=torch.float32 if dtype == "f32" else torch.float64).pin_memory()
-    host_in = pinned.numpy()
-    host_in[...] = q0
-    host_out = torch.empty_like(pinned).pin_memory().numpy()
+    host_out = torch.empty((7, n, n, n), dtype=hdt).pin_memory().numpy()
     e2e_steps = args.steps
     barrier()
     t0 = time.perf_counter()
@@ -274,16 +335,29 @@ def run_ours(args):
            "d2h_bytes_per_step": (state_bytes + 8 * e2e_steps) / e2e_steps,
            "note": "per job: state upload from pinned host memory, K x (mhd_step(1) + mhd_reduce(B_rms)), "
                    "state download"}
+    run.close()
+    del host_in, host_out
 
     # --- FP64 beside FP32 on the same workload (few steps: ALU-bound) ---
     fp64 = None
     if dtype == "f32" and not args.skip_fp64:
-        run64 = Run(n=n, device=dev, dtype=B.MHD_F64, **WORKLOAD)
-        run64.set_state(q0)
+        run64 = Run(n=n, device=dev, dtype=B.MHD_F64, **dict(wl, seed=wl["seed"] + rank))
+        run64.set_seed_field(seed_key, SEED_AMP)
         run64.step(1)
         run64.sync()
-        st64, tot64 = B.mhd_step_timed(run64.ctx, 3)
+        k64 = args.fp64_steps
+        st64, tot64 = B.mhd_step_timed(run64.ctx, k64)
+        d64 = run64.diagnostics()
         run64.close()
+        # per-quantity FP32 error against FP64 after the same 1 + k64 steps
+        # from the same initial state (the at-scale configuration's check)
+        run32 = Run(n=n, device=dev, dtype=B.MHD_F32, **dict(wl, seed=wl["seed"] + rank))
+        run32.set_seed_field(seed_key, SEED_AMP)
+        run32.step(1 + k64)
+        d32 = run32.diagnostics()
+        run32.close()
+        err32 = {k: abs(d32[k] - d64[k]) / max(abs(d64[k]), 1e-300)
+                 for k in ("urms", "brms", "umax", "bmax", "ekin", "emag", "mass", "vmax")}
         sub64 = sum(st64[1:4])
         peaks = alu_peaks()
         fl64 = ncu_flops("f64")
@@ -291,12 +365,13 @@ def run_ours(args):
                "peak_source": "measured FP64 FMA chains on this GPU (mhd_alu_peak)",
                "flops_per_cell_update": fl64, "achieved": None, "frac": None}
         if fl64:
-            alu["achieved"] = fl64 * cells * 3 / (sub64 / 1e3) / 1e12
+            alu["achieved"] = fl64 * cells * k64 / (sub64 / 1e3) / 1e12
             alu["frac"] = alu["achieved"] / alu["peak"]
-        fp64 = {"value": cells * 3 / (tot64 / 1e3), "unit": UNIT, "steps": 3,
-                "ms_per_step": tot64 / 3,
-                "hbm_frac": BYTES_PER_CELL["f64"] * cells * 3 / (sub64 / 1e3) / 1e9 / peak,
+        fp64 = {"value": cells * k64 / (tot64 / 1e3), "unit": UNIT, "steps": k64, "grid": n,
+                "ms_per_step": tot64 / k64,
+                "hbm_frac": BYTES_PER_CELL["f64"] * cells * k64 / (sub64 / 1e3) / 1e9 / peak,
                 "roofline": alu,
+                "fp32_rel_err": {"steps": 1 + k64, **err32},
                 "fma_peaks_tflops": {k: v / 1e12 for k, v in peaks.items()}}
         fl32 = ncu_flops("f32")
         if fl32:
@@ -305,7 +380,14 @@ def run_ours(args):
                            "flops_per_cell_update": fl32,
                            "peak_source": "measured FP32 FMA chains on this GPU (mhd_alu_peak)"}
             roof["alu"]["frac"] = roof["alu"]["achieved"] / roof["alu"]["peak"]
-    run.close()
+
+    # --- batched ensemble and serving loop (C4, C5), rank 0 of a 1-GPU job ---
+    batch = serve = None
+    if world == 1 and not args.skip_batch:
+        batch = measure_batch(steps=args.batch_steps, warmup=3, tune=False)
+    if world == 1 and not args.skip_serve:
+        serve = measure_serve(requests=args.requests, rate=args.serve_rate, scale=args.serve_scale,
+                              chunk=args.serve_chunk, checks=args.serve_checks)
 
     cb = cpu_baseline() if (rank == 0 and world == 1 and not args.skip_cpu) else None
     if rank == 0:
@@ -314,6 +396,7 @@ def run_ours(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                 "config": step_config(n, dtype, world),
                 "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "fp64": fp64,
+                "batch": batch, "serving": serve,
                 "gpu_launches": 4 * args.steps, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -321,41 +404,45 @@ def run_ours(args):
     return 0
 
 
-def run_batch(args):
+BATCH_SIZES = [64] * 16 + [128] * 8
+
+
+def measure_batch(steps=20, warmup=3, tune=True):
     """C4: 16 x 64^3 + 8 x 128^3 runs, nu = eta log-spaced for Re_M 5-250,
-    alternating helicity, FP32; one batch (persistent launch per stage, CUDA
-    graph) against the same runs stepped one at a time."""
+    alternating helicity, FP32 with FP64 reductions; one batch (one launch
+    per kernel stage over the combined tile table, k steps replayed from a
+    CUDA graph) against the same runs stepped one at a time.  Device time
+    with CUDA events on the runs' stream."""
     import torch
 
     from paper_2012_08758_b300 import autotune
     from paper_2012_08758_b300 import binding as B
-    from paper_2012_08758_b300 import inputs
     from paper_2012_08758_b300.run import Batch, Run
-    from paper_2012_08758_b300.serving import KF
 
-    sizes = [64] * 16 + [128] * 8
+    sizes = BATCH_SIZES
     rems = np.exp(np.linspace(np.log(5.0), np.log(250.0), len(sizes)))
-    best = autotune.tune([(n, n, n) for n in sizes], B.MHD_F32, steps=3)
+    best = autotune.tune([(n, n, n) for n in sizes], B.MHD_F32, steps=3) if tune else \
+        {"kernel": 0, "tile": 0, "note": "default variant (no autotuning in this line)"}
     cells = sum(n ** 3 for n in sizes)
 
     def make():
         runs = []
         for i, (n, rem) in enumerate(zip(sizes, rems)):
-            nu = 0.05 / (rem * KF)
+            nu = URMS0 / (rem * KF)
             r = Run(n=n, nu=nu, eta=nu, f0=0.02, sigma=float(i % 2), seed=100 + i, kernel=best["kernel"],
                     tile=best["tile"])
-            r.set_state(inputs.seed_field_state(n, seed=i))
+            r.set_seed_field(10_000 + i, SEED_AMP)
             runs.append(r)
         return runs
 
     runs = make()
     b = Batch(runs)
-    b.step(args.warmup)
+    b.step(warmup)
     torch.cuda.synchronize()
     stream = runs[0].stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    b.step(args.steps)
+    b.step(steps)
     e1.record(stream)
     e1.synchronize()
     t_batch = e0.elapsed_time(e1) / 1e3
@@ -366,42 +453,38 @@ def run_batch(args):
         r.close()
     runs = make()
     for r in runs:
-        r.step(args.warmup)
+        r.step(warmup)
     torch.cuda.synchronize()
     e0.record(stream)
     for r in runs:
-        r.step(args.steps)
+        r.step(steps)
     e1.record(stream)
     e1.synchronize()
     t_serial = e0.elapsed_time(e1) / 1e3
     for r in runs:
         r.close()
-    line = {"workload": "batch: 16x64^3 + 8x128^3, Re_M 5-250 log-spaced, sigma 0/1 alternating, FP32",
-            "metric": UNIT, "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
-            "batched": cells * args.steps / t_batch, "one_at_a_time": cells * args.steps / t_serial,
-            "speedup": t_serial / t_batch, "autotune": best, "cells": cells}
-    print(json.dumps(line), flush=True)
-    return 0
+    return {"workload": "batch: 16x64^3 + 8x128^3, Re_M 5-250 log-spaced, sigma 0/1 alternating, FP32",
+            "unit": UNIT, "steps": steps, "warmup": warmup,
+            "batched": cells * steps / t_batch, "one_at_a_time": cells * steps / t_serial,
+            "speedup": t_serial / t_batch, "variant": best, "cells": cells,
+            "launches": "4 per step (prologue + 3 substeps) over all 24 runs, replayed from a CUDA graph"}
 
 
-def run_serve(args):
+def measure_serve(requests=200, rate=4.0, scale=0.1, chunk=25, checks=6):
     """C5: Poisson stream of seeded requests (grid uniform over {64, 96, 128,
     192, 256}, Re_M log-uniform 10-250, sigma in {0, 1}); the step budgets
-    are the config's 500-5000 scaled by --serve-scale.  Continuous batching
-    under a 150 GB HBM budget; p50/p99 latency and aggregate throughput,
-    against serial FP64 stepping of the same work (per-size FP64 rates
-    measured here) and growth rates against FP64 runs of the smallest
-    requests."""
-    import torch
-
+    are the config's 500-5000 times `scale`.  Continuous batching under a
+    150 GB HBM budget; p50/p99 latency and aggregate throughput, against
+    serial FP64 stepping of the same work (per-size FP64 rates measured here)
+    and growth rates against FP64 runs of the smallest requests."""
     from paper_2012_08758_b300 import binding as B
+    from paper_2012_08758_b300.growth import brms_series, fit_last
     from paper_2012_08758_b300.run import Run
     from paper_2012_08758_b300.serving import Server, requests_from_inputs, run_params, start, summarize
-    from paper_2012_08758_b300.growth import brms_series, fit_last
 
-    lo, hi = int(500 * args.serve_scale), int(5000 * args.serve_scale)
-    reqs = requests_from_inputs(n=args.requests, seed=2025, rate=args.serve_rate, steps=(max(lo, 20), max(hi, 40)))
-    srv = Server(budget_bytes=150e9, chunk=args.serve_chunk)
+    lo, hi = max(int(500 * scale), 20), max(int(5000 * scale), 40)
+    reqs = requests_from_inputs(n=requests, seed=2025, rate=rate, steps=(lo, hi))
+    srv = Server(budget_bytes=150e9, chunk=chunk)
     t0 = time.perf_counter()
     res = srv.serve(reqs, realtime=True)
     wall = time.perf_counter() - t0
@@ -415,12 +498,13 @@ def run_serve(args):
         st, tot = B.mhd_step_timed(rr.ctx, 3)
         rates[n] = n ** 3 * 3 / (tot / 1e3)
         rr.close()
+    work = sum(r.n ** 3 * r.steps for r in reqs)
     t_serial64 = sum(r.n ** 3 * r.steps / rates[r.n] for r in reqs)
     # growth-rate accuracy: the served FP32 result equals the FP32 run alone
     # (tested bit for bit), so FP32 and FP64 runs of the same request with the
     # same sampling are compared, for the smallest requests
-    checks = []
-    for r in sorted(reqs, key=lambda q: q.n ** 3 * q.steps)[: args.serve_checks]:
+    cks = []
+    for r in sorted(reqs, key=lambda q: q.n ** 3 * q.steps)[:checks]:
         lam = {}
         for dt in (B.MHD_F32, B.MHD_F64):
             rr = Run(**run_params(r, dtype=dt))
@@ -428,16 +512,27 @@ def run_serve(args):
             ts, bs = brms_series(rr, r.steps, max(1, r.steps // 40))
             rr.close()
             lam[dt] = fit_last(ts, bs, 0.5)
-        checks.append({"id": r.id, "n": r.n, "steps": r.steps, "lambda_f32": lam[B.MHD_F32],
-                       "lambda_f64": lam[B.MHD_F64],
-                       "rel_diff": abs(lam[B.MHD_F32] - lam[B.MHD_F64]) / max(abs(lam[B.MHD_F64]), 1e-300)})
-    line = {"workload": f"serve: {args.requests} Poisson requests (rate {args.serve_rate}/s), steps "
-                        f"{max(lo, 20)}-{max(hi, 40)}, FP32 continuous batching, 150 GB budget",
-            "metric": "p50/p99 job latency and aggregate cell-updates/s", **summ,
-            "serial_fp64_cell_updates_per_s": sum(r.n ** 3 * r.steps for r in reqs) / t_serial64,
-            "speedup_vs_serial_fp64": summ["cell_updates_per_s"] / (sum(r.n ** 3 * r.steps for r in reqs) / t_serial64),
-            "fp64_rates": rates, "growth_rate_checks": checks,
-            "max_growth_rate_rel_diff": max((c["rel_diff"] for c in checks), default=None)}
+        cks.append({"id": r.id, "n": r.n, "steps": r.steps, "lambda_f32": lam[B.MHD_F32],
+                    "lambda_f64": lam[B.MHD_F64],
+                    "rel_diff": abs(lam[B.MHD_F32] - lam[B.MHD_F64]) / max(abs(lam[B.MHD_F64]), 1e-300)})
+    return {"workload": f"serve: {requests} Poisson requests (rate {rate}/s), step budgets {lo}-{hi} "
+                        f"(the config's 500-5000 scaled by {scale}), FP32 continuous batching, 150 GB budget",
+            "metric": "p50/p99 job latency and aggregate cell-updates/s", "budget_scale": scale, **summ,
+            "serial_fp64_cell_updates_per_s": work / t_serial64,
+            "speedup_vs_serial_fp64": summ["cell_updates_per_s"] / (work / t_serial64),
+            "fp64_rates": rates, "growth_rate_checks": cks,
+            "max_growth_rate_rel_diff": max((c["rel_diff"] for c in cks), default=None)}
+
+
+def run_batch(args):
+    line = measure_batch(steps=args.steps, warmup=args.warmup, tune=not args.no_tune)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    line = measure_serve(requests=args.requests, rate=args.serve_rate, scale=args.serve_scale,
+                         chunk=args.serve_chunk, checks=args.serve_checks)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -717,10 +812,10 @@ def run_fp32vs64(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--workload", choices=["step", "batch", "serve", "fp32vs64", "paper", "spectrum", "tables",
                                            "c2", "cpu"],
@@ -748,6 +843,11 @@ def main():
     ap.add_argument("--tile", type=int, default=0, help="tile variant id (0: default)")
     ap.add_argument("--skip-cpu", action="store_true", help="omit the CPU-baseline leg")
     ap.add_argument("--skip-fp64", action="store_true", help="omit the FP64 side measurement")
+    ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 leg")
+    ap.add_argument("--skip-batch", action="store_true", help="omit the batched-ensemble leg")
+    ap.add_argument("--skip-serve", action="store_true", help="omit the serving leg")
+    ap.add_argument("--batch-steps", type=int, default=20, help="timed steps of the batched-ensemble leg")
+    ap.add_argument("--no-tune", action="store_true", help="batch workload: default variant, no autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -272,8 +272,9 @@ void mhd_batch_destroy(mhd_batch *b);
  * and can fail once another allocator has reserved the memory.
  *
  * Computes the MHD_NREDUCE quantities of mhd_diagnostics (same order, same
- * definitions) for a state the caller already holds on the device; no
- * context is involved.
+ * definitions; per-point values formed in the working precision and summed
+ * in FP64, as mhd_diagnostics does) for a state the caller already holds on
+ * the device; no context of this library is involved.
  *   state_dev  device pointer, read only: 7*nx*ny*nz values of `dtype`
  *              (MHD_F32 or MHD_F64), dense SoA without ghost zones, x fastest,
  *              fields ln rho, u_x, u_y, u_z, A_x, A_y, A_z (periodic box).
@@ -285,9 +286,12 @@ void mhd_batch_destroy(mhd_batch *b);
  * is one static device array of 256 KiB inside this library, which every GPU
  * that loads the library keeps until the process exits.  That bounds the grid
  * to MHD_NOALLOC_MAX_POINTS points (2^24, e.g. 256^3); larger grids are
- * rejected with MHD_EINVAL and a message saying so.  The first call on a
- * device looks up the device address of the array with that device current;
- * make that first call before any stream capture.  All calls share the one
+ * rejected with MHD_EINVAL and a message saying so.  The array exists once
+ * per CUDA context: the first call in a context (the calling thread's current
+ * one; the device's primary context if none is current) looks up the array's
+ * device address there and caches it under the context's unique id, so a
+ * device reset or another context gets its own lookup at its first call.
+ * Make that first call before any stream capture.  All calls share the one
  * array, which keeps the last call's partials: the counter is cleared at the
  * start of every call, but calls whose work overlaps on the GPU (different
  * streams or threads without ordering) race and give wrong results -- order

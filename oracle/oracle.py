@@ -30,15 +30,28 @@ LIB = os.environ.get("ORACLE_LIB_OVERRIDE") or os.path.join(HERE, "liboracle.so"
 DIAG_NAMES = ("urms", "brms", "umax", "bmax", "ekin", "emag", "divb_max", "mass", "vmax")
 
 
+# gcc flags of every build of the oracle (ISO C11: no contraction of a*b+c
+# into fused multiply-adds, so every build rounds the same operations).
+CFLAGS = ("-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11")
+# The timed CPU baseline's build: the same source and rounding, tuned for the
+# host it runs on (built there, next to nothing else, on first use).
+CFLAGS_NATIVE = ("-O3", "-march=native", "-fopenmp", "-fPIC", "-shared", "-std=c11")
+
+
+def compile_oracle(src: str, out: str, flags=CFLAGS) -> str:
+    """gcc `src` into the shared library `out` with `flags`."""
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", *flags, "-o", tmp, src, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile liboracle.so with gcc (OpenMP over z-planes of the RHS)."""
     if os.environ.get("ORACLE_LIB_OVERRIDE"):
         return LIB
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp, SRC, "-lm"]
-        subprocess.check_call(cmd)
-        os.replace(tmp, LIB)
+        compile_oracle(SRC, LIB)
     return LIB
 
 
@@ -96,13 +109,39 @@ class Params:
         return (7, self.nz, self.ny, self.nx)
 
 
+def host_tag() -> str:
+    """Short hash of this host's CPU model and flags (a -march=native build
+    is only valid on a CPU like the one it was built on)."""
+    import hashlib
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = [l for l in f if l.startswith(("model name", "flags"))][:2]
+    except OSError:
+        info = []
+    return hashlib.sha256("".join(info).encode()).hexdigest()[:12]
+
+
+def use_native() -> str:
+    """Switch this process to the host-tuned build (CFLAGS_NATIVE), compiled
+    on first use for this host's CPU; same source, same rounding.  Used by
+    the timed CPU baseline only."""
+    global LIB, _lib
+    path = os.path.join(HERE, f"liboracle_native_{host_tag()}.so")
+    if not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(SRC):
+        compile_oracle(SRC, path, CFLAGS_NATIVE)
+    if LIB != path:
+        LIB, _lib = path, None
+    return path
+
+
 _lib = None
 
 
 def lib():
     global _lib
     if _lib is None:
-        build()
+        if not os.path.basename(LIB).startswith("liboracle_native_"):
+            build()
         L = C.CDLL(LIB)
         dp = C.POINTER(C.c_double)
         pp = C.POINTER(OrcParams)

@@ -2,6 +2,7 @@
 // not allocate device memory.  Its scratch (per-block partial sums and the
 // last-block counter) is a file-scope static device array of fixed size
 // instead of a context workspace.  See include/mhd.h for the contract.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -31,26 +32,63 @@ int na_fail(int code, const char *msg) {
   return code;
 }
 
-// Device address of g_noalloc_scratch, looked up once per device with that
-// device current.  In host code the symbol name is only a host-side stand-in;
-// the kernel must be given this address.
-constexpr int NA_MAX_DEVICES = 64;
+// Device address of g_noalloc_scratch in the calling thread's current CUDA
+// context.  In host code the symbol name is only a host-side stand-in; the
+// kernel must be given this address.  The array is instantiated once per
+// context, so the address is looked up with cudaGetSymbolAddress once per
+// context and cached under the context's unique id (cuCtxGetId): a device
+// reset or a new context has a new id and gets a fresh lookup at its first
+// call, and a cached address is never used in a context it does not belong to.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+template <typename F>
+F driver_fn(const char *name) {
+  void *f = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess)
+    return nullptr;
+  return reinterpret_cast<F>(f);
+}
+
+constexpr int NA_CACHE = 64;
 std::mutex g_na_mu;
-void *g_na_addr[NA_MAX_DEVICES] = {};
+unsigned long long g_na_ctx[NA_CACHE] = {};  // context ids (0: empty slot)
+void *g_na_addr[NA_CACHE] = {};
+int g_na_next = 0;
 
 int scratch_address(void **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return na_fail(MHD_ECUDA, cudaGetErrorString(e));
-  if (dev < 0 || dev >= NA_MAX_DEVICES) return na_fail(MHD_EINVAL, "device index out of range");
-  std::lock_guard<std::mutex> lock(g_na_mu);
-  if (!g_na_addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  static CtxGetCurrentFn get_current = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent");
+  static CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId");
+  if (!get_current || !get_id) return na_fail(MHD_ECUDA, "cuCtxGetCurrent / cuCtxGetId not available from the driver");
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS) return na_fail(MHD_ECUDA, "cuCtxGetCurrent failed");
+  cudaError_t e;
+  if (!ctx) {
+    // no context yet on this thread: make the current device's primary
+    // context current (cudaSetDevice initialises it; nothing is allocated)
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaSetDevice(dev);
     if (e != cudaSuccess) return na_fail(MHD_ECUDA, cudaGetErrorString(e));
-    g_na_addr[dev] = p;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return na_fail(MHD_ECUDA, "no current CUDA context");
   }
-  *out = g_na_addr[dev];
+  unsigned long long id = 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return na_fail(MHD_ECUDA, "cuCtxGetId failed");
+  std::lock_guard<std::mutex> lock(g_na_mu);
+  for (int i = 0; i < NA_CACHE; ++i)
+    if (g_na_ctx[i] == id) {
+      *out = g_na_addr[i];
+      return MHD_OK;
+    }
+  void *p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return na_fail(MHD_ECUDA, cudaGetErrorString(e));
+  g_na_ctx[g_na_next] = id;
+  g_na_addr[g_na_next] = p;
+  g_na_next = (g_na_next + 1) % NA_CACHE;
+  *out = p;
   return MHD_OK;
 }
 
@@ -69,14 +107,14 @@ __device__ __forceinline__ long long at(const DenseGrid &g, int i, int j, int k)
   return ((long long)k * g.ny + j) * g.nx + i;
 }
 
-// First derivative along `ax` of field f at (i, j, k), periodic wrap; same
-// weights and operation order as the context path.
+// First derivative along `ax` of field f at (i, j, k), periodic wrap, with
+// the fixed rounding sequence every reduction of the library uses (d1_vals).
 template <typename T>
 __device__ __forceinline__ T d1w(const DenseGrid &g, const T *f, int i, int j, int k, int ax,
                                  const T *w) {
   const int di = ax == 0, dj = ax == 1, dk = ax == 2;
   auto v = [&](int s) { return f[at<T>(g, i + s * di, j + s * dj, k + s * dk)]; };
-  return w[1] * (v(1) - v(-1)) + w[2] * (v(2) - v(-2)) + w[3] * (v(3) - v(-3));
+  return d1_vals(v(1), v(-1), v(2), v(-2), v(3), v(-3), w);
 }
 
 // Component c of B = curl A at (i, j, k).
@@ -98,42 +136,38 @@ __global__ void __launch_bounds__(NA_THREADS)
   T w[3][4];
   for (int a = 0; a < 3; ++a)
     for (int s = 0; s < 4; ++s) w[a][s] = T(W1(s) * g.inv_h[a]);
-  double su2 = 0, sb2 = 0, sk = 0, sm = 0, mu = 0, mb = 0, mv = 0, md = 0;
+  // per-point values in the working precision, sums accumulated in FP64,
+  // maxima kept in the working precision (exact): as mhd_diagnostics forms them
+  double su2 = 0, sb2 = 0, sk = 0, sm = 0;
+  T mu = 0, mb = 0, mv = 0, md = 0;
+  const T cs2 = T(g.cs2);
   const long long base = (long long)blockIdx.x * NA_CELLS_PER_BLOCK;
   for (int r = 0; r < NA_CELLS_PER_THREAD; ++r) {
     const long long c = base + (long long)r * NA_THREADS + threadIdx.x;
     if (c >= g.n) break;
     const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((long long)g.nx * g.ny));
-    const double ux = q[g.n + c], uy = q[2 * g.n + c], uz = q[3 * g.n + c];
-    const double bx = curl_c(g, q, i, j, k, 0, w), by = curl_c(g, q, i, j, k, 1, w),
-                 bz = curl_c(g, q, i, j, k, 2, w);
-    T div = T(0);
-    {
-      // div B with the first-derivative stencil applied to B itself
-      T dx = T(0), dy = T(0), dz = T(0);
-      dx = w[0][1] * (curl_c(g, q, i + 1, j, k, 0, w) - curl_c(g, q, i - 1, j, k, 0, w)) +
-           w[0][2] * (curl_c(g, q, i + 2, j, k, 0, w) - curl_c(g, q, i - 2, j, k, 0, w)) +
-           w[0][3] * (curl_c(g, q, i + 3, j, k, 0, w) - curl_c(g, q, i - 3, j, k, 0, w));
-      dy = w[1][1] * (curl_c(g, q, i, j + 1, k, 1, w) - curl_c(g, q, i, j - 1, k, 1, w)) +
-           w[1][2] * (curl_c(g, q, i, j + 2, k, 1, w) - curl_c(g, q, i, j - 2, k, 1, w)) +
-           w[1][3] * (curl_c(g, q, i, j + 3, k, 1, w) - curl_c(g, q, i, j - 3, k, 1, w));
-      dz = w[2][1] * (curl_c(g, q, i, j, k + 1, 2, w) - curl_c(g, q, i, j, k - 1, 2, w)) +
-           w[2][2] * (curl_c(g, q, i, j, k + 2, 2, w) - curl_c(g, q, i, j, k - 2, 2, w)) +
-           w[2][3] * (curl_c(g, q, i, j, k + 3, 2, w) - curl_c(g, q, i, j, k - 3, 2, w));
-      div = dx + dy + dz;
-    }
-    const double u2 = ux * ux + uy * uy + uz * uz, b2 = bx * bx + by * by + bz * bz;
-    const double rho = exp((double)q[c]);
-    su2 += u2;
-    sb2 += b2;
-    sk += rho * u2;
-    sm += rho;
-    mu = fmax(mu, sqrt(u2));
+    const T ux = q[g.n + c], uy = q[2 * g.n + c], uz = q[3 * g.n + c];
+    const T bx = curl_c(g, q, i, j, k, 0, w), by = curl_c(g, q, i, j, k, 1, w), bz = curl_c(g, q, i, j, k, 2, w);
+    // div B with the first-derivative stencil applied to B itself
+    auto bxa = [&](int s) { return curl_c(g, q, i + s, j, k, 0, w); };
+    auto bya = [&](int s) { return curl_c(g, q, i, j + s, k, 1, w); };
+    auto bza = [&](int s) { return curl_c(g, q, i, j, k + s, 2, w); };
+    const T div = d1_vals(bxa(1), bxa(-1), bxa(2), bxa(-2), bxa(3), bxa(-3), w[0]) +
+                  d1_vals(bya(1), bya(-1), bya(2), bya(-2), bya(3), bya(-3), w[1]) +
+                  d1_vals(bza(1), bza(-1), bza(2), bza(-2), bza(3), bza(-3), w[2]);
+    const T u2 = ux * ux + uy * uy + uz * uz, b2 = norm2_rn(bx, by, bz);
+    const T rho = exp(q[c]);
+    const T umag = sqrt(u2);
+    su2 += (double)u2;
+    sb2 += (double)b2;
+    sk += (double)(rho * u2);
+    sm += (double)rho;
+    mu = fmax(mu, umag);
     mb = fmax(mb, sqrt(b2));
-    mv = fmax(mv, sqrt(u2) + sqrt(g.cs2 + b2 / rho));
-    md = fmax(md, fabs((double)div));
+    mv = fmax(mv, umag + sqrt(cs2 + b2 / rho));
+    md = fmax(md, fabs(div));
   }
-  const double vals[NPART] = {su2, sb2, sk, sm, mu, mb, mv, md};
+  const double vals[NPART] = {su2, sb2, sk, sm, (double)mu, (double)mb, (double)mv, (double)md};
   const int t = threadIdx.x;
   for (int v = 0; v < NPART; ++v) {
     const double r = v < 4 ? block_sum(vals[v], sh) : block_max(vals[v], sh);

@@ -6,12 +6,17 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_prints_one_complete_line():
+    import time
+    t0 = time.perf_counter()
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "3"],
                        cwd=ROOT, capture_output=True, text=True, timeout=300)
+    wall = time.perf_counter() - t0
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
     assert len(lines) == 1
@@ -20,7 +25,11 @@ def test_reference_arm_prints_one_complete_line():
                 "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in d, key
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
-    assert d["config"]["grid"] == 256 and "workload" in d["config"]
+    assert d["config"]["grid"] == 512 and "workload" in d["config"]
+    # the line reports what this run measured: its K timed steps fit in the
+    # wall time of the whole command, and each step is the stated sample
+    assert d["steps"] * d["ms_per_step"] / 1e3 < wall
+    assert d["value"] == pytest.approx(d["sample"]["cells_per_step"] / (d["ms_per_step"] / 1e3), rel=1e-9)
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

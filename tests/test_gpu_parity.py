@@ -1,8 +1,9 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
 the same seeded inputs.  Tolerances: states, relative L-infinity per field
-with the scale of its physical quantity (tests/gpu_util.rel_linf_state):
-FP64 1e-12, FP32 2e-5; right-hand sides, relative L-infinity per field:
-FP64 1e-12, FP32 1e-5."""
+with the scale of its physical quantity (tests/gpu_util.rel_linf_state) and,
+for every u / A component that is not degenerate, with its own max|q|
+(tests/gpu_util.per_field_linf): FP64 1e-12, FP32 2e-5; right-hand sides,
+relative L-infinity per field: FP64 1e-12, FP32 1e-5."""
 import math
 
 import numpy as np
@@ -10,7 +11,8 @@ import pytest
 
 from oracle import oracle as O
 from paper_2012_08758_b300 import inputs
-from tests.gpu_util import gpu_params, oracle_params, rel_linf, rel_linf_state
+from tests.gpu_util import (assert_state_matches, gpu_params, oracle_params, oracle_state, rel_linf,
+                            rel_linf_state)
 from tests.states import coords, k2sq_mod, rk3_gain
 
 pytestmark = pytest.mark.gpu
@@ -99,7 +101,7 @@ def test_rhs_with_unequal_box_lengths(dtype, tol, kernel, tile):
     got_q, _, _ = run.get_state()
     q1 = q.copy()
     O.run(p, q1, 3)
-    assert rel_linf_state(got_q, q1, cs=0.9).max() < (1e-12 if dtype == "f64" else 2e-5)
+    assert_state_matches(got_q, q1, dtype, cs=0.9)
     run.close()
 
 
@@ -125,8 +127,7 @@ def test_c1_step_parity(dtype, tol, kernel, tile):
         got, t_gpu, step_gpu = run.get_state()
         assert step_gpu == target
         assert abs(t_gpu - t_or) <= (1e-13 if dtype == "f64" else 1e-6) * t_or
-        err = rel_linf_state(got, q, cs=1.0)
-        assert err.max() < tol, (target, err, rel_linf(got, q))
+        assert_state_matches(got, q, dtype, cs=1.0, what=f"after step {target}")
     run.close()
 
 
@@ -143,8 +144,7 @@ def test_ragged_and_degenerate_step_parity(shape, kernel, tile):
     got, t, _ = run.get_state()
     q = q0.copy()
     O.run(oracle_params(**kw), q, 4)
-    err = rel_linf_state(got, q)
-    assert err.max() < 1e-12, err
+    assert_state_matches(got, q, "f64")
     run.close()
 
 
@@ -160,7 +160,7 @@ def test_every_tma_tile_fp32_step_parity(kernel, tile):
     got, _, _ = run.get_state()
     q = q0.copy()
     O.run(oracle_params(**kw), q, 5)
-    assert rel_linf_state(got, q).max() < 2e-5
+    assert_state_matches(got, q, "f32")
     d = run.diagnostics()  # reductions run with this tile's block shape
     o = O.diagnostics(oracle_params(**kw), q)
     for key in ("urms", "brms", "ekin", "emag", "mass", "vmax"):
@@ -182,7 +182,7 @@ def test_every_fp64_tma_tile_step_parity(tile):
     run.close()
     q = q0.copy()
     O.run(oracle_params(**kw), q, 4)
-    assert rel_linf_state(got, q).max() < 1e-12
+    assert_state_matches(got, q, "f64")
 
 
 SCALAR_TMA_TILES = [1, 2, 3, 4, 5, 6, 9, 10, 11, 12, 13, 14, 15, 16]
@@ -257,8 +257,7 @@ def test_upwinded_step_parity(dtype, tol):
     q = q0.copy()
     t_or, _ = O.run(oracle_params(**kw), q, 10)
     assert abs(t_gpu - t_or) <= (1e-13 if dtype == "f64" else 1e-6) * t_or
-    err = rel_linf_state(got, q, cs=1.0)
-    assert err.max() < tol, err
+    assert_state_matches(got, q, dtype, cs=1.0)
     run.close()
 
 
@@ -272,7 +271,7 @@ def test_forcing_once_per_step_mode():
     got, _, _ = run.get_state()
     q = q0.copy()
     O.run(oracle_params(**kw), q, 3)
-    assert rel_linf_state(got, q).max() < 1e-12
+    assert_state_matches(got, q, "f64")
     run.close()
 
 
@@ -286,7 +285,7 @@ def test_fixed_dt_and_clock():
     assert step == 12 and abs(t - (2.0 + 5 * 1.19209e-3)) < 1e-14
     q = q0.copy()
     O.run(oracle_params(**kw), q, 5, step0=7)
-    assert rel_linf_state(got, q).max() < 1e-12
+    assert_state_matches(got, q, "f64")
     tt, dtl, st = run.time()
     assert dtl == 1.19209e-3 and st == 12
     run.close()
@@ -465,7 +464,7 @@ def test_ideal_mhd_step_parity(dtype, tol, kernel, tile):
     q = q0.copy()
     t_o, _ = O.run(oracle_params(**kw), q, 5)
     assert abs(t - t_o) <= (1e-13 if dtype == "f64" else 1e-6) * t_o
-    assert rel_linf_state(got, q).max() < tol
+    assert_state_matches(got, q, dtype)
     run.close()
 
 
@@ -566,10 +565,50 @@ def test_batch_is_bitwise_identical_to_alone():
     b = Batch(runs)
     b.step(5)  # graph of 5 steps
     b.step(2)  # replay path / direct remainder
-    for r, ref in zip(runs, alone):
-        got, _, step = r.get_state(dtype=np.float32)
+    for c, q0, r, ref in zip(cfgs, states, runs, alone):
+        got, t, step = r.get_state(dtype=np.float32)
         assert step == 7
         assert np.array_equal(got, ref)
+        # and the batched run against the FP64 oracle from the same state
+        want, t_or = oracle_state(q0, 7, **c)
+        assert abs(t - t_or) <= 1e-6 * t_or
+        assert_state_matches(got.astype(np.float64), want, "f32", what=str(c))
+        d, o = r.diagnostics(), O.diagnostics(oracle_params(**c), want)
+        for key in ("urms", "brms", "ekin", "emag", "mass", "vmax"):
+            assert d[key] == pytest.approx(o[key], rel=2e-5), (c, key)
+    b.close()
+    for r in runs:
+        r.close()
+
+
+def test_fp64_batch_matches_oracle():
+    """An FP64 batch of three runs of different sizes (one ragged, one
+    anisotropic, forced and unforced, CFL and fixed dt), stepped with a
+    captured graph and its remainder: each run within 1e-12 of the FP64
+    oracle, diagnostics within 1e-12."""
+    from paper_2012_08758_b300.run import Batch
+    cfgs = [dict(nx=32, ny=32, nz=32, f0=0.02, sigma=1.0, seed=1, nu=4e-3, eta=4e-3, dtype="f64"),
+            dict(nx=37, ny=23, nz=11, f0=0.05, sigma=0.0, seed=2, nu=5e-3, eta=3e-3, dtype="f64", upwind=1),
+            dict(nx=24, ny=20, nz=28, lx=4.0, ly=3.0, lz=3.5, f0=0.0, seed=3, nu=5e-3, eta=5e-3,
+                 dt_fixed=3e-3, dtype="f64")]
+    states = [inputs.random_modes_state(c["nx"], c["ny"], c["nz"], seed=30 + i, amp=0.15)
+              + inputs.noise_state(c["nx"], c["ny"], c["nz"], seed=40 + i, amp=1e-3)
+              for i, c in enumerate(cfgs)]
+    runs = [make_run(**c) for c in cfgs]
+    for r, q in zip(runs, states):
+        r.set_state(q)
+    b = Batch(runs)
+    b.step(4)
+    b.step(2)
+    for c, q0, r in zip(cfgs, states, runs):
+        got, t, step = r.get_state()
+        assert step == 6
+        want, t_or = oracle_state(q0, 6, **c)
+        assert abs(t - t_or) <= 1e-13 * t_or
+        assert_state_matches(got, want, "f64", what=str(c))
+        d, o = r.diagnostics(), O.diagnostics(oracle_params(**c), want)
+        for key in ("urms", "brms", "ekin", "emag", "mass", "vmax", "umax", "bmax"):
+            assert d[key] == pytest.approx(o[key], rel=1e-12), (c, key)
     b.close()
     for r in runs:
         r.close()
@@ -598,9 +637,12 @@ def test_batch_honours_each_runs_own_options():
         r.set_state(q)
     b = Batch(runs)
     b.step(6)
-    for r, ref in zip(runs, alone):
+    for c, q0, r, ref in zip(cfgs, states, runs, alone):
         got, _, step = r.get_state(dtype=np.float32)
         assert step == 6 and np.array_equal(got, ref)
+        want, _ = oracle_state(q0, 6, **c)
+        cs = c.get("cs", 1.0)
+        assert_state_matches(got.astype(np.float64), want, "f32", cs=cs, what=str(c))
     b.close()
     for r in runs:
         r.close()
@@ -647,7 +689,7 @@ def test_bounded_wait_gives_up_and_leaves_the_gpu_usable():
     got, _, _ = run.get_state()
     q = q0.copy()
     O.run(oracle_params(**kw), q, 2)
-    assert rel_linf_state(got, q).max() < 1e-12
+    assert_state_matches(got, q, "f64")
     run.close()
 
 

@@ -1,7 +1,8 @@
 """Batching and serving: each run's result is the same alone and inside a
 continuously batched serving loop (bit for bit: per-run reductions have a
-fixed order and substeps are pointwise); the autotuner returns a variant
-that runs; admission honours the HBM budget."""
+fixed order and substeps are pointwise) and matches the FP64 oracle from the
+same initial state; the autotuner returns a variant that runs; admission
+honours the HBM budget."""
 import numpy as np
 import pytest
 
@@ -39,6 +40,52 @@ def test_serving_results_equal_runs_alone():
             assert r.diagnostics[key] == d[key], key
         assert r.latency >= 0 and r.finished >= r.admitted >= 0
         assert np.isfinite(r.growth_rate)
+
+
+def _oracle_series(req, steps):
+    """The FP64 oracle from the request's initial state (host copy of the
+    device generator): t and B_rms after every step, final state."""
+    from oracle import oracle as O
+    from paper_2012_08758_b300.serving import initial_state, run_params
+    from tests.gpu_util import oracle_params
+    p = oracle_params(**run_params(req))
+    q = initial_state(req)
+    ts, bs = [0.0], [O.diagnostics(p, q)["brms"]]
+    w = np.zeros_like(q)
+    t = 0.0
+    for n in range(steps):
+        dt, _ = O.step(p, q, n, w)
+        t += dt
+        ts.append(t)
+        bs.append(O.diagnostics(p, q)["brms"])
+    return np.array(ts), np.array(bs), q, p
+
+
+def test_served_results_match_the_oracle():
+    """Each served run (FP32, stepped in chunks inside changing batches)
+    against the FP64 oracle from the same initial state: the B_rms sample
+    of every chunk and the final diagnostics within 2e-5, the growth rate
+    fitted over the same samples within 1%."""
+    from oracle import oracle as O
+    from paper_2012_08758_b300.growth import fit_last
+    from paper_2012_08758_b300.serving import Server
+
+    reqs = _requests()
+    srv = Server(chunk=10, time_scale=1.0)
+    res = {r.id: r for r in srv.serve(reqs, realtime=True)}
+    for req in reqs:
+        r = res[req.id]
+        ts, bs, q, p = _oracle_series(req, req.steps)
+        # every sample sits at some step; its time picks that step out
+        idx = [int(np.argmin(np.abs(ts - t))) for t in r.t]
+        assert idx[-1] == req.steps and len(set(idx)) == len(idx)
+        np.testing.assert_allclose(r.t, ts[idx], rtol=1e-6, atol=0)
+        np.testing.assert_allclose(r.brms, bs[idx], rtol=2e-5, atol=0)
+        lam = fit_last(ts[idx], bs[idx], srv.window)
+        assert r.growth_rate == pytest.approx(lam, rel=1e-2, abs=1e-6), (req, r.growth_rate, lam)
+        o = O.diagnostics(p, q)
+        for key in ("urms", "brms", "ekin", "emag", "mass", "vmax"):
+            assert r.diagnostics[key] == pytest.approx(o[key], rel=2e-5), (req.id, key)
 
 
 def test_admission_respects_budget():

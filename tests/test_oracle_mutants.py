@@ -44,7 +44,32 @@ MUTANTS = {
     "upwind_downstream": ("uu[a] >= 0.0 ? 1 : -1", "uu[a] >= 0.0 ? -1 : 1"),
     "upwind_weight": ("+ 30.0 * f[1] - 3.0 * f[2]", "+ 30.0 * f[1] - 2.0 * f[2]"),
     "upwind_ignored": ("p->upwind ? orc_dup", "0 ? orc_dup"),
+    "mode1_third_dt": ("q[(1 + a) * n + c] += dt * f[a];", "q[(1 + a) * n + c] += dt / 3.0 * f[a];"),
+    "mode1_into_A": ("q[(1 + a) * n + c] += dt * f[a];", "q[(4 + a) * n + c] += dt * f[a];"),
+    "mode1_sign": ("q[(1 + a) * n + c] += dt * f[a];", "q[(1 + a) * n + c] -= dt * f[a];"),
+    "mode1_also_in_rhs": ("p->forcing_mode == 0) orc_forcing_at", "p->forcing_mode >= 0) orc_forcing_at"),
 }
+
+
+def _run_pins_with_c_source(tmp_path, src):
+    """Pins against a scratch build of the C source `src`, compiled with the
+    oracle's own flags and loaded through ORACLE_LIB_OVERRIDE."""
+    from oracle import oracle as O
+    mut = tmp_path / "mutant.c"
+    mut.write_text(src)
+    lib = O.compile_oracle(str(mut), str(tmp_path / "libmutant.so"))
+    env = dict(os.environ, ORACLE_LIB_OVERRIDE=lib)
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                           os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                          env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+
+
+def test_c_mutation_harness_passes_the_unmodified_oracle(tmp_path):
+    """Control: the unmodified source through the same scratch build and
+    library override passes every pin, so a failing mutant fails for its
+    planted mistake and not for the harness."""
+    r = _run_pins_with_c_source(tmp_path, open(SRC).read())
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
@@ -52,14 +77,7 @@ def test_pins_reject_mutant(name, tmp_path):
     before, after = MUTANTS[name]
     src = open(SRC).read()
     assert src.count(before) == 1, f"mutation site not unique/found: {name}"
-    mut = tmp_path / "mutant.c"
-    mut.write_text(src.replace(before, after))
-    lib = tmp_path / "libmutant.so"
-    subprocess.check_call(["gcc", "-O1", "-fopenmp", "-fPIC", "-shared", "-o", str(lib), str(mut), "-lm"])
-    env = dict(os.environ, ORACLE_LIB_OVERRIDE=str(lib))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
-                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    r = _run_pins_with_c_source(tmp_path, src.replace(before, after))
     assert r.returncode != 0, f"mutant {name} survived the pins"
 
 

@@ -557,6 +557,49 @@ def test_forcing_field_is_a_single_fourier_mode():
         assert np.abs(spec).max() < 1e-10
 
 
+def test_forcing_once_per_step_adds_dt_f_to_u():
+    """Forcing mode 1 (the alternative reading of where the forcing enters
+    the RK step): a gas at rest with uniform density, A = 0 and no diffusion
+    has a zero right-hand side without forcing, so one step leaves ln rho and
+    A as they were and sets u to dt * f(x) -- once, with the step's own dt in
+    the normalisation of Eq. 5 and the draw of that step index."""
+    nx, ny, nz, dt = 12, 10, 8, 0.013
+    p = O.Params(nx=nx, ny=ny, nz=nz, nu=0.0, eta=0.0, f0=0.05, sigma=0.7, kmin=2.5, kmax=3.5,
+                 seed=5, dt_fixed=dt, forcing_mode=1)
+    q = zero_state(nx, ny, nz)
+    q[0] = 0.3
+    d, F = O.step(p, q, step_index=4)
+    assert d == dt
+    G = O.forcing_draw(p, 4, dt=dt)
+    assert F.k == G.k and F.amp == G.amp
+    f = O.forcing_field(p, G)
+    np.testing.assert_allclose(q[1:4], dt * f, rtol=0, atol=1e-16)
+    assert np.abs(q[1:4]).max() > 1e-4  # the forcing is really there
+    assert np.all(q[0] == 0.3) and np.all(q[4:] == 0.0)
+
+
+def test_forcing_once_per_step_is_the_unforced_step_plus_dt_f():
+    """On a general state, forcing mode 1 equals the unforced RK3 step (same
+    dt) followed by u += dt * f of the step's draw; mode 0 differs from it
+    only at second order in dt (RK3 applies a constant forcing with total
+    weight dt over the three substeps)."""
+    from paper_2012_08758_b300.inputs import random_modes_state
+    n, dt = 10, 0.004
+    base = dict(nx=n, ny=n, nz=n, nu=0.02, eta=0.03, f0=0.05, sigma=0.4, seed=9, dt_fixed=dt)
+    q0 = random_modes_state(n, seed=3, amp=0.2, kmax=2, nmodes=4)
+    q1 = q0.copy()
+    O.step(O.Params(**base, forcing_mode=1), q1, step_index=2)
+    qu = q0.copy()
+    O.step(O.Params(**dict(base, f0=0.0)), qu, step_index=2)
+    f = O.forcing_field(O.Params(**base), O.forcing_draw(O.Params(**base), 2, dt=dt))
+    np.testing.assert_allclose(q1[[0, 4, 5, 6]], qu[[0, 4, 5, 6]], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(q1[1:4], qu[1:4] + dt * f, rtol=0, atol=1e-15)
+    q0m = q0.copy()
+    O.step(O.Params(**base, forcing_mode=0), q0m, step_index=2)
+    diff = np.abs(q0m - q1).max()
+    assert 0 < diff < 20 * dt * dt * np.abs(f).max()
+
+
 def test_forcing_draw_covers_shell_uniformly():
     p = O.Params(f0=0.02, kmin=2.5, kmax=3.5, seed=77)
     sh = {tuple(v) for v in O.kshell(2.5, 3.5)}
