@@ -620,93 +620,26 @@ def paper_tables():
     return rows
 
 
-def shell_mean_k(kmin, kmax):
-    K = int(math.floor(kmax))
-    ks = [math.sqrt(a * a + b * b + c * c) for a in range(-K, K + 1) for b in range(-K, K + 1)
-          for c in range(-K, K + 1) if kmin <= math.sqrt(a * a + b * b + c * c) <= kmax]
-    return sum(ks) / len(ks)
-
-
 def run_tables(args):
-    """Kinematic growth rates at the setup of the paper's Tables 1-2 (Sec. 4:
-    shell 4.5 <= |k| <= 5.5, nu = eta, seed field 1e-5, upwinding on, CFL
-    0.4), all rows of the chosen grids stepped as one FP32 batch to
-    t = --tables-tmax.  The forcing scale f0 (--tables-f0) defaults to 0.029,
-    calibrated so that the first row of Table 1 (64^3, eta = 5e-3, helical)
-    has the printed Re_M = 3.6: the paper's f0 = 0.08 with Eq. 5 as printed
-    drives u_rms about 2.7 times higher than its tables report.  lambda = slope of ln B_rms over t in [100, t_b], t_b the
-    end of the run or the first sample with B_rms > 0.1 u_rms (the field
-    starts to act back); Re_M = <u_rms> over that window / (eta k_f), k_f the
-    mean |k| of the shell."""
-    from paper_2012_08758_b300 import binding as B
-    from paper_2012_08758_b300 import inputs
-    from paper_2012_08758_b300.growth import growth_rate
-    from paper_2012_08758_b300.run import Batch, Run
+    """Kinematic growth rates at the setup of the paper's Tables 1-2 (rows of
+    the chosen grids, --tables-seeds forcing realisations each), stepped as one
+    FP32 batch to t = --tables-tmax (paper_2012_08758_b300.tables); the JSON
+    record goes to stdout and, with --tables-out, to that file."""
+    from paper_2012_08758_b300 import tables
 
     grids = [int(g) for g in args.tables_grids.split(",")]
     etas = [float(e) for e in args.tables_eta.split(",")] if args.tables_eta else None
     rows = [dict(r, realisation=s) for r in paper_tables() if r["n"] in grids and (etas is None or r["eta"] in etas)
             for s in range(args.tables_seeds)]
-    kf = shell_mean_k(4.5, 5.5)
-    runs, series, spectra, live = [], [], [], []
-    for i, r in enumerate(rows):
-        run = Run(n=r["n"], nu=r["eta"], eta=r["eta"], f0=args.tables_f0, kmin=4.5, kmax=5.5, sigma=r["sigma"],
-                  seed=1000 + i + 7919 * r["realisation"], upwind=args.tables_upwind, cfl=0.4)
-        run.set_state(inputs.seed_field_state(r["n"], seed=i, amp=1e-5))
-        d = run.diagnostics()
-        runs.append(run)
-        series.append([(0.0, d["brms"], d["urms"])])
-        spectra.append([run.spectrum()] if args.tables_spectra else [])
-        live.append(i)
-    status = ["ok"] * len(rows)
-    t0 = time.perf_counter()
-    steps = 0
-    batch = None
-    while live:
-        if batch is None:
-            batch = Batch([runs[i] for i in live])
-        batch.step(args.tables_chunk)
-        steps += args.tables_chunk
-        done = []
-        for i in live:
-            try:
-                d = runs[i].diagnostics()
-            except B.MhdError as e:
-                status[i] = f"failed: {e}"
-                done.append(i)
-                continue
-            t = runs[i].time()[0]
-            series[i].append((t, d["brms"], d["urms"]))
-            if args.tables_spectra:
-                spectra[i].append(runs[i].spectrum())
-            if t >= args.tables_tmax:
-                done.append(i)
-        if done:
-            batch.close()
-            batch = None
-            live = [i for i in live if i not in done]
-    wall = time.perf_counter() - t0
-    out = []
-    for i, r in enumerate(rows):
-        runs[i].close()
-        ts, bs, us = (np.array(c) for c in zip(*series[i]))
-        m = ts >= 100.0
-        sat = np.nonzero(m & (bs > 0.1 * us))[0]
-        if len(sat):
-            m &= ts < ts[sat[0]]
-        res = dict(sigma=r["sigma"], n=r["n"], eta=r["eta"], lambda_paper=r["lam"], rem_paper=r["rem"],
-                   realisation=r["realisation"], status=status[i], t_end=float(ts[-1]))
-        if args.tables_series:
-            res["series"] = {"t": ts.tolist(), "brms": bs.tolist(), "urms": us.tolist()}
-        if status[i] == "ok" and m.sum() >= 3:
-            res.update(lambda_=growth_rate(ts[m], bs[m]), rem=float(us[m].mean() / (r["eta"] * kf)),
-                       window=[float(ts[m][0]), float(ts[m][-1])])
-            if args.tables_spectra:
-                E = np.array(spectra[i])[m]
-                res["lambda_k"] = {k: 0.5 * growth_rate(ts[m], E[:, k]) for k in (1, 5, 9) if k < E.shape[1]}
-        out.append(res)
-    print(json.dumps({"workload": f"growth rates at the setup of Tables 1-2, grids {grids}, t <= {args.tables_tmax}",
-                      "f0": args.tables_f0, "k_f": kf, "steps": steps, "wall_s": wall, "rows": out}), flush=True)
+    res = tables.run_rows(rows, f0=args.tables_f0, tmax=args.tables_tmax, chunk=args.tables_chunk,
+                          upwind=args.tables_upwind, spectra=args.tables_spectra, series=args.tables_series)
+    line = {"workload": f"growth rates at the setup of Tables 1-2, grids {grids}, "
+                        f"{args.tables_seeds} realisation(s) per row, t <= {args.tables_tmax}",
+            "command": "python bench.py " + " ".join(sys.argv[1:]), **res}
+    if args.tables_out:
+        with open(args.tables_out, "w") as f:
+            json.dump(line, f, indent=1)
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -830,9 +763,10 @@ def main():
     ap.add_argument("--serve-chunk", type=int, default=25)
     ap.add_argument("--serve-checks", type=int, default=6)
     ap.add_argument("--tables-grids", default="64", help="grids of the Tables 1-2 rows to run")
-    ap.add_argument("--tables-tmax", type=float, default=600.0)
+    ap.add_argument("--tables-tmax", type=float, default=400.0)
     ap.add_argument("--tables-chunk", type=int, default=200)
     ap.add_argument("--tables-f0", type=float, default=0.029)
+    ap.add_argument("--tables-out", default="", help="also write the tables record (JSON) to this file")
     ap.add_argument("--tables-eta", default="", help="comma-separated eta values to keep (default: all rows)")
     ap.add_argument("--tables-seeds", type=int, default=1, help="forcing realisations per table row")
     ap.add_argument("--tables-series", action="store_true", help="include the (t, B_rms, u_rms) samples")

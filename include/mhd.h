@@ -263,6 +263,54 @@ int mhd_batch_step(mhd_batch *b, int nsteps);
 /* Releases the batch (not the contexts).  NULL is ignored. */
 void mhd_batch_destroy(mhd_batch *b);
 
+/* ---- z-slab domain decomposition (Sec. 3.3 and 3.4) -----------------------
+ * The grid is cut along z into nslabs slabs of nz/nslabs planes (the first
+ * nz mod nslabs slabs one plane more), each a context of its own, as the
+ * paper decomposes its domain over GPUs.  Every substep, each slab sends its
+ * three planes nearest a face -- all seven fields, with their x/y ghost
+ * columns -- into the ghost planes of the neighbour across that face
+ * (periodically: the last slab's top neighbour is the first slab); the time
+ * step is the minimum over all slabs (one reduction of the CFL maxima of all
+ * slabs), and the forcing is evaluated at global z.  With overlap = 1 each
+ * substep first computes the slabs' outer planes (within three of a face),
+ * then the exchange runs on a second stream while the inner planes are
+ * computed, as in the paper's inner/outer split; overlap = 0 computes all
+ * planes, then exchanges.  The substep arithmetic per point is that of the
+ * undecomposed run, so the decomposed state equals it bit for bit; the
+ * diagnostics are summed over the slabs' tiles in another order (equal up to
+ * rounding).  All slabs live on the current device (one GPU); the exchange
+ * is one cudaMemcpy2DAsync per face and direction.  Requires the TMA kernel
+ * (MHD_KERNEL_AUTO or MHD_KERNEL_TMA) and at least 3 planes per slab.
+ * Errors are reported by mhd_last_error(NULL). */
+typedef struct mhd_slabs mhd_slabs;
+
+/* Creates the decomposition of the grid of p into nslabs z-slabs on the
+ * current device, ordered on `stream` (NULL: legacy stream).  The state is
+ * zero at t = 0, step 0.  Synchronising.  Errors: MHD_EINVAL (bad parameters,
+ * nslabs < 1, fewer than 3 planes per slab, the plane-ring kernel),
+ * MHD_ENOMEM, MHD_ECUDA. */
+int mhd_slabs_create(const mhd_params *p, int nslabs, int overlap, void *stream, mhd_slabs **out);
+
+/* First global plane *z0 and plane count *nz of slab `slab`.  Host only. */
+int mhd_slabs_extent(const mhd_slabs *s, int slab, int *z0, int *nz);
+
+/* As mhd_set_state / mhd_get_state for the whole grid: host_soa holds 7 *
+ * nx*ny*nz values (SoA, x fastest); each slab takes or gives its planes.
+ * Synchronising. */
+int mhd_slabs_set_state(mhd_slabs *s, const void *host_soa, int host_dtype, double t, int64_t step);
+int mhd_slabs_get_state(mhd_slabs *s, void *host_soa, int host_dtype, double *t, int64_t *step);
+
+/* Enqueues nsteps steps of the decomposed run.  Asynchronous. */
+int mhd_slabs_step(mhd_slabs *s, int nsteps);
+
+/* The MHD_NREDUCE diagnostics of the whole grid into out[MHD_NREDUCE]
+ * (B = curl A per slab, B's ghost planes exchanged, one reduction over all
+ * slabs' tiles).  Synchronising. */
+int mhd_slabs_diagnostics(mhd_slabs *s, double *out);
+
+/* Releases the slabs and their device memory.  NULL is ignored. */
+void mhd_slabs_destroy(mhd_slabs *s);
+
 /* ---- diagnostics without device allocation ---------------------------------
  * The paper has no counterpart to this entry point.  It serves callers that
  * cannot allocate device memory: a plugin inside an application whose own

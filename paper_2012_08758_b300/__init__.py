@@ -19,6 +19,8 @@ _BINDING_NAMES = {
     "REDUCE_NAMES", "MHD_URMS", "MHD_BRMS", "MHD_UMAX", "MHD_BMAX", "MHD_EKIN", "MHD_EMAG",
     "MHD_DIVB_MAX", "MHD_MASS", "MHD_VMAX", "MHD_NREDUCE", "MHD_KERNEL_AUTO", "MHD_KERNEL_SMEM",
     "MHD_KERNEL_TMA", "mhd_diagnostics_noalloc", "MHD_NOALLOC_MAX_POINTS", "mhd_alu_peak", "MHD_F32X2", "mhd_spectrum", "mhd_spectrum_shells", "mhd_set_seed_field", "mhd_substep_plan", "mhd_padding_check", "mhd_wait_selftest",
+    "mhd_slabs_create", "mhd_slabs_extent", "mhd_slabs_set_state", "mhd_slabs_get_state", "mhd_slabs_step",
+    "mhd_slabs_diagnostics", "mhd_slabs_destroy",
 }
 
 
@@ -29,4 +31,7 @@ def __getattr__(name):
     if name in ("Run", "Batch"):
         from . import run
         return getattr(run, name)
+    if name == "Slabs":
+        from . import slabs
+        return slabs.Slabs
     raise AttributeError(name)

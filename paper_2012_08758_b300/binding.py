@@ -86,6 +86,13 @@ def lib():
             "mhd_substep_plan": (C.c_int, [pp, C.c_int, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int),
                                            C.POINTER(C.c_int)]),
             "mhd_spectrum": (C.c_int, [vp, dp, C.c_int, C.POINTER(C.c_int)]),
+            "mhd_slabs_create": (C.c_int, [pp, C.c_int, C.c_int, vp, C.POINTER(vp)]),
+            "mhd_slabs_extent": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+            "mhd_slabs_set_state": (C.c_int, [vp, vp, C.c_int, C.c_double, i64]),
+            "mhd_slabs_get_state": (C.c_int, [vp, vp, C.c_int, dp, C.POINTER(i64)]),
+            "mhd_slabs_step": (C.c_int, [vp, C.c_int]),
+            "mhd_slabs_diagnostics": (C.c_int, [vp, dp]),
+            "mhd_slabs_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -236,6 +243,49 @@ def mhd_batch_step(batch: int, nsteps: int) -> None:
 
 def mhd_batch_destroy(batch: int) -> None:
     lib().mhd_batch_destroy(C.c_void_p(batch))
+
+
+def mhd_slabs_create(p: MhdParams, nslabs: int, overlap: int = 1, stream: int = 0) -> int:
+    """The grid of p decomposed into nslabs z-slabs on the current device."""
+    out = C.c_void_p()
+    _check(lib().mhd_slabs_create(C.byref(p), int(nslabs), int(overlap), C.c_void_p(stream or None),
+                                  C.byref(out)))
+    return out.value
+
+
+def mhd_slabs_extent(slabs: int, slab: int) -> tuple[int, int]:
+    z0, nz = C.c_int(), C.c_int()
+    _check(lib().mhd_slabs_extent(C.c_void_p(slabs), int(slab), C.byref(z0), C.byref(nz)))
+    return z0.value, nz.value
+
+
+def mhd_slabs_set_state(slabs: int, q: np.ndarray, t: float = 0.0, step: int = 0) -> None:
+    q = np.ascontiguousarray(q)
+    dt = MHD_F32 if q.dtype == np.float32 else MHD_F64
+    q = q if q.dtype in (np.float32, np.float64) else q.astype(np.float64)
+    _check(lib().mhd_slabs_set_state(C.c_void_p(slabs), q.ctypes.data_as(C.c_void_p), dt, float(t), int(step)))
+
+
+def mhd_slabs_get_state(slabs: int, shape, dtype=np.float64):
+    out = np.empty(shape, dtype=dtype)
+    t, st = C.c_double(), C.c_int64()
+    _check(lib().mhd_slabs_get_state(C.c_void_p(slabs), out.ctypes.data_as(C.c_void_p),
+                                     MHD_F32 if out.dtype == np.float32 else MHD_F64, C.byref(t), C.byref(st)))
+    return out, t.value, st.value
+
+
+def mhd_slabs_step(slabs: int, nsteps: int) -> None:
+    _check(lib().mhd_slabs_step(C.c_void_p(slabs), int(nsteps)))
+
+
+def mhd_slabs_diagnostics(slabs: int) -> dict:
+    out = (C.c_double * MHD_NREDUCE)()
+    _check(lib().mhd_slabs_diagnostics(C.c_void_p(slabs), out))
+    return dict(zip(REDUCE_NAMES, list(out)))
+
+
+def mhd_slabs_destroy(slabs: int) -> None:
+    lib().mhd_slabs_destroy(C.c_void_p(slabs))
 
 
 MHD_NOALLOC_MAX_POINTS = 1 << 24

@@ -123,10 +123,13 @@ constexpr double MIN_SHARE = 6.0;  // smallest remainder share, in weighted plan
 
 struct SubCol {
   int run, x0, y0, nz;
-  double w;  // work per plane relative to a full tile
+  double w;    // work per plane relative to a full tile
+  int zb = 0;  // first interior plane of the column's z-range
 };
 
-void add_columns(std::vector<SubCol> *cols, int run, int nx, int ny, int nz, int tw, int th) {
+// Columns of planes zb .. zb + nz - 1 of one run (zb > 0: the inner or outer
+// z-range of a slab of a decomposed domain).
+void add_columns(std::vector<SubCol> *cols, int run, int nx, int ny, int nz, int tw, int th, int zb = 0) {
   for (int y0 = 0; y0 < ny; y0 += th)
     for (int x0 = 0; x0 < nx; x0 += tw) {
       const double act = (double)std::min(tw, nx - x0) * std::min(th, ny - y0) / ((double)tw * th);
@@ -134,7 +137,7 @@ void add_columns(std::vector<SubCol> *cols, int run, int nx, int ny, int nz, int
       double w = act >= 1.0 ? 1.0 : 0.565 + 0.435 * act;
       if (xface) w *= 1.10;
       if (yface) w *= 1.05;
-      cols->push_back(SubCol{run, x0, y0, nz, w});
+      cols->push_back(SubCol{run, x0, y0, nz, w, zb});
     }
 }
 
@@ -150,7 +153,7 @@ std::vector<Tile> split_columns(const std::vector<SubCol> &cols, int G, int *gri
   std::vector<double> load(G, 0.0);
   for (size_t k = 0; k < q * G; ++k) {
     const SubCol &c = cols[full[k]];
-    per[k % G].push_back(Tile{c.run, c.x0, c.y0, 0, c.nz, 0});
+    per[k % G].push_back(Tile{c.run, c.x0, c.y0, c.zb, c.zb + c.nz, 0});
     load[k % G] += c.w * c.nz;
   }
   for (size_t k = q * G; k < full.size(); ++k) rest.push_back(full[k]);
@@ -185,7 +188,7 @@ std::vector<Tile> split_columns(const std::vector<SubCol> &cols, int G, int *gri
       const SubCol &c = cols[rest[cj]];
       const double W = c.w * c.nz;
       const int z0 = plane_at(std::max(a, Sj) - Sj, c), z1 = plane_at(std::min(b, Sj + W) - Sj, c);
-      if (z1 > z0) per[g].push_back(Tile{c.run, c.x0, c.y0, z0, z1, 0});
+      if (z1 > z0) per[g].push_back(Tile{c.run, c.x0, c.y0, c.zb + z0, c.zb + z1, 0});
       Sj += W;
     }
     a = b;
@@ -413,6 +416,58 @@ int enqueue_step(cudaStream_t s, int dtype, int kernel, int tile, int tw, int th
 
 size_t host_esz(int host_dtype) { return host_dtype == MHD_F32 ? 4 : 8; }
 
+// Host <-> device transfer of the interior of the 7 fields of one state
+// buffer (dev: its first field) of ctx.  Host field f starts at host + f *
+// hfield bytes and holds nz planes of nx * ny values (x fastest), nx, ny, nz
+// those of ctx.  Same precision: one strided 3-D copy per field; otherwise a
+// dense copy through staging (the RK register, dead between steps) and a
+// converting kernel.  Asynchronous on the context's stream.
+int upload_fields(mhd_ctx *ctx, const char *host, size_t hfield, int host_dtype, char *dev) {
+  const RunDesc &R = ctx->h_run;
+  const size_t esz = ctx->L.esz, hb = (size_t)R.nx * R.ny * R.nz * host_esz(host_dtype);
+  cudaStream_t s = ctx->stream;
+  for (int f = 0; f < NF; ++f) {
+    char *field = dev + (size_t)f * R.fstride * esz;
+    const char *src = host + f * hfield;
+    if (host_dtype == ctx->p.dtype) {
+      cudaMemcpy3DParms c3 = {};
+      c3.srcPtr = make_cudaPitchedPtr(const_cast<char *>(src), (size_t)R.nx * esz, R.nx, R.ny);
+      c3.dstPtr = make_cudaPitchedPtr(field, (size_t)R.px * esz, R.px, R.py);
+      c3.dstPos = make_cudaPos((size_t)OX * esz, OY, OZ);
+      c3.extent = make_cudaExtent((size_t)R.nx * esz, R.ny, R.nz);
+      c3.kind = cudaMemcpyHostToDevice;
+      CK(ctx, cudaMemcpy3DAsync(&c3, s));
+    } else {
+      CK(ctx, cudaMemcpyAsync(R.w, src, hb, cudaMemcpyHostToDevice, s));
+      CK(ctx, launch_set_field(ctx->p.dtype, host_dtype, R.w, field, R.nx, R.ny, R.nz, R.px, R.py, s));
+    }
+  }
+  return MHD_OK;
+}
+
+int download_fields(mhd_ctx *ctx, const char *dev, int host_dtype, char *host, size_t hfield) {
+  const RunDesc &R = ctx->h_run;
+  const size_t esz = ctx->L.esz, hb = (size_t)R.nx * R.ny * R.nz * host_esz(host_dtype);
+  cudaStream_t s = ctx->stream;
+  for (int f = 0; f < NF; ++f) {
+    const char *field = dev + (size_t)f * R.fstride * esz;
+    char *out = host + f * hfield;
+    if (host_dtype == ctx->p.dtype) {
+      cudaMemcpy3DParms c3 = {};
+      c3.srcPtr = make_cudaPitchedPtr(const_cast<char *>(field), (size_t)R.px * esz, R.px, R.py);
+      c3.srcPos = make_cudaPos((size_t)OX * esz, OY, OZ);
+      c3.dstPtr = make_cudaPitchedPtr(out, (size_t)R.nx * esz, R.nx, R.ny);
+      c3.extent = make_cudaExtent((size_t)R.nx * esz, R.ny, R.nz);
+      c3.kind = cudaMemcpyDeviceToHost;
+      CK(ctx, cudaMemcpy3DAsync(&c3, s));
+    } else {
+      CK(ctx, launch_get_field(ctx->p.dtype, host_dtype, field, R.w, R.nx, R.ny, R.nz, R.px, R.py, s));
+      CK(ctx, cudaMemcpyAsync(out, R.w, hb, cudaMemcpyDeviceToHost, s));
+    }
+  }
+  return MHD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -486,6 +541,9 @@ int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t worksp
   R.nx = p->nx;
   R.ny = p->ny;
   R.nz = p->nz;
+  R.nzg = p->nz;  // a whole grid: no z-slab decomposition
+  R.z_off = 0;
+  R.z_open = 0;
   R.px = L.px;
   R.py = L.py;
   R.pz = L.pz;
@@ -619,28 +677,12 @@ int mhd_set_state(mhd_ctx *ctx, const void *host_soa, int host_dtype, double t, 
   if (host_dtype != MHD_F32 && host_dtype != MHD_F64) return fail(ctx, MHD_EINVAL, "bad host_dtype");
   if (step < 0) return fail(ctx, MHD_EINVAL, "step must be >= 0");
   const RunDesc &R = ctx->h_run;
-  const size_t npts = (size_t)R.nx * R.ny * R.nz, hb = npts * host_esz(host_dtype);
-  const int dt = ctx->p.dtype;
+  const size_t hb = (size_t)R.nx * R.ny * R.nz * host_esz(host_dtype);
   char *dst = static_cast<char *>(R.q[step & 1]);
-  void *staging = R.w;  // dead between steps; holds one host-typed field
   cudaStream_t s = ctx->stream;
-  for (int f = 0; f < NF; ++f) {
-    char *field = dst + (size_t)f * R.fstride * ctx->L.esz;
-    const char *src = static_cast<const char *>(host_soa) + f * hb;
-    if (host_dtype == dt) {  // same precision: one strided copy into the padded interior
-      cudaMemcpy3DParms c3 = {};
-      c3.srcPtr = make_cudaPitchedPtr(const_cast<char *>(src), (size_t)R.nx * ctx->L.esz, R.nx, R.ny);
-      c3.dstPtr = make_cudaPitchedPtr(field, (size_t)R.px * ctx->L.esz, R.px, R.py);
-      c3.dstPos = make_cudaPos((size_t)OX * ctx->L.esz, OY, OZ);
-      c3.extent = make_cudaExtent((size_t)R.nx * ctx->L.esz, R.ny, R.nz);
-      c3.kind = cudaMemcpyHostToDevice;
-      CK(ctx, cudaMemcpy3DAsync(&c3, s));
-    } else {
-      CK(ctx, cudaMemcpyAsync(staging, src, hb, cudaMemcpyHostToDevice, s));
-      CK(ctx, launch_set_field(dt, host_dtype, staging, field, R.nx, R.ny, R.nz, R.px, R.py, s));
-    }
-  }
-  CK(ctx, launch_halo(dt, dst, NF, R.fstride, R.nx, R.ny, R.nz, R.px, R.py, s));
+  int rc = upload_fields(ctx, static_cast<const char *>(host_soa), hb, host_dtype, dst);
+  if (rc) return rc;
+  CK(ctx, launch_halo(ctx->p.dtype, dst, NF, R.fstride, R.nx, R.ny, R.nz, R.px, R.py, s));
   Clock c;
   std::memset(&c, 0, sizeof c);
   c.t = t;
@@ -674,27 +716,11 @@ int mhd_get_state(mhd_ctx *ctx, void *host_soa, int host_dtype, double *t, int64
   if (rc) return rc;
   if (host_soa) {
     const RunDesc &R = ctx->h_run;
-    const size_t npts = (size_t)R.nx * R.ny * R.nz, hb = npts * host_esz(host_dtype);
-    const char *src = static_cast<const char *>(R.q[c.step & 1]);
-    void *staging = R.w;
-    cudaStream_t s = ctx->stream;
-    for (int f = 0; f < NF; ++f) {
-      const char *field = src + (size_t)f * R.fstride * ctx->L.esz;
-      char *out = static_cast<char *>(host_soa) + f * hb;
-      if (host_dtype == ctx->p.dtype) {  // same precision: one strided copy from the padded interior
-        cudaMemcpy3DParms c3 = {};
-        c3.srcPtr = make_cudaPitchedPtr(const_cast<char *>(field), (size_t)R.px * ctx->L.esz, R.px, R.py);
-        c3.srcPos = make_cudaPos((size_t)OX * ctx->L.esz, OY, OZ);
-        c3.dstPtr = make_cudaPitchedPtr(out, (size_t)R.nx * ctx->L.esz, R.nx, R.ny);
-        c3.extent = make_cudaExtent((size_t)R.nx * ctx->L.esz, R.ny, R.nz);
-        c3.kind = cudaMemcpyDeviceToHost;
-        CK(ctx, cudaMemcpy3DAsync(&c3, s));
-      } else {
-        CK(ctx, launch_get_field(ctx->p.dtype, host_dtype, field, staging, R.nx, R.ny, R.nz, R.px, R.py, s));
-        CK(ctx, cudaMemcpyAsync(out, staging, hb, cudaMemcpyDeviceToHost, s));
-      }
-    }
-    CK(ctx, cudaStreamSynchronize(s));
+    const size_t hb = (size_t)R.nx * R.ny * R.nz * host_esz(host_dtype);
+    rc = download_fields(ctx, static_cast<const char *>(R.q[c.step & 1]), host_dtype,
+                         static_cast<char *>(host_soa), hb);
+    if (rc) return rc;
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
   }
   if (t) *t = c.t;
   if (step) *step = c.step;
@@ -1175,6 +1201,375 @@ void mhd_batch_destroy(mhd_batch *b) {
   cudaFree(b->d_tiles);
   cudaFree(b->d_sub);
   delete b;
+}
+
+}  // extern "C"
+
+// ---- z-slab domain decomposition (Sec. 3.3, 3.4) ----------------------------
+// Each slab is a context of its own (own workspace, TMA maps and tiles) whose
+// run descriptor is patched: the grid spacing, forcing wave-vector scale and
+// z roots of unity of the whole grid, its global plane offset, open z faces
+// (no periodic z images), and one clock, one set of step constants, one
+// partial-sum array and one set of counters shared by all slabs, so that a
+// single prologue launch over every slab's tiles reduces the CFL maximum of
+// the whole grid, sets one dt and draws one forcing for all slabs.
+struct mhd_slabs {
+  mhd_params p;  // the whole grid (resolved kernel and tile)
+  int n = 0, overlap = 0;
+  std::vector<mhd_ctx *> s;
+  std::vector<int> z0, nzs;
+  cudaStream_t stream = nullptr, side = nullptr;
+  cudaEvent_t ev_outer = nullptr, ev_copied = nullptr;
+  char *shared = nullptr;    // clock, coefficients, partials, counters, diagnostics, z roots
+  Clock *clock = nullptr;
+  double *diag = nullptr;
+  RunDesc *d_runs = nullptr;  // slab k's patched descriptor at index k
+  Tile *d_tab = nullptr;      // all tile tables below, back to back
+  int nred = 0;               // reduction tiles of all slabs (slots numbered across slabs)
+  int nall = 0, grid_all = 1, nouter = 0, grid_outer = 1, ninner = 0, grid_inner = 1;
+  size_t off_all = 0, off_outer = 0, off_inner = 0;
+  long long step = 0;  // host copy of the step index: which state buffer is current
+  int iso = 1;
+};
+
+namespace {
+
+int slabs_fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define SCK(call)                                                                               \
+  do {                                                                                          \
+    cudaError_t e__ = (cudaError_t)(call);                                                      \
+    if (e__ != cudaSuccess) return slabs_fail(MHD_ECUDA, "%s: %s", #call, cudaGetErrorString(e__)); \
+  } while (0)
+
+// Halo exchange along z of state buffer `buf` (use_w: the RK register) over
+// its first nf fields: slab k's top three interior planes go to the bottom
+// ghost planes of slab k+1, and slab k+1's bottom three interior planes to
+// the top ghost planes of slab k (periodic in k).  A plane is px * py values
+// including its x/y ghost columns; the nf fields of a slab are fstride apart,
+// so each face and direction is one 2-D copy of nf rows.
+int slab_exchange(mhd_slabs *S, bool use_w, int buf, int nf, cudaStream_t st) {
+  for (int k = 0; k < S->n; ++k) {
+    mhd_ctx *lo = S->s[k], *hi = S->s[(k + 1) % S->n];
+    const RunDesc &A = lo->h_run, &B = hi->h_run;
+    const size_t esz = lo->L.esz, plane = (size_t)A.px * A.py * esz;
+    char *a = static_cast<char *>(use_w ? A.w : A.q[buf]);
+    char *b = static_cast<char *>(use_w ? B.w : B.q[buf]);
+    const size_t pa = (size_t)A.fstride * esz, pb = (size_t)B.fstride * esz;
+    // up: interior planes nz-3 .. nz-1 of lo (padded nz .. nz+2) -> ghost planes 0 .. 2 of hi
+    SCK(cudaMemcpy2DAsync(b, pb, a + (size_t)A.nz * plane, pa, 3 * plane, nf, cudaMemcpyDeviceToDevice, st));
+    // down: interior planes 0 .. 2 of hi (padded 3 .. 5) -> ghost planes nz+3 .. nz+5 of lo
+    SCK(cudaMemcpy2DAsync(a + (size_t)(A.nz + OZ) * plane, pa, b + (size_t)OZ * plane, pb, 3 * plane, nf,
+                          cudaMemcpyDeviceToDevice, st));
+  }
+  return MHD_OK;
+}
+
+int slab_prologue(mhd_slabs *S) {
+  const mhd_params &p = S->p;
+  const Layout &L = S->s[0]->L;
+  return launch_prologue(p.dtype, p.kernel, p.tile, S->d_runs, S->d_tab, S->nred, L.tw, L.th, S->stream);
+}
+
+int slab_substep(mhd_slabs *S, size_t off, int ntab, int grid, int sub, cudaStream_t st) {
+  if (ntab <= 0) return 0;
+  return launch_substep(S->p.dtype, S->p.kernel, S->p.tile, S->d_runs, S->d_tab + off, ntab, sub, grid, S->iso,
+                        st);
+}
+
+}  // namespace
+
+extern "C" {
+
+void mhd_slabs_destroy(mhd_slabs *S) {
+  if (!S) return;
+  if (S->stream || S->s.size()) cudaStreamSynchronize(S->stream);
+  if (S->side) {
+    cudaStreamSynchronize(S->side);
+    cudaStreamDestroy(S->side);
+  }
+  if (S->ev_outer) cudaEventDestroy(S->ev_outer);
+  if (S->ev_copied) cudaEventDestroy(S->ev_copied);
+  for (mhd_ctx *c : S->s) mhd_destroy(c);
+  cudaFree(S->shared);
+  cudaFree(S->d_runs);
+  cudaFree(S->d_tab);
+  delete S;
+}
+
+int mhd_slabs_create(const mhd_params *p_in, int nslabs, int overlap, void *stream, mhd_slabs **out) {
+  std::string why;
+  if (!out) return slabs_fail(MHD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (validate(p_in, &why)) return slabs_fail(MHD_EINVAL, "%s", why.c_str());
+  const mhd_params p = resolved(p_in);
+  if (p.kernel != MHD_KERNEL_TMA) return slabs_fail(MHD_EINVAL, "slabs need the TMA kernel");
+  if (nslabs < 1) return slabs_fail(MHD_EINVAL, "nslabs must be >= 1");
+  if (p.nz < 3 * nslabs) return slabs_fail(MHD_EINVAL, "%d planes cannot give %d slabs of at least 3", p.nz, nslabs);
+  mhd_slabs *S = new mhd_slabs();
+  S->p = p;
+  S->n = nslabs;
+  S->overlap = overlap != 0;
+  S->stream = static_cast<cudaStream_t>(stream);
+  auto bail = [&](int code) {
+    const std::string msg = g_err;
+    mhd_slabs_destroy(S);
+    g_err = msg;
+    return code;
+  };
+  // slab extents and contexts
+  int z = 0;
+  for (int k = 0; k < nslabs; ++k) {
+    const int nzk = p.nz / nslabs + (k < p.nz % nslabs ? 1 : 0);
+    S->z0.push_back(z);
+    S->nzs.push_back(nzk);
+    z += nzk;
+    mhd_params sp = p;
+    sp.nz = nzk;
+    sp.lz = p.lz * nzk / p.nz;  // spacing and wave vectors are patched to the whole grid's below
+    mhd_ctx *c = nullptr;
+    const int rc = mhd_create(&sp, stream, nullptr, 0, &c);
+    if (rc) return bail(rc);
+    S->s.push_back(c);
+  }
+  const size_t esz = S->s[0]->L.esz;
+  int ntot = 0;
+  for (mhd_ctx *c : S->s) ntot += c->ntiles;
+  S->nred = ntot;
+  // shared region: clock, step constants, partials of all slabs' tiles,
+  // counters, diagnostics, z roots of unity of the whole grid
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align_up(o + bytes, ALIGN);
+    return at;
+  };
+  const size_t o_clock = take(sizeof(Clock)), o_coeffs = take(sizeof(StepCoeffs)),
+               o_part = take(sizeof(double) * NPART * ntot), o_cnt = take(sizeof(unsigned int) * 4),
+               o_diag = take(sizeof(double) * NDIAG), o_roots = take((size_t)p.nz * 2 * esz);
+  if (cudaMalloc(&S->shared, o) != cudaSuccess) return bail(slabs_fail(MHD_ENOMEM, "cudaMalloc of %zu bytes", o));
+  S->clock = reinterpret_cast<Clock *>(S->shared + o_clock);
+  S->diag = reinterpret_cast<double *>(S->shared + o_diag);
+  // whole-grid spacing, wave-vector scale and minimum spacing, formed as
+  // mhd_create forms them for an undecomposed run
+  const double Lb[3] = {p.lx, p.ly, p.lz};
+  const int ng[3] = {p.nx, p.ny, p.nz};
+  double inv_h[3], kscale[3], dmin = 1e300;
+  for (int a = 0; a < 3; ++a) {
+    const double h = Lb[a] / ng[a];
+    inv_h[a] = 1.0 / h;
+    kscale[a] = 2.0 * M_PI / Lb[a];
+    dmin = std::min(dmin, h);
+  }
+  S->iso = inv_h[0] == inv_h[1] && inv_h[1] == inv_h[2];
+  std::vector<char> roots((size_t)p.nz * 2 * esz);
+  for (int m = 0; m < p.nz; ++m) {
+    const double ang = 2.0 * M_PI * (double)m / p.nz, c = std::cos(ang), s = std::sin(ang);
+    if (esz == 4) {
+      reinterpret_cast<float *>(roots.data())[2 * m] = (float)c;
+      reinterpret_cast<float *>(roots.data())[2 * m + 1] = (float)s;
+    } else {
+      reinterpret_cast<double *>(roots.data())[2 * m] = c;
+      reinterpret_cast<double *>(roots.data())[2 * m + 1] = s;
+    }
+  }
+  // patched descriptors and the tile tables over all slabs
+  std::vector<RunDesc> descs;
+  std::vector<Tile> red, all, outer, inner;
+  std::vector<SubCol> c_all, c_outer, c_inner;
+  int slot0 = 0;
+  for (int k = 0; k < nslabs; ++k) {
+    mhd_ctx *c = S->s[k];
+    RunDesc &R = c->h_run;
+    for (int a = 0; a < 3; ++a) {
+      R.inv_h[a] = inv_h[a];
+      R.kscale[a] = kscale[a];
+    }
+    R.dmin = dmin;
+    R.roots[2] = S->shared + o_roots;
+    R.nzg = p.nz;
+    R.z_off = S->z0[k];
+    R.z_open = 1;
+    R.clock = S->clock;
+    R.coeffs = reinterpret_cast<StepCoeffs *>(S->shared + o_coeffs);
+    R.partials = reinterpret_cast<double *>(S->shared + o_part);
+    R.counter = reinterpret_cast<unsigned int *>(S->shared + o_cnt);
+    R.diag = S->diag;
+    R.ntiles = ntot;
+    c->iso = S->iso;
+    descs.push_back(R);
+    for (Tile t : c->L.tiles_host) {
+      t.run = k;
+      t.slot += slot0;
+      red.push_back(t);
+    }
+    slot0 += c->ntiles;
+    const int nzk = S->nzs[k];
+    add_columns(&c_all, k, p.nx, p.ny, nzk, c->L.tw, c->L.th);
+    if (nzk >= 2 * 2 * RAD) {  // outer: the three planes at each face; inner: the rest
+      add_columns(&c_outer, k, p.nx, p.ny, RAD, c->L.tw, c->L.th, 0);
+      add_columns(&c_outer, k, p.nx, p.ny, RAD, c->L.tw, c->L.th, nzk - RAD);
+      add_columns(&c_inner, k, p.nx, p.ny, nzk - 2 * RAD, c->L.tw, c->L.th, RAD);
+    } else {  // too thin to split: all of it is outer
+      add_columns(&c_outer, k, p.nx, p.ny, nzk, c->L.tw, c->L.th, 0);
+    }
+  }
+  int bps = 1;
+  if (substep_max_grid(p.dtype, p.kernel, p.tile, &bps) != 0 || bps < 1) bps = 1;
+  const int G = std::min(bps * num_sms(), GMAX);
+  all = split_columns(c_all, G, &S->grid_all);
+  if (!c_outer.empty()) outer = split_columns(c_outer, G, &S->grid_outer);
+  if (!c_inner.empty()) inner = split_columns(c_inner, G, &S->grid_inner);
+  S->nall = (int)all.size();
+  S->nouter = (int)outer.size();
+  S->ninner = (int)inner.size();
+  std::vector<Tile> tab = red;
+  S->off_all = tab.size();
+  tab.insert(tab.end(), all.begin(), all.end());
+  S->off_outer = tab.size();
+  tab.insert(tab.end(), outer.begin(), outer.end());
+  S->off_inner = tab.size();
+  tab.insert(tab.end(), inner.begin(), inner.end());
+  cudaStream_t st = S->stream;
+  cudaError_t e = cudaMalloc(&S->d_runs, sizeof(RunDesc) * descs.size());
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_tab, sizeof(Tile) * tab.size());
+  if (e == cudaSuccess) e = cudaMemsetAsync(S->shared, 0, o, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S->shared + o_roots, roots.data(), roots.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(S->d_runs, descs.data(), sizeof(RunDesc) * descs.size(), cudaMemcpyHostToDevice, st);
+  for (int k = 0; k < nslabs && e == cudaSuccess; ++k)  // each slab's own descriptor too
+    e = cudaMemcpyAsync(S->s[k]->d_run, &descs[k], sizeof(RunDesc), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S->d_tab, tab.data(), sizeof(Tile) * tab.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_outer, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->ev_copied, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return bail(slabs_fail(MHD_ECUDA, "mhd_slabs_create: %s", cudaGetErrorString(e)));
+  // the zero state: fill the z ghost planes from the neighbours
+  int rc = slab_exchange(S, false, 0, NF, st);
+  if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = slabs_fail(MHD_ECUDA, "mhd_slabs_create sync");
+  if (rc) return bail(rc);
+  *out = S;
+  return MHD_OK;
+}
+
+int mhd_slabs_extent(const mhd_slabs *S, int slab, int *z0, int *nz) {
+  if (!S || slab < 0 || slab >= S->n) return slabs_fail(MHD_EINVAL, "no such slab");
+  if (z0) *z0 = S->z0[slab];
+  if (nz) *nz = S->nzs[slab];
+  return MHD_OK;
+}
+
+int mhd_slabs_set_state(mhd_slabs *S, const void *host_soa, int host_dtype, double t, int64_t step) {
+  if (!S || !host_soa) return slabs_fail(MHD_EINVAL, "slabs and host_soa must be non-NULL");
+  if (host_dtype != MHD_F32 && host_dtype != MHD_F64) return slabs_fail(MHD_EINVAL, "bad host_dtype");
+  if (step < 0) return slabs_fail(MHD_EINVAL, "step must be >= 0");
+  const size_t plane = (size_t)S->p.nx * S->p.ny * host_esz(host_dtype), hfield = plane * S->p.nz;
+  const int b = (int)(step & 1);
+  for (int k = 0; k < S->n; ++k) {
+    mhd_ctx *c = S->s[k];
+    const char *src = static_cast<const char *>(host_soa) + (size_t)S->z0[k] * plane;
+    int rc = upload_fields(c, src, hfield, host_dtype, static_cast<char *>(c->h_run.q[b]));
+    if (rc) return slabs_fail(rc, "%s", c->err.c_str());
+    // x/y ghost columns (the z ghost planes it fills by local wrap are
+    // replaced by the exchange below)
+    SCK(launch_halo(S->p.dtype, c->h_run.q[b], NF, c->h_run.fstride, c->h_run.nx, c->h_run.ny, c->h_run.nz,
+                    c->h_run.px, c->h_run.py, S->stream));
+  }
+  int rc = slab_exchange(S, false, b, NF, S->stream);
+  if (rc) return rc;
+  Clock c;
+  std::memset(&c, 0, sizeof c);
+  c.t = t;
+  c.step = step;
+  SCK(cudaMemcpyAsync(S->clock, &c, sizeof c, cudaMemcpyHostToDevice, S->stream));
+  SCK(cudaStreamSynchronize(S->stream));
+  S->step = step;
+  return MHD_OK;
+}
+
+static int slabs_read_clock(mhd_slabs *S, Clock *c) {
+  SCK(cudaMemcpyAsync(c, S->clock, sizeof(Clock), cudaMemcpyDeviceToHost, S->stream));
+  SCK(cudaStreamSynchronize(S->stream));
+  if (c->status & 2) return slabs_fail(MHD_ETIMEOUT, "a bounded wait for a TMA plane copy gave up by step %lld", c->step);
+  if (c->status & 1) return slabs_fail(MHD_ENONFINITE, "non-finite time step at step %lld (run blew up)", c->step);
+  return MHD_OK;
+}
+
+int mhd_slabs_get_state(mhd_slabs *S, void *host_soa, int host_dtype, double *t, int64_t *step) {
+  if (!S) return slabs_fail(MHD_EINVAL, "slabs is NULL");
+  if (host_dtype != MHD_F32 && host_dtype != MHD_F64) return slabs_fail(MHD_EINVAL, "bad host_dtype");
+  Clock c;
+  SCK(cudaMemcpyAsync(&c, S->clock, sizeof(Clock), cudaMemcpyDeviceToHost, S->stream));
+  SCK(cudaStreamSynchronize(S->stream));
+  if (host_soa) {
+    const size_t plane = (size_t)S->p.nx * S->p.ny * host_esz(host_dtype), hfield = plane * S->p.nz;
+    for (int k = 0; k < S->n; ++k) {
+      mhd_ctx *x = S->s[k];
+      char *dst = static_cast<char *>(host_soa) + (size_t)S->z0[k] * plane;
+      int rc = download_fields(x, static_cast<const char *>(x->h_run.q[c.step & 1]), host_dtype, dst, hfield);
+      if (rc) return slabs_fail(rc, "%s", x->err.c_str());
+    }
+    SCK(cudaStreamSynchronize(S->stream));
+  }
+  if (t) *t = c.t;
+  if (step) *step = c.step;
+  return slabs_read_clock(S, &c);
+}
+
+int mhd_slabs_step(mhd_slabs *S, int nsteps) {
+  if (!S) return slabs_fail(MHD_EINVAL, "slabs is NULL");
+  if (nsteps < 0) return slabs_fail(MHD_EINVAL, "nsteps must be >= 0");
+  cudaStream_t st = S->stream;
+  for (int i = 0; i < nsteps; ++i) {
+    SCK(slab_prologue(S));
+    for (int sub = 0; sub < 3; ++sub) {
+      // substep `sub` of step n writes state buffer (n + sub + 1) mod 2
+      const int b = (int)((S->step + sub + 1) & 1);
+      if (S->overlap && S->ninner > 0) {
+        SCK(slab_substep(S, S->off_outer, S->nouter, S->grid_outer, sub, st));
+        SCK(cudaEventRecord(S->ev_outer, st));
+        SCK(cudaStreamWaitEvent(S->side, S->ev_outer, 0));
+        int rc = slab_exchange(S, false, b, NF, S->side);
+        if (rc) return rc;
+        SCK(cudaEventRecord(S->ev_copied, S->side));
+        SCK(slab_substep(S, S->off_inner, S->ninner, S->grid_inner, sub, st));
+        SCK(cudaStreamWaitEvent(st, S->ev_copied, 0));
+      } else {
+        SCK(slab_substep(S, S->off_all, S->nall, S->grid_all, sub, st));
+        int rc = slab_exchange(S, false, b, NF, st);
+        if (rc) return rc;
+      }
+    }
+    ++S->step;
+  }
+  return MHD_OK;
+}
+
+int mhd_slabs_diagnostics(mhd_slabs *S, double *out) {
+  if (!S || !out) return slabs_fail(MHD_EINVAL, "slabs and out must be non-NULL");
+  cudaStream_t st = S->stream;
+  const int dt = S->p.dtype;
+  for (mhd_ctx *c : S->s) {
+    const RunDesc &R = c->h_run;
+    SCK(launch_curl(dt, c->d_run, c->d_tiles, c->ntiles, c->L.tw, c->L.th, st));
+    SCK(launch_halo(dt, R.w, 3, R.fstride, R.nx, R.ny, R.nz, R.px, R.py, st));
+  }
+  int rc = slab_exchange(S, true, 0, 3, st);
+  if (rc) return rc;
+  const Layout &L = S->s[0]->L;
+  SCK(launch_diag_pass(dt, S->d_runs, S->d_tab, S->nred, L.tw, L.th, st));
+  SCK(cudaMemcpyAsync(out, S->diag, sizeof(double) * NDIAG, cudaMemcpyDeviceToHost, st));
+  Clock c;
+  return slabs_read_clock(S, &c);
 }
 
 }  // extern "C"

@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(TX *TY)
           derivs_from_ring(S, c, d);
           T f[3] = {T(0), T(0), T(0)};
           if (forcing) {
-            const Cplx<T> e = cmul(exy, cmul(rz[(int)(((long long)K.kmod[2] * z) % nz)], ephi));
+            const Cplx<T> e = cmul(exy, cmul(rz[(int)(((long long)K.kmod[2] * (z + R.z_off)) % R.nzg)], ephi));
             for (int a = 0; a < 3; ++a) f[a] = fa[a] * e.re - fb[a] * e.im;
           }
           const T fr[3] = {force_in_rhs ? f[0] : T(0), force_in_rhs ? f[1] : T(0),
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(TX *TY)
           if (force_at_end)
             for (int a = 0; a < 3; ++a) qn[1 + a] += dt * f[a];
           const bool near = x < RAD || x >= nx - RAD || y < RAD || y >= ny - RAD || z < RAD || z >= nz - RAD;
-          store_with_images<T, false>(qout, fs, cidx, qn, near, x, y, z, nx, ny, nz, px, py);
+          store_with_images<T, false>(qout, fs, cidx, qn, near, x, y, z, nx, ny, nz, px, py, R.z_open == 0);
         }
       }
       __syncthreads();

@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(32 * TY, TY <= 6 ? 2 : 1)
     const StepCoeffs &K = *R.coeffs;
     StencilCoefs<T, ISO> c;
     c.load(R);
-    const int nx = R.nx, ny = R.ny, nz = R.nz, px = R.px, py = R.py;
+    const int nx = R.nx, ny = R.ny, nz = R.nz, px = R.px, py = R.py, nzg = R.nzg;
+    const bool zper = R.z_open == 0;
     const long long fs = R.fstride;
     const int par = (K.parity + substep) & 1;
     const CUtensorMap *map = &R.tmap[par];
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(32 * TY, TY <= 6 ? 2 : 1)
         fa[a] = T(K.fa[a]);
         fb[a] = T(K.fb[a]);
       }
-      mz = (int)(((long long)K.kmod[2] * tile.z0) % nz);
+      mz = (int)(((long long)K.kmod[2] * (tile.z0 + R.z_off)) % R.nzg);  // global plane index
     }
     const int kz = K.kmod[2];
     const Cplx<T> ephi = {T(K.cphi), T(K.sphi)};
@@ -386,13 +387,13 @@ __global__ void __launch_bounds__(32 * TY, TY <= 6 ? 2 : 1)
         if (force_at_end)
           for (int a = 0; a < 3; ++a) qn[1 + a] += dt * f[a];
         store_with_images<T, true>(qout, fs, cidx, qn, edge_xy || z < RAD || z >= nz - RAD, x, y, z, nx, ny, nz,
-                                   px, py);
+                                   px, py, zper);
       }
       if (p >= 2 * RAD) {
         cidx += wplane;
         if (forcing) {
           mz += kz;
-          if (mz >= nz) mz -= nz;
+          if (mz >= nzg) mz -= nzg;
         }
       }
       // retire the accumulators of the output plane: its ring slot becomes
@@ -514,7 +515,8 @@ __global__ void __launch_bounds__(32 * TY, 1)
       WMp[q] = pk(c.wm(0, q), c.wm(0, q));
       WMn[q] = pk(-c.wm(0, q), -c.wm(0, q));
     }
-    const int nx = R.nx, ny = R.ny, nz = R.nz, px = R.px, py = R.py;
+    const int nx = R.nx, ny = R.ny, nz = R.nz, px = R.px, py = R.py, nzg = R.nzg;
+    const bool zper = R.z_open == 0;
     const long long fs = R.fstride;
     const int par = (K.parity + substep) & 1;
     const CUtensorMap *map = &R.tmap[par];
@@ -542,7 +544,7 @@ __global__ void __launch_bounds__(32 * TY, 1)
         fa[a] = T(K.fa[a]);
         fb[a] = T(K.fb[a]);
       }
-      mz = (int)(((long long)K.kmod[2] * tile.z0) % nz);
+      mz = (int)(((long long)K.kmod[2] * (tile.z0 + R.z_off)) % R.nzg);  // global plane index
     }
     const int kz = K.kmod[2];
     const Cplx<T> ephi = {T(K.cphi), T(K.sphi)};
@@ -730,13 +732,13 @@ __global__ void __launch_bounds__(32 * TY, 1)
         if (force_at_end)
           for (int a = 0; a < 3; ++a) qn[1 + a] += dt * fz[a];
         store_with_images<T, true>(qout, fs, cidx, qn, edge_xy || z < RAD || z >= nz - RAD, x, y, z, nx, ny, nz,
-                                   px, py);
+                                   px, py, zper);
       }
       if (p >= 2 * RAD) {
         cidx += wplane;
         if (forcing) {
           mz += kz;
-          if (mz >= nz) mz -= nz;
+          if (mz >= nzg) mz -= nzg;
         }
       }
 #pragma unroll
@@ -928,7 +930,7 @@ __global__ void __launch_bounds__(32 * TY, 2)
     v = block_max(v, sh);
     sum = block_sum(sum, sh);
     if (tid != 0) return;
-    R.diag[1] = sqrt(sum / ((double)R.nx * R.ny * R.nz));
+    R.diag[1] = sqrt(sum / ((double)R.nx * R.ny * R.nzg));
     R.clock->cache_vmax = v;
     R.clock->cache_tag = step + 1;
     R.counter[2] = 0u;

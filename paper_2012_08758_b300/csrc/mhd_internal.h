@@ -70,6 +70,11 @@ struct RunDesc {
   unsigned long long seed;
   int ntiles;               // reduction tiles of this run
   int upwind;               // 1: upwind-biased ln rho advection (Sec. 4)
+  // z-slab of a decomposed domain (Sec. 3.3): the slab holds global planes
+  // z_off .. z_off + nz - 1 of a grid of nzg planes.  z_open = 1: the z ghost
+  // planes come from the neighbouring slabs (halo exchange), so no periodic
+  // z images are stored.  An undecomposed run has z_off = 0, nzg = nz, z_open = 0.
+  int z_off, nzg, z_open;
 };
 
 static_assert(alignof(RunDesc) >= 64 && sizeof(RunDesc) % 64 == 0,
@@ -142,6 +147,9 @@ int launch_spectrum_bins(int dtype, const void *bh, long long odist, int nx, int
                          double *shells_out, cudaStream_t s);
 int launch_diagnostics(int dtype, const RunDesc *run_dev, const RunDesc &run_host,
                        const Tile *tiles, int ntiles, int tw, int th, cudaStream_t s);
+// the reduction pass of the diagnostics alone (B with its halo in w)
+int launch_diag_pass(int dtype, const RunDesc *runs, const Tile *tiles, int ntiles, int tw, int th,
+                     cudaStream_t s);
 int launch_coeffs(int dtype, const RunDesc *run, int64_t draw_step, double dt_update,
                   double dt_forcing, int parity, cudaStream_t s);
 int launch_forcing_draw(const RunDesc *run, int64_t step, double *out13, cudaStream_t s);

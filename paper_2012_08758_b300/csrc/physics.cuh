@@ -198,10 +198,13 @@ __device__ __forceinline__ int periodic_images(int i, int n, int *out) {
 // next substep finds its halo filled.  With at least 2 RAD + 1 points on
 // every axis a point has at most one image per axis (i + n below RAD, i - n
 // at or above n - RAD), so the images are the up to seven sums of those
-// shifts; smaller grids take the general enumeration.
+// shifts; smaller grids take the general enumeration.  zper = false (a
+// z-slab of a decomposed domain): no images along z, whose ghost planes the
+// halo exchange fills from the neighbouring slabs.
 template <typename T, bool STREAM>
 __device__ __forceinline__ void store_with_images(T *qout, long long fs, long long c, const T qn[NF], bool near,
-                                                  int x, int y, int z, int nx, int ny, int nz, int px, int py) {
+                                                  int x, int y, int z, int nx, int ny, int nz, int px, int py,
+                                                  bool zper = true) {
   auto put = [&](long long o) {
     T *p = qout + o;
 #pragma unroll
@@ -214,11 +217,11 @@ __device__ __forceinline__ void store_with_images(T *qout, long long fs, long lo
   };
   put(c);
   if (!near) return;
-  if (nx >= 2 * RAD + 1 && ny >= 2 * RAD + 1 && nz >= 2 * RAD + 1) {
+  if (nx >= 2 * RAD + 1 && ny >= 2 * RAD + 1 && (nz >= 2 * RAD + 1 || !zper)) {
     const long long sy = px, sz = (long long)px * py;
     const long long dx = x < RAD ? nx : (x >= nx - RAD ? -nx : 0);
     const long long dy = y < RAD ? ny * sy : (y >= ny - RAD ? -ny * sy : 0);
-    const long long dz = z < RAD ? nz * sz : (z >= nz - RAD ? -nz * sz : 0);
+    const long long dz = !zper ? 0 : z < RAD ? nz * sz : (z >= nz - RAD ? -nz * sz : 0);
     // the images are the non-empty subsets of the non-zero shifts; a
     // rolled loop over those subsets issues only the stores that exist
     const int mask = (dx != 0 ? 1 : 0) | (dy != 0 ? 2 : 0) | (dz != 0 ? 4 : 0);
@@ -229,7 +232,9 @@ __device__ __forceinline__ void store_with_images(T *qout, long long fs, long lo
     int ix[7], iy[7], iz[7];
     const int cx = periodic_images(x, nx, ix);
     const int cy = periodic_images(y, ny, iy);
-    const int cz = periodic_images(z, nz, iz);
+    int cz = 1;
+    iz[0] = z;
+    if (zper) cz = periodic_images(z, nz, iz);
     for (int a = 0; a < cz; ++a)
       for (int b = 0; b < cy; ++b)
         for (int e = 0; e < cx; ++e) put(((long long)(iz[a] + OZ) * py + (iy[b] + OY)) * px + (ix[e] + OX));

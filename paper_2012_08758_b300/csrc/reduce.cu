@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS) k_diag(const RunDesc *__rest
   for (int i = 0; i < 4; ++i) tot[i] = block_sum(loc[i], sh);
   for (int i = 4; i < NPART; ++i) tot[i] = block_max(loc[i], sh);
   if (tid != 0) return;
-  const double n = (double)R.nx * R.ny * R.nz;
+  const double n = (double)R.nx * R.ny * R.nzg;  // all points of the (possibly decomposed) grid
   R.diag[0] = sqrt(tot[0] / n);  // u_rms
   R.diag[1] = sqrt(tot[1] / n);  // B_rms
   R.diag[2] = tot[4];            // max |u|
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(MAX_TILE_THREADS) k_brms(const RunDesc *__rest
   for (int t = tid; t < R.ntiles; t += nthr) loc += __ldcg(&R.partials[(long long)t * NPART + 1]);
   const double tot = block_sum(loc, sh);
   if (tid != 0) return;
-  R.diag[1] = sqrt(tot / ((double)R.nx * R.ny * R.nz));
+  R.diag[1] = sqrt(tot / ((double)R.nx * R.ny * R.nzg));
   R.counter[2] = 0u;
 }
 
@@ -261,6 +261,19 @@ int launch_diagnostics(int dtype, const RunDesc *run_dev, const RunDesc &run_hos
     k_diag<float><<<ntiles, dim3(tw, th), 0, s>>>(run_dev, tiles);
   else
     k_diag<double><<<ntiles, dim3(tw, th), 0, s>>>(run_dev, tiles);
+  return (int)cudaGetLastError();
+}
+
+// The reduction pass of the diagnostics alone (B and its halo already in
+// the RK register): used by decomposed domains, whose B halo along z comes
+// from the neighbouring slabs.
+int launch_diag_pass(int dtype, const RunDesc *runs, const Tile *tiles, int ntiles, int tw, int th,
+                     cudaStream_t s) {
+  if (ntiles <= 0) return 0;
+  if (dtype == 0)
+    k_diag<float><<<ntiles, dim3(tw, th), 0, s>>>(runs, tiles);
+  else
+    k_diag<double><<<ntiles, dim3(tw, th), 0, s>>>(runs, tiles);
   return (int)cudaGetLastError();
 }
 

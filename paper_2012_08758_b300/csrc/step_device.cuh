@@ -87,7 +87,7 @@ __device__ __forceinline__ void make_coeffs(const RunDesc &R, long long draw_ste
     Draw D;
     forcing_draw(R, draw_step, D);
     const double amp = R.f0 * R.cs * sqrt(D.kk * R.cs / dt_forcing);
-    const int n[3] = {R.nx, R.ny, R.nz};
+    const int n[3] = {R.nx, R.ny, R.nzg};  // k mod N of the whole (possibly decomposed) grid
     for (int d = 0; d < 3; ++d) {
       C->fa[d] = amp * D.a[d];
       C->fb[d] = amp * D.b[d];

