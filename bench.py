@@ -680,6 +680,49 @@ def run_c2(args):
     return 0
 
 
+def run_slabs(args):
+    """The decomposed run on one GPU: device time per step of the n^3
+    workload cut into 1, 2 and 4 z-slabs, with and without overlapping the
+    halo exchange with the inner planes, against the undecomposed run (the
+    cost of the decomposition's outer/inner split and copies on one GPU)."""
+    import torch
+
+    from paper_2012_08758_b300 import binding as B
+    from paper_2012_08758_b300.run import Run
+    from paper_2012_08758_b300.slabs import Slabs
+
+    n = args.n
+    wl = workload(n)
+    dt = B.MHD_F32 if args.dtype == "f32" else B.MHD_F64
+    out = {}
+    run = Run(n=n, dtype=dt, **wl)
+    run.set_seed_field(1, SEED_AMP)
+    run.step(args.warmup)
+    run.sync()
+    st, tot = B.mhd_step_timed(run.ctx, args.steps)
+    out["undecomposed"] = tot / args.steps
+    q = run.get_state(dtype=np.float32 if dt == B.MHD_F32 else np.float64)[0]
+    run.close()
+    stream = torch.cuda.Stream()
+    for ns in (1, 2, 4):
+        for ov in (0, 1):
+            sl = Slabs(ns, n=n, dtype=dt, overlap=bool(ov), stream=stream, **wl)
+            sl.set_state(q)
+            sl.step(args.warmup)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sl.step(args.steps)
+            e1.record(stream)
+            e1.synchronize()
+            out[f"{ns}_slabs_overlap{ov}"] = e0.elapsed_time(e1) / args.steps
+            sl.close()
+    line = {"workload": f"{n}^3 {args.dtype.upper()} step decomposed into z-slabs on one GPU", "ms_per_step": out,
+            "steps": args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_cpu(args):
     """The FP64 oracle timed on the host: one core and all cores, whole steps
     at 64^3 and 128^3 (per-cell cost, which extrapolates to 512^3 by the
@@ -751,7 +794,7 @@ def main():
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--workload", choices=["step", "batch", "serve", "fp32vs64", "paper", "spectrum", "tables",
-                                           "c2", "cpu"],
+                                           "c2", "cpu", "slabs"],
                     default="step",
                     help="step: the benchmark line; the others measure the batch (16x64^3+8x128^3), "
                          "serving and FP32-vs-FP64 configurations and the paper's timing protocol")
@@ -803,6 +846,8 @@ def main():
         return run_c2(args)
     if args.workload == "cpu":
         return run_cpu(args)
+    if args.workload == "slabs":
+        return run_slabs(args)
     return run_ours(args)
 
 

@@ -30,76 +30,15 @@
 #include "mhd_internal.h"
 #include "physics.cuh"
 #include "step_device.cuh"
+#include "tma_util.cuh"
+#include "x2_variants.h"
 
 namespace mhd {
 
+using namespace tma;
+
 namespace {
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n"
-      "  .reg .pred p;\n"
-      "  mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      "  selp.u32 %0, 1, 0, p;\n"
-      "}\n"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: gives up after TRIES polls.  Each poll may suspend the
-// thread for a hardware-defined time, measured by the self-test at about
-// 8 us on B300, so the kernels' 2^17 polls give up after about a second.
-constexpr uint32_t MAX_TRIES = 1u << 17;
-
-template <uint32_t TRIES = MAX_TRIES>
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  for (uint32_t i = 0; i < TRIES; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0,
-                                            int c1, int c2, int c3) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
-      : "memory");
-}
-
-template <typename T, int TY>
-struct TmaShape {
-  static constexpr int TX = 32;
-  static constexpr int SX = TX + 8;  // box width: x0-4 .. x0+TX+3 (16-byte multiple)
-  static constexpr int SY = TY + 2 * RAD;
-  static constexpr int FIELD = SX * SY;
-  static constexpr int STAGE_BYTES_RAW = NF * FIELD * (int)sizeof(T);
-  static constexpr int STAGE_BYTES = (STAGE_BYTES_RAW + 127) / 128 * 128;
-};
 
 }  // namespace
 
@@ -781,9 +720,9 @@ __global__ void __launch_bounds__(32 * TY, 1)
 // One CTA per tile; the last CTA of each run sets dt, draws the forcing and
 // advances the clock (finalize_step).
 // Stage count of the prologue: small enough for two CTAs per SM.
-template <typename T, int TY>
+template <typename T, int TY, int TXW = 32>
 __host__ __device__ constexpr int pro_stages() {
-  return TmaShape<T, TY>::STAGE_BYTES * 6 <= 110 * 1024 ? 6 : 5;
+  return TmaShape<T, TY, TXW>::STAGE_BYTES * 6 <= 110 * 1024 ? 6 : 5;
 }
 
 // MODE 0: the step prologue.  MODE 1: the same sweep as a B_rms reduction of
@@ -791,13 +730,13 @@ __host__ __device__ constexpr int pro_stages() {
 // block and tile order of every other B_rms reduction); its CFL maximum is
 // kept in the clock, tagged with the step, and the prologue of that step
 // takes it instead of sweeping the state again.
-template <typename T, int TY, int MODE>
-__global__ void __launch_bounds__(32 * TY, 2)
+template <typename T, int TY, int MODE, int TXW>
+__global__ void __launch_bounds__(TXW * TY, TXW == 32 ? 2 : 1)
     k_prologue_tma(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles) {
-  using SH = TmaShape<T, TY>;
-  constexpr int TX = SH::TX, SX = SH::SX, FIELD = SH::FIELD, NS = pro_stages<T, TY>(), P = NS - 1;
+  using SH = TmaShape<T, TY, TXW>;
+  constexpr int TX = SH::TX, SX = SH::SX, FIELD = SH::FIELD, NS = pro_stages<T, TY, TXW>(), P = NS - 1;
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ double sh[32 * TY];
+  __shared__ double sh[TXW * TY];
   __shared__ int flag;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * SH::STAGE_BYTES);
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
@@ -919,7 +858,7 @@ __global__ void __launch_bounds__(32 * TY, 2)
     }
     if (!last_tile_done(&R.counter[2], R.ntiles, &flag)) return;
     // the CFL maximum as finalize_step would form it, and the |B|^2 sum
-    const int nthr = 32 * TY;
+    const int nthr = TXW * TY;
     double v = 0.0, sum = 0.0;
     for (int t = tid; t < R.ntiles; t += nthr) {
       const double pm = __ldcg(&R.partials[(long long)t * NPART]);
@@ -1012,14 +951,14 @@ int occupancy_tma(int *bps) {
   X(1, 3, double, 8, 6, false, 1)      \
   X(1, 4, double, 8, 7, false, 2)
 
-int tma_num_tiles(int dtype) { return dtype == 0 ? 16 : 4; }
+int tma_num_tiles(int dtype) { return dtype == 0 ? MHD_X2_LAST : 4; }
 
-template <typename T, int TY>
+template <typename T, int TY, int TXW = 32>
 int pro_smem_bytes() {
-  return pro_stages<T, TY>() * TmaShape<T, TY>::STAGE_BYTES + pro_stages<T, TY>() * 8;
+  return pro_stages<T, TY, TXW>() * TmaShape<T, TY, TXW>::STAGE_BYTES + pro_stages<T, TY, TXW>() * 8;
 }
 
-static_assert(32 * 16 <= MAX_TILE_THREADS, "reduction kernels run with the tile's block shape");
+static_assert(32 * 16 <= MAX_TILE_THREADS && 64 * 8 <= MAX_TILE_THREADS, "reduction kernels run with the tile's block shape");
 
 // packed tiles: id -> (scalar tile of the same shape, TY, stages)
 #define MHD_PACKED_VARIANTS(X) \
@@ -1028,6 +967,11 @@ static_assert(32 * 16 <= MAX_TILE_THREADS, "reduction kernels run with the tile'
 
 int tma_tile_shape(int dtype, int tile, int *tx, int *ty) {
   *tx = 32;
+  if (dtype == 0 && x2_rows(tile) > 0) {  // paired-point variants: 64-point rows
+    *tx = 64;
+    *ty = x2_rows(tile);
+    return 0;
+  }
 #define X(ID, SC, TY, NS) \
   if (dtype == 0 && tile == ID) { *ty = TY; return 0; }
   MHD_PACKED_VARIANTS(X)
@@ -1040,6 +984,19 @@ int tma_tile_shape(int dtype, int tile, int *tx, int *ty) {
 }
 
 int tma_prepare(int dtype, int tile) {
+#define X(ID, TY, NS, BR)                                                                                       \
+  if (dtype == 0 && tile == ID) {                                                                              \
+    int e = x2_prepare(tile);                                                                                  \
+    if (!e)                                                                                                    \
+      e = (int)cudaFuncSetAttribute(k_prologue_tma<float, TY, 0, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                    pro_smem_bytes<float, TY, 64>());                                          \
+    if (!e)                                                                                                    \
+      e = (int)cudaFuncSetAttribute(k_prologue_tma<float, TY, 1, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                    pro_smem_bytes<float, TY, 64>());                                          \
+    return e;                                                                                                  \
+  }
+  MHD_X2_VARIANTS(X)
+#undef X
 #define X(ID, SC, TY, NS)                                                                            \
   if (dtype == 0 && tile == ID) {                                                                    \
     int e = (int)cudaFuncSetAttribute(k_substep_tma_f2<TY, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
@@ -1052,10 +1009,10 @@ int tma_prepare(int dtype, int tile) {
   if (dtype == DT && tile == ID) {                                                                       \
     int e = prepare_tma<T, TY, NS, U, BR>();                                                                 \
     if (!e)                                                                                              \
-      e = (int)cudaFuncSetAttribute(k_prologue_tma<T, TY, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+      e = (int)cudaFuncSetAttribute(k_prologue_tma<T, TY, 0, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                     pro_smem_bytes<T, TY>());                                               \
     if (!e)                                                                                                 \
-      e = (int)cudaFuncSetAttribute(k_prologue_tma<T, TY, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+      e = (int)cudaFuncSetAttribute(k_prologue_tma<T, TY, 1, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                     pro_smem_bytes<T, TY>());                                               \
     return e;                                                                                            \
   }
@@ -1065,6 +1022,7 @@ int tma_prepare(int dtype, int tile) {
 }
 
 int tma_occupancy(int dtype, int tile, int *bps) {
+  if (dtype == 0 && x2_rows(tile) > 0) return x2_occupancy(tile, bps);
 #define X(ID, SC, TY, NS)                                                                                \
   if (dtype == 0 && tile == ID)                                                                          \
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_substep_tma_f2<TY, NS>, 32 * TY,    \
@@ -1081,6 +1039,16 @@ int tma_occupancy(int dtype, int tile, int *bps) {
 int tma_launch_prologue(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles,
                         cudaStream_t s, int mode) {
   if (ntiles <= 0) return 0;
+#define X(ID, TY, NS, BR)                                                                                   \
+  if (dtype == 0 && tile == ID) {                                                                          \
+    if (mode == 1)                                                                                         \
+      k_prologue_tma<float, TY, 1, 64><<<ntiles, dim3(64, TY), pro_smem_bytes<float, TY, 64>(), s>>>(runs, tiles); \
+    else                                                                                                   \
+      k_prologue_tma<float, TY, 0, 64><<<ntiles, dim3(64, TY), pro_smem_bytes<float, TY, 64>(), s>>>(runs, tiles); \
+    return (int)cudaGetLastError();                                                                        \
+  }
+  MHD_X2_VARIANTS(X)
+#undef X
 #define X(ID, SC, TY, NS) \
   if (dtype == 0 && tile == ID) return tma_launch_prologue(0, SC, runs, tiles, ntiles, s, mode);
   MHD_PACKED_VARIANTS(X)
@@ -1088,9 +1056,9 @@ int tma_launch_prologue(int dtype, int tile, const RunDesc *runs, const Tile *ti
 #define X(DT, ID, T, TY, NS, U, BR)                                                                       \
   if (dtype == DT && tile == ID) {                                                                    \
     if (mode == 1)                                                                                    \
-      k_prologue_tma<T, TY, 1><<<ntiles, dim3(32, TY), pro_smem_bytes<T, TY>(), s>>>(runs, tiles);    \
+      k_prologue_tma<T, TY, 1, 32><<<ntiles, dim3(32, TY), pro_smem_bytes<T, TY>(), s>>>(runs, tiles);    \
     else                                                                                              \
-      k_prologue_tma<T, TY, 0><<<ntiles, dim3(32, TY), pro_smem_bytes<T, TY>(), s>>>(runs, tiles);    \
+      k_prologue_tma<T, TY, 0, 32><<<ntiles, dim3(32, TY), pro_smem_bytes<T, TY>(), s>>>(runs, tiles);    \
     return (int)cudaGetLastError();                                                                   \
   }
   MHD_TMA_VARIANTS(X)
@@ -1100,6 +1068,7 @@ int tma_launch_prologue(int dtype, int tile, const RunDesc *runs, const Tile *ti
 
 int tma_launch(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles, int substep, int grid,
                int iso, cudaStream_t s) {
+  if (dtype == 0 && x2_rows(tile) > 0) return x2_launch(tile, runs, tiles, ntiles, substep, grid, iso, s);
 #define X(ID, SC, TY, NS)                                                                             \
   if (dtype == 0 && tile == ID) {                                                                     \
     if (!iso) return tma_launch(0, SC, runs, tiles, ntiles, substep, grid, iso, s);                   \

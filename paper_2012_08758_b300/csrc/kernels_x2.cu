@@ -1,0 +1,647 @@
+// Substep kernel, paired-point TMA variant (FP32).
+//
+// The arithmetic of one stage of the 3rd-order 2N-storage Runge-Kutta scheme
+// (Sec. 2) on the right-hand side of Eqs. 1-3 with the forcing of Eqs. 4-6,
+// as in kernels_tma.cu, organised so that one thread computes TWO
+// neighbouring x-points (x, x+1):
+//
+//  * a CTA owns a 64 x TY column and sweeps it along z; every z-plane of all
+//    seven fields (3-point x/y halo) arrives by one TMA copy completed on an
+//    mbarrier, P planes ahead;
+//  * shared-memory reads are 64-bit pairs (f(x), f(x+1)), so one load serves
+//    both points, and the arithmetic whose operands come as such pairs -- y
+//    and z stencils, the right-hand side, the RK update -- runs on packed
+//    FP32 pairs (__ffma2_rn / __fadd2_rn / __fmul2_rn); x-direction
+//    differences, whose samples straddle pairs, are formed per point;
+//  * the output plane o is computed once lead plane o+3 has arrived: its
+//    z-neighbours o+1..o+3 are read from the stages still in shared memory,
+//    only the three planes below (o-3..o-1) are kept in registers;
+//  * the mixed x-z / y-z derivatives are split into the half from planes
+//    above o, read from shared memory at o, and the half from planes below,
+//    accumulated into a three-deep register ring as each plane passes
+//    (S_s(o) = d_s(o+s) - d_s(o-s), d_s the x- or y-difference at distance s).
+// Every wait on an mbarrier is bounded; on time-out the CTA records status
+// bit 1 in the run's clock, waits (bounded) for its copies and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mhd_internal.h"
+#include "physics.cuh"
+#include "step_device.cuh"
+#include "tma_util.cuh"
+#include "x2_variants.h"
+
+namespace mhd {
+
+using namespace tma;
+
+namespace {
+
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+
+// Stencil weights of the run as packed pairs (both lanes equal).
+template <bool ISO>
+struct PairCoefs {
+  static constexpr int NA = ISO ? 1 : 3;
+  float2 c1[NA][4], c2[NA][4], cm[NA][4];
+  float2 cmn[NA][4];  // -cm (the half of a mixed derivative from planes below)
+  float2 c6[NA];
+  float2 cs2, nu, eta;
+  int upwind;
+  __device__ __forceinline__ void load(const RunDesc &R) {
+    const int pa[3] = {0, 0, 1}, pb[3] = {1, 2, 2};
+    for (int a = 0; a < NA; ++a) {
+      for (int s = 0; s < 4; ++s) {
+        c1[a][s] = bc(float(W1(s) * R.inv_h[a]));
+        c2[a][s] = bc(float(W2(s) * R.inv_h[a] * R.inv_h[a]));
+        cm[a][s] = bc(float(WM(s) * R.inv_h[pa[a]] * R.inv_h[pb[a]]));
+        cmn[a][s] = bc(-float(WM(s) * R.inv_h[pa[a]] * R.inv_h[pb[a]]));
+      }
+      c6[a] = bc(float(R.inv_h[a] / 60.0));
+    }
+    cs2 = bc(float(R.cs2));
+    nu = bc(float(R.nu));
+    eta = bc(float(R.eta));
+    upwind = R.upwind;
+  }
+  __device__ __forceinline__ float2 w1(int a, int s) const { return c1[ISO ? 0 : a][s]; }
+  __device__ __forceinline__ float2 w2(int a, int s) const { return c2[ISO ? 0 : a][s]; }
+  __device__ __forceinline__ float2 wm(int p, int s) const { return cm[ISO ? 0 : p][s]; }
+  __device__ __forceinline__ float2 wmn(int p, int s) const { return cmn[ISO ? 0 : p][s]; }
+  __device__ __forceinline__ float2 w6(int a) const { return c6[ISO ? 0 : a]; }
+};
+
+// First and second derivative from the paired differences d_s = f(+s) - f(-s)
+// and sums e_s = f(+s) + f(-s), s = 1..3, and the centre c.
+template <bool ISO>
+__device__ __forceinline__ float2 d1p(const PairCoefs<ISO> &c, int a, float2 d1, float2 d2, float2 d3) {
+  return fma2(c.w1(a, 3), d3, fma2(c.w1(a, 2), d2, mul2(c.w1(a, 1), d1)));
+}
+template <bool ISO>
+__device__ __forceinline__ float2 d2p(const PairCoefs<ISO> &c, int a, float2 c0, float2 e1, float2 e2, float2 e3) {
+  return fma2(c.w2(a, 3), e3, fma2(c.w2(a, 2), e2, fma2(c.w2(a, 1), e1, mul2(c.w2(a, 0), c0))));
+}
+
+}  // namespace
+
+namespace {
+
+// Derivatives at a pair of points (lane 0: x, lane 1: x+1).
+struct PairDerivs {
+  float2 lnr, u[3];
+  float2 g[3];      // grad ln rho
+  float2 G[3][3];   // G[a][b] = d u_a / d x_b
+  float2 B[3];      // curl A (first-derivative stencil)
+  float2 lapu[3], gdu[3], lapA[3];
+  float2 jc[3];     // j = grad div A - lap A, d_a d_a A_a cancelled analytically (mu0 = 1)
+  float2 up;        // upwinding term of d ln rho / dt (0 when off)
+};
+
+// dq/dt of Eqs. 1-3 at a pair of points, packed; f = forcing (zero when off).
+// The same terms as rhs_point, with the scalar operations paired.
+template <bool ISO>
+__device__ __forceinline__ void rhs_pair(const PairDerivs &d, const PairCoefs<ISO> &c, const float2 f[3],
+                                         float2 out[NF]) {
+  const float2 M1 = bc(-1.f), third = bc(1.f / 3.f), mthird = bc(-1.f / 3.f), half = bc(0.5f), two = bc(2.f);
+  const float2 rinv = pk(__expf(-d.lnr.x), __expf(-d.lnr.y));
+  const float2 divu = add2(add2(d.G[0][0], d.G[1][1]), d.G[2][2]);
+  // Eq. 1: D ln rho / Dt = -div u
+  const float2 ug = fma2(d.u[2], d.g[2], fma2(d.u[1], d.g[1], mul2(d.u[0], d.g[0])));
+  out[0] = sub2(sub2(d.up, ug), divu);
+  const float2 nB[3] = {mul2(d.B[0], M1), mul2(d.B[1], M1), mul2(d.B[2], M1)};
+  const float2 jxB[3] = {fma2(d.jc[1], d.B[2], mul2(d.jc[2], nB[1])), fma2(d.jc[2], d.B[0], mul2(d.jc[0], nB[2])),
+                         fma2(d.jc[0], d.B[1], mul2(d.jc[1], nB[0]))};
+  const float2 uxB[3] = {fma2(d.u[1], d.B[2], mul2(d.u[2], nB[1])), fma2(d.u[2], d.B[0], mul2(d.u[0], nB[2])),
+                         fma2(d.u[0], d.B[1], mul2(d.u[1], nB[0]))};
+  // traceless rate of strain (symmetric)
+  float2 S[3][3];
+  S[0][1] = S[1][0] = mul2(half, add2(d.G[0][1], d.G[1][0]));
+  S[0][2] = S[2][0] = mul2(half, add2(d.G[0][2], d.G[2][0]));
+  S[1][2] = S[2][1] = mul2(half, add2(d.G[1][2], d.G[2][1]));
+#pragma unroll
+  for (int a = 0; a < 3; ++a) S[a][a] = fma2(mthird, divu, d.G[a][a]);
+  const float2 mcs2 = mul2(c.cs2, M1);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float2 Sg = fma2(S[a][2], d.g[2], fma2(S[a][1], d.g[1], mul2(S[a][0], d.g[0])));
+    const float2 adv = fma2(d.u[2], d.G[a][2], fma2(d.u[1], d.G[a][1], mul2(d.u[0], d.G[a][0])));
+    const float2 visc = fma2(two, Sg, fma2(third, d.gdu[a], d.lapu[a]));
+    // Eq. 2
+    out[1 + a] = fma2(c.nu, visc, fma2(jxB[a], rinv, fma2(mcs2, d.g[a], sub2(f[a], adv))));
+    // Eq. 3 (diffusive gauge)
+    out[4 + a] = fma2(c.eta, d.lapA[a], uxB[a]);
+  }
+}
+
+}  // namespace
+
+namespace {
+
+// The samples of one field along x around a pair: 64-bit loads at x-4, x-2,
+// x, x+2, x+4 (x even), and per point the differences d_s = f(+s) - f(-s)
+// and sums e_s = f(+s) + f(-s), s = 1..3, paired.
+struct XRow {
+  float2 c, d1, d2, d3, e1, e2, e3;
+};
+__device__ __forceinline__ XRow xrow(const float *b) {
+  const float2 A = ld2(b - 4), Bq = ld2(b - 2), C = ld2(b), D = ld2(b + 2), E = ld2(b + 4);
+  XRow r;
+  r.c = C;
+  r.d1 = pk(C.y - Bq.y, D.x - C.x);
+  r.d2 = pk(D.x - Bq.x, D.y - Bq.y);
+  r.d3 = pk(D.y - A.y, E.x - Bq.x);
+  r.e1 = pk(C.y + Bq.y, D.x + C.x);
+  r.e2 = pk(D.x + Bq.x, D.y + Bq.y);
+  r.e3 = pk(D.y + A.y, E.x + Bq.x);
+  return r;
+}
+
+// The x-differences d_s = f(+s) - f(-s) of a pair in the row at b, for one s.
+template <int S>
+__device__ __forceinline__ float2 xdiff(const float *b) {
+  if (S == 1) {
+    const float2 Bq = ld2(b - 2), C = ld2(b), D = ld2(b + 2);
+    return pk(C.y - Bq.y, D.x - C.x);
+  } else if (S == 2) {
+    const float2 Bq = ld2(b - 2), D = ld2(b + 2);
+    return pk(D.x - Bq.x, D.y - Bq.y);
+  } else {
+    const float2 A = ld2(b - 4), Bq = ld2(b - 2), D = ld2(b + 2), E = ld2(b + 4);
+    return pk(D.y - A.y, E.x - Bq.x);
+  }
+}
+
+// Samples along y: d_s = f(y+s) - f(y-s), e_s = f(y+s) + f(y-s), paired.
+struct YRow {
+  float2 d1, d2, d3, e1, e2, e3;
+};
+template <int SX>
+__device__ __forceinline__ YRow yrow(const float *b) {
+  YRow r;
+  float2 p = ld2(b + SX), m = ld2(b - SX);
+  r.d1 = sub2(p, m);
+  r.e1 = add2(p, m);
+  p = ld2(b + 2 * SX), m = ld2(b - 2 * SX);
+  r.d2 = sub2(p, m);
+  r.e2 = add2(p, m);
+  p = ld2(b + 3 * SX), m = ld2(b - 3 * SX);
+  r.d3 = sub2(p, m);
+  r.e3 = add2(p, m);
+  return r;
+}
+
+// x-y mixed derivative of a pair on the two diagonals (R1):
+// sum_s wm_s [(f(x+s, y+s) - f(x-s, y+s)) - (f(x+s, y-s) - f(x-s, y-s))].
+template <int SX, bool ISO>
+__device__ __forceinline__ float2 dxy_pair(const float *b, const PairCoefs<ISO> &c) {
+  const float2 S1 = sub2(xdiff<1>(b + SX), xdiff<1>(b - SX));
+  const float2 S2 = sub2(xdiff<2>(b + 2 * SX), xdiff<2>(b - 2 * SX));
+  const float2 S3 = sub2(xdiff<3>(b + 3 * SX), xdiff<3>(b - 3 * SX));
+  return fma2(c.wm(0, 3), S3, fma2(c.wm(0, 2), S2, mul2(c.wm(0, 1), S1)));
+}
+
+}  // namespace
+
+template <int TY, int NS, int BAR, bool ISO>
+__global__ void __launch_bounds__(32 * TY, 1)
+    k_substep_x2(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles, int ntiles, int substep) {
+  using SH = TmaShape<float, TY, 64>;
+  constexpr int SX = SH::SX, FIELD = SH::FIELD;
+  // Prefetch distance: the stage of plane q is last read when q is the output
+  // plane (lead plane q+3) and refilled by plane q+NS, issued P planes ahead;
+  // warps drift apart by up to BAR planes between CTA barriers.
+  constexpr int P = NS - 3 - BAR;
+  static_assert(P >= 1, "need at least one plane of prefetch");
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * SH::STAGE_BYTES);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  unsigned long long G = 0;  // planes issued by this CTA before the current tile
+  bool failed = false, waits_ok = true;
+  int fail_run = -1, fail_p = 0, issued_hi = 0;
+
+  for (int t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+    const Tile tile = tiles[t];
+    if (tile.z1 <= tile.z0) continue;  // padding entry of the work split
+    const RunDesc &R = runs[tile.run];
+    const StepCoeffs &K = *R.coeffs;
+    PairCoefs<ISO> c;
+    c.load(R);
+    const int nx = R.nx, ny = R.ny, nz = R.nz, px = R.px, py = R.py, nzg = R.nzg;
+    const bool zper = R.z_open == 0;
+    const long long fs = R.fstride;
+    const int par = (K.parity + substep) & 1;
+    const CUtensorMap *map = &R.tmap[par];
+    float *__restrict__ qout = static_cast<float *>(R.q[par ^ 1]);
+    float *__restrict__ w = static_cast<float *>(R.w);
+    const float2 dt = bc(float(K.dt));
+    const float2 alpha = bc(float(RK_ALPHA(substep))), beta = bc(float(RK_BETA(substep)));
+    const int x = tile.x0 + 2 * tx, y = tile.y0 + ty;
+    const bool act0 = x < nx && y < ny, act1 = x + 1 < nx && y < ny;
+    const bool yedge = y < RAD || y >= ny - RAD;
+    const bool edge0 = yedge || x < RAD || x >= nx - RAD, edge1 = yedge || x + 1 < RAD || x + 1 >= nx - RAD;
+    const int npl = (tile.z1 - tile.z0) + 2 * RAD;  // lead planes z0-3 .. z1+2
+
+    const bool forcing = K.forcing != 0;
+    const bool force_in_rhs = forcing && R.forcing_mode == 0;
+    const bool force_at_end = forcing && R.forcing_mode == 1 && substep == 2;
+    float2 exr = bc(1.f), exi = bc(0.f);  // e^{i (k_x x + k_y y)} of the two points
+    int mz = 0;                            // (k_z * z_out) mod nzg, global plane index
+    if (forcing) {
+      const Cplx<float> *rx = static_cast<const Cplx<float> *>(R.roots[0]);
+      const Cplx<float> *ry = static_cast<const Cplx<float> *>(R.roots[1]);
+      if (act0) {
+        const Cplx<float> ey = ry[(int)(((long long)K.kmod[1] * y) % ny)];
+        const Cplx<float> e0 = cmul(rx[(int)(((long long)K.kmod[0] * x) % nx)], ey);
+        const Cplx<float> e1 = act1 ? cmul(rx[(int)(((long long)K.kmod[0] * (x + 1)) % nx)], ey) : e0;
+        exr = pk(e0.re, e1.re);
+        exi = pk(e0.im, e1.im);
+      }
+      mz = (int)(((long long)K.kmod[2] * (tile.z0 + R.z_off)) % nzg);
+    }
+    const int kz = K.kmod[2];
+    const Cplx<float> ephi = {float(K.cphi), float(K.sphi)};
+    const Cplx<float> *rz = static_cast<const Cplx<float> *>(R.roots[2]);
+
+    int slot = (int)(G % NS);
+    uint32_t phase = (uint32_t)((G / NS) & 1ull);
+    auto issue = [&](int p, int sl) {
+      uint64_t *bar = &bars[sl];
+      mbar_arrive_expect_tx(bar, (uint32_t)(NF * FIELD * sizeof(float)));
+      tma_load_4d(smem + sl * SH::STAGE_BYTES, map, bar, tile.x0, tile.y0, tile.z0 + p, 0);
+    };
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      const int first = npl < P ? npl : P;
+      for (int p = 0; p < first; ++p) issue(p, (slot + p) % NS);
+      issued_hi = first;
+    }
+
+    // Registers that follow the sweep: the three planes below the centre
+    // plane (pz[f][k]: plane o-3+k), and the halves of the x-z / y-z mixed
+    // derivatives contributed by planes below, for output planes o, o+1, o+2
+    // (a*[k]).  aX1 = d_x d_z u_z, aY1 = d_y d_z u_z, aZ1 = d_x d_z u_x +
+    // d_y d_z u_y; aX2, aY2, aZ2 the same for A.
+    float2 pz[NF][3];
+    float2 aX1[3], aY1[3], aZ1[3], aX2[3], aY2[3], aZ2[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) pz[f][k] = bc(0.f);
+      aX1[k] = aY1[k] = aZ1[k] = aX2[k] = aY2[k] = aZ2[k] = bc(0.f);
+    }
+    const int cxy = (ty + RAD) * SX + 2 * tx + 4;  // the pair's first point inside a field plane
+    const bool need_w = substep > 0 && act0;
+    const long long wplane = (long long)py * px;
+    // padded index of the first point of the pair in output plane z0
+    long long cidx = ((long long)(tile.z0 + OZ) * py + (y + OY)) * px + (x + OX);
+    float fa[3] = {0.f, 0.f, 0.f}, fb[3] = {0.f, 0.f, 0.f};
+    if (forcing)
+      for (int a = 0; a < 3; ++a) {
+        fa[a] = float(K.fa[a]);
+        fb[a] = float(K.fb[a]);
+      }
+
+    // the halves from planes below: ring update with the differences d_s of
+    // the plane that is leaving the centre (output o+s receives -wm_s d_s)
+    auto pass1 = [&](float2 a[3], int pr, float2 d1, float2 d2, float2 d3) {
+      a[0] = fma2(c.wmn(pr, 1), d1, a[1]);
+      a[1] = fma2(c.wmn(pr, 2), d2, a[2]);
+      a[2] = mul2(c.wmn(pr, 3), d3);
+    };
+    auto pass2 = [&](float2 a[3], float2 x1, float2 x2, float2 x3, float2 y1, float2 y2, float2 y3) {
+      a[0] = fma2(c.wmn(2, 1), y1, fma2(c.wmn(1, 1), x1, a[1]));
+      a[1] = fma2(c.wmn(2, 2), y2, fma2(c.wmn(1, 2), x2, a[2]));
+      a[2] = fma2(c.wmn(2, 3), y3, mul2(c.wmn(1, 3), x3));
+    };
+    auto ydiff = [&](const float *b, int s) { return sub2(ld2(b + s * SX), ld2(b - s * SX)); };
+
+    for (int p = 0; p < npl && !failed; ++p) {
+      if (tid == 0 && p + P < npl) {
+        fence_proxy_async_smem();
+        int sl = slot + P;
+        if (sl >= NS) sl -= NS;
+        issue(p + P, sl);
+        issued_hi = p + P + 1;
+      }
+      const int o = p - RAD;       // centre plane (lead index), interior plane z0 + o - 3
+      const bool outp = o >= RAD;  // an interior plane of this tile: computed and stored
+      float2 wc[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) wc[f] = bc(0.f);
+      if (need_w && outp) {
+        const float *wp = w + cidx;
+#pragma unroll
+        for (int f = 0; f < NF; ++f, wp += fs) wc[f] = __ldcs(reinterpret_cast<const float2 *>(wp));
+      }
+      const bool ok = mbar_wait(&bars[slot], phase);
+      if (o >= 0 && ok) {
+        int os = slot - RAD;
+        if (os < 0) os += NS;
+        auto stage = [&](int k) {  // plane o + k, k = 0..3
+          int sl = os + k;
+          if (sl >= NS) sl -= NS;
+          return reinterpret_cast<const float *>(smem + sl * SH::STAGE_BYTES) + cxy;
+        };
+        const float *so = stage(0);
+        if (!outp) {
+          // halo plane below the tile: only its centres and differences enter the registers
+          float2 cen[NF];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) cen[f] = ld2(so + f * FIELD);
+          const XRow xux = xrow(so + 1 * FIELD), xuz = xrow(so + 3 * FIELD), xAx = xrow(so + 4 * FIELD),
+                     xAz = xrow(so + 6 * FIELD);
+          const YRow yuy = yrow<SX>(so + 2 * FIELD), yuz = yrow<SX>(so + 3 * FIELD), yAy = yrow<SX>(so + 5 * FIELD),
+                     yAz = yrow<SX>(so + 6 * FIELD);
+          pass1(aX1, 1, xuz.d1, xuz.d2, xuz.d3);
+          pass1(aY1, 2, yuz.d1, yuz.d2, yuz.d3);
+          pass2(aZ1, xux.d1, xux.d2, xux.d3, yuy.d1, yuy.d2, yuy.d3);
+          pass1(aX2, 1, xAz.d1, xAz.d2, xAz.d3);
+          pass1(aY2, 2, yAz.d1, yAz.d2, yAz.d3);
+          pass2(aZ2, xAx.d1, xAx.d2, xAx.d3, yAy.d1, yAy.d2, yAy.d3);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            pz[f][0] = pz[f][1];
+            pz[f][1] = pz[f][2];
+            pz[f][2] = cen[f];
+          }
+        } else {
+          // ---- output plane: the planes above come from shared memory ----
+          const float *s1 = stage(1), *s2 = stage(2), *s3 = stage(3);
+          auto zrow = [&](int f, float2 &d1, float2 &d2, float2 &d3, float2 &e1, float2 &e2, float2 &e3) {
+            const float2 p1 = ld2(s1 + f * FIELD), p2 = ld2(s2 + f * FIELD), p3 = ld2(s3 + f * FIELD);
+            d1 = sub2(p1, pz[f][2]);
+            e1 = add2(p1, pz[f][2]);
+            d2 = sub2(p2, pz[f][1]);
+            e2 = add2(p2, pz[f][1]);
+            d3 = sub2(p3, pz[f][0]);
+            e3 = add2(p3, pz[f][0]);
+          };
+          // halves of the x-z / y-z mixed derivatives from the planes above
+          auto fxz = [&](int f) {
+            return fma2(c.wm(1, 3), xdiff<3>(s3 + f * FIELD),
+                        fma2(c.wm(1, 2), xdiff<2>(s2 + f * FIELD), mul2(c.wm(1, 1), xdiff<1>(s1 + f * FIELD))));
+          };
+          auto fyz = [&](int f) {
+            return fma2(c.wm(2, 3), ydiff(s3 + f * FIELD, 3),
+                        fma2(c.wm(2, 2), ydiff(s2 + f * FIELD, 2), mul2(c.wm(2, 1), ydiff(s1 + f * FIELD, 1))));
+          };
+          PairDerivs d;
+          float2 zd1, zd2, zd3, ze1, ze2, ze3;
+
+          // vector potential: B = curl A, lap A, j
+          const XRow xAx = xrow(so + 4 * FIELD), xAy = xrow(so + 5 * FIELD), xAz = xrow(so + 6 * FIELD);
+          const YRow yAx = yrow<SX>(so + 4 * FIELD), yAy = yrow<SX>(so + 5 * FIELD), yAz = yrow<SX>(so + 6 * FIELD);
+          float2 Axz_, Ayz_, Azz;
+          zrow(4, zd1, zd2, zd3, ze1, ze2, ze3);
+          const float2 dzAx = d1p(c, 2, zd1, zd2, zd3);
+          Axz_ = d2p(c, 2, xAx.c, ze1, ze2, ze3);
+          zrow(5, zd1, zd2, zd3, ze1, ze2, ze3);
+          const float2 dzAy = d1p(c, 2, zd1, zd2, zd3);
+          Ayz_ = d2p(c, 2, xAy.c, ze1, ze2, ze3);
+          zrow(6, zd1, zd2, zd3, ze1, ze2, ze3);
+          Azz = d2p(c, 2, xAz.c, ze1, ze2, ze3);
+          d.B[0] = sub2(d1p(c, 1, yAz.d1, yAz.d2, yAz.d3), dzAy);
+          d.B[1] = sub2(dzAx, d1p(c, 0, xAz.d1, xAz.d2, xAz.d3));
+          d.B[2] = sub2(d1p(c, 0, xAy.d1, xAy.d2, xAy.d3), d1p(c, 1, yAx.d1, yAx.d2, yAx.d3));
+          const float2 Axx = d2p(c, 0, xAx.c, xAx.e1, xAx.e2, xAx.e3), Axy_ = d2p(c, 1, xAx.c, yAx.e1, yAx.e2, yAx.e3);
+          const float2 Ayx = d2p(c, 0, xAy.c, xAy.e1, xAy.e2, xAy.e3), Ayy = d2p(c, 1, xAy.c, yAy.e1, yAy.e2, yAy.e3);
+          const float2 Azx = d2p(c, 0, xAz.c, xAz.e1, xAz.e2, xAz.e3), Azy = d2p(c, 1, xAz.c, yAz.e1, yAz.e2, yAz.e3);
+          d.lapA[0] = add2(add2(Axx, Axy_), Axz_);
+          d.lapA[1] = add2(add2(Ayx, Ayy), Ayz_);
+          d.lapA[2] = add2(add2(Azx, Azy), Azz);
+          d.jc[0] = sub2(sub2(add2(dxy_pair<SX>(so + 5 * FIELD, c), add2(fxz(6), aX2[0])), Axy_), Axz_);
+          d.jc[1] = sub2(sub2(add2(dxy_pair<SX>(so + 4 * FIELD, c), add2(fyz(6), aY2[0])), Ayx), Ayz_);
+          d.jc[2] = sub2(sub2(add2(add2(fxz(4), fyz(5)), aZ2[0]), Azx), Azy);
+
+          // velocity: grad u, lap u, grad div u
+          const XRow xux = xrow(so + 1 * FIELD), xuy = xrow(so + 2 * FIELD), xuz = xrow(so + 3 * FIELD);
+          const YRow yux = yrow<SX>(so + 1 * FIELD), yuy = yrow<SX>(so + 2 * FIELD), yuz = yrow<SX>(so + 3 * FIELD);
+          d.u[0] = xux.c;
+          d.u[1] = xuy.c;
+          d.u[2] = xuz.c;
+          float2 uz2[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const XRow &xr = a == 0 ? xux : a == 1 ? xuy : xuz;
+            const YRow &yr = a == 0 ? yux : a == 1 ? yuy : yuz;
+            zrow(1 + a, zd1, zd2, zd3, ze1, ze2, ze3);
+            d.G[a][0] = d1p(c, 0, xr.d1, xr.d2, xr.d3);
+            d.G[a][1] = d1p(c, 1, yr.d1, yr.d2, yr.d3);
+            d.G[a][2] = d1p(c, 2, zd1, zd2, zd3);
+            const float2 xx = d2p(c, 0, xr.c, xr.e1, xr.e2, xr.e3), yy = d2p(c, 1, xr.c, yr.e1, yr.e2, yr.e3),
+                         zz = d2p(c, 2, xr.c, ze1, ze2, ze3);
+            d.lapu[a] = add2(add2(xx, yy), zz);
+            uz2[a] = a == 0 ? xx : a == 1 ? yy : zz;  // the d_a d_a u_a term of grad div u
+          }
+          d.gdu[0] = add2(add2(uz2[0], dxy_pair<SX>(so + 2 * FIELD, c)), add2(fxz(3), aX1[0]));
+          d.gdu[1] = add2(add2(dxy_pair<SX>(so + 1 * FIELD, c), uz2[1]), add2(fyz(3), aY1[0]));
+          d.gdu[2] = add2(add2(add2(fxz(1), fyz(2)), aZ1[0]), uz2[2]);
+
+          // density: grad ln rho and the upwinding term
+          const XRow xl = xrow(so);
+          const YRow yl = yrow<SX>(so);
+          zrow(0, zd1, zd2, zd3, ze1, ze2, ze3);
+          d.lnr = xl.c;
+          d.g[0] = d1p(c, 0, xl.d1, xl.d2, xl.d3);
+          d.g[1] = d1p(c, 1, yl.d1, yl.d2, yl.d3);
+          d.g[2] = d1p(c, 2, zd1, zd2, zd3);
+          d.up = bc(0.f);
+          if (c.upwind) {
+            // sixth difference (f-3 + f3) - 6 (f-2 + f2) + 15 (f-1 + f1) - 20 f0 per axis
+            const float2 m20 = mul2(bc(-20.f), xl.c);
+            auto d6 = [&](float2 e1, float2 e2, float2 e3) {
+              return add2(fma2(bc(-6.f), e2, e3), fma2(bc(15.f), e1, m20));
+            };
+            auto absu = [&](float2 u) { return pk(fabsf(u.x), fabsf(u.y)); };
+            d.up = fma2(mul2(c.w6(2), absu(d.u[2])), d6(ze1, ze2, ze3),
+                        fma2(mul2(c.w6(1), absu(d.u[1])), d6(yl.e1, yl.e2, yl.e3),
+                             mul2(mul2(c.w6(0), absu(d.u[0])), d6(xl.e1, xl.e2, xl.e3))));
+          }
+
+          // forcing of the step at the pair (Eqs. 4-6)
+          float2 fz[3] = {bc(0.f), bc(0.f), bc(0.f)};
+          if (forcing) {
+            const Cplx<float> ez = cmul(rz[mz], ephi);  // e^{i (k_z z + phi)}
+            const float2 er = fma2(exr, bc(ez.re), mul2(exi, bc(-ez.im)));
+            const float2 ei = fma2(exr, bc(ez.im), mul2(exi, bc(ez.re)));
+#pragma unroll
+            for (int a = 0; a < 3; ++a) fz[a] = fma2(bc(fa[a]), er, mul2(bc(-fb[a]), ei));
+          }
+          const float2 fr[3] = {force_in_rhs ? fz[0] : bc(0.f), force_in_rhs ? fz[1] : bc(0.f),
+                                force_in_rhs ? fz[2] : bc(0.f)};
+          float2 r[NF];
+          rhs_pair(d, c, fr, r);
+
+          // RK3-2N update: w <- alpha w + dt RHS, q <- q + beta w
+          const float2 qc[NF] = {xl.c, xux.c, xuy.c, xuz.c, xAx.c, xAy.c, xAz.c};
+          float2 wv[NF], qn[NF];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            wv[f] = mul2(dt, r[f]);
+            if (substep > 0) wv[f] = fma2(alpha, wc[f], wv[f]);
+            qn[f] = fma2(beta, wv[f], qc[f]);
+          }
+          if (force_at_end)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) qn[1 + a] = fma2(dt, fz[a], qn[1 + a]);
+          if (act0) {
+            const int z = tile.z0 + o - RAD;  // interior index of the output plane
+            const bool zn = z < RAD || z >= nz - RAD;
+            const bool near0 = edge0 || zn, near1 = edge1 || zn;
+            if (act1 && !near0 && !near1) {
+              float *wp = w + cidx, *qp = qout + cidx;
+#pragma unroll
+              for (int f = 0; f < NF; ++f, wp += fs, qp += fs) {
+                if (substep < 2) __stcs(reinterpret_cast<float2 *>(wp), wv[f]);
+                __stcs(reinterpret_cast<float2 *>(qp), qn[f]);
+              }
+            } else {
+              float q0[NF], q1[NF];
+#pragma unroll
+              for (int f = 0; f < NF; ++f) {
+                q0[f] = qn[f].x;
+                q1[f] = qn[f].y;
+                if (substep < 2) {
+                  __stcs(w + cidx + f * fs, wv[f].x);
+                  if (act1) __stcs(w + cidx + 1 + f * fs, wv[f].y);
+                }
+              }
+              store_with_images<float, true>(qout, fs, cidx, q0, near0, x, y, z, nx, ny, nz, px, py, zper);
+              if (act1)
+                store_with_images<float, true>(qout, fs, cidx + 1, q1, near1, x + 1, y, z, nx, ny, nz, px, py, zper);
+            }
+          }
+
+          // the output plane leaves the centre: its differences and centres enter the registers
+          pass1(aX1, 1, xuz.d1, xuz.d2, xuz.d3);
+          pass1(aY1, 2, yuz.d1, yuz.d2, yuz.d3);
+          pass2(aZ1, xux.d1, xux.d2, xux.d3, yuy.d1, yuy.d2, yuy.d3);
+          pass1(aX2, 1, xAz.d1, xAz.d2, xAz.d3);
+          pass1(aY2, 2, yAz.d1, yAz.d2, yAz.d3);
+          pass2(aZ2, xAx.d1, xAx.d2, xAx.d3, yAy.d1, yAy.d2, yAy.d3);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            pz[f][0] = pz[f][1];
+            pz[f][1] = pz[f][2];
+            pz[f][2] = qc[f];
+          }
+        }
+      }
+      if (outp) {
+        cidx += wplane;
+        if (forcing) {
+          mz += kz;
+          if (mz >= nzg) mz -= nzg;
+        }
+      }
+      if (++slot == NS) {
+        slot = 0;
+        phase ^= 1u;
+      }
+      if constexpr (BAR == 1) {
+        if (__syncthreads_or(!ok)) {
+          failed = true;
+          fail_run = tile.run;
+          fail_p = p;
+        }
+      } else {
+        // a wait that gave up between barriers is remembered and caught at
+        // the next one; the clean-up then waits again from the earliest
+        // plane it could concern
+        waits_ok &= ok;
+        if (p % BAR == BAR - 1 || p == npl - 1) {
+          if (__syncthreads_or(!waits_ok)) {
+            failed = true;
+            fail_run = tile.run;
+            fail_p = p >= BAR - 1 ? p - (BAR - 1) : 0;
+          }
+        }
+      }
+    }
+    if (!failed) G += npl;
+  }
+
+  if (failed && tid == 0) {
+    // record the time-out, then wait (bounded) for the copies still in flight
+    atomicOr(&runs[fail_run].clock->status, 2);
+    for (int p = fail_p; p < issued_hi; ++p) {
+      const unsigned long long g = G + p;
+      mbar_wait(&bars[(int)(g % NS)], (uint32_t)((g / NS) & 1ull));
+    }
+  }
+}
+
+namespace {
+template <int TY, int NS>
+constexpr int x2_smem_bytes() {
+  return NS * TmaShape<float, TY, 64>::STAGE_BYTES + NS * 8;
+}
+}  // namespace
+
+// Tile rows of a paired-point variant (0 if `tile` is not one).
+int x2_rows(int tile) {
+#define X(ID, TY, NS, BR) \
+  if (tile == ID) return TY;
+  MHD_X2_VARIANTS(X)
+#undef X
+  return 0;
+}
+
+int x2_prepare(int tile) {
+#define X(ID, TY, NS, BR)                                                                                   \
+  if (tile == ID) {                                                                                         \
+    int e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, true>,                                        \
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, x2_smem_bytes<TY, NS>()); \
+    if (!e)                                                                                                 \
+      e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, false>,                                         \
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, x2_smem_bytes<TY, NS>());   \
+    return e;                                                                                               \
+  }
+  MHD_X2_VARIANTS(X)
+#undef X
+  return (int)cudaErrorInvalidValue;
+}
+
+int x2_occupancy(int tile, int *bps) {
+#define X(ID, TY, NS, BR)                                                                                  \
+  if (tile == ID)                                                                                          \
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_substep_x2<TY, NS, BR, true>, 32 * TY, \
+                                                              x2_smem_bytes<TY, NS>());
+  MHD_X2_VARIANTS(X)
+#undef X
+  return (int)cudaErrorInvalidValue;
+}
+
+int x2_launch(int tile, const RunDesc *runs, const Tile *tiles, int ntiles, int substep, int grid, int iso,
+              cudaStream_t s) {
+  if (grid <= 0 || grid > ntiles) grid = ntiles;
+  if (grid == 0) return 0;
+#define X(ID, TY, NS, BR)                                                                                       \
+  if (tile == ID) {                                                                                             \
+    if (iso)                                                                                                    \
+      k_substep_x2<TY, NS, BR, true><<<grid, dim3(32, TY), x2_smem_bytes<TY, NS>(), s>>>(runs, tiles, ntiles,   \
+                                                                                          substep);             \
+    else                                                                                                        \
+      k_substep_x2<TY, NS, BR, false><<<grid, dim3(32, TY), x2_smem_bytes<TY, NS>(), s>>>(runs, tiles, ntiles,  \
+                                                                                           substep);            \
+    return (int)cudaGetLastError();                                                                             \
+  }
+  MHD_X2_VARIANTS(X)
+#undef X
+  return (int)cudaErrorInvalidValue;
+}
+
+}  // namespace mhd

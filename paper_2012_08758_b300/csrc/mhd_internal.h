@@ -116,6 +116,13 @@ int tma_launch_prologue(int dtype, int tile, const RunDesc *runs, const Tile *ti
                         cudaStream_t s, int mode = 0);
 int tma_launch(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles, int substep,
                int grid, int iso, cudaStream_t s);
+// Paired-point FP32 substep variants (kernels_x2.cu): x2_rows(tile) is the
+// tile's row count (0: not such a variant); tiles are 64 points wide.
+int x2_rows(int tile);
+int x2_prepare(int tile);
+int x2_occupancy(int tile, int *bps);
+int x2_launch(int tile, const RunDesc *runs, const Tile *tiles, int ntiles, int substep, int grid, int iso,
+              cudaStream_t s);
 int substep_tile_shape(int dtype, int kernel, int tile, int *tx, int *ty);
 int substep_max_grid(int dtype, int kernel, int tile, int *blocks_per_sm);
 int launch_halo(int dtype, void *fields, int nfields, long long fstride, int nx, int ny, int nz,

@@ -1,0 +1,13 @@
+// Tile variants of the paired-point substep kernel (kernels_x2.cu), FP32:
+// id -> (TY rows of 64 points, TMA stages, planes between CTA barriers).
+// Each thread computes two neighbouring x-points; a CTA of 32 x TY threads
+// covers a 64 x TY column.  Prefetch distance NS - 3 - BAR >= 1 planes.
+#pragma once
+#define MHD_X2_VARIANTS(X) \
+  X(17, 8, 6, 2)           \
+  X(18, 8, 7, 3)           \
+  X(19, 4, 5, 1)           \
+  X(20, 6, 6, 2)           \
+  X(21, 8, 5, 1)
+#define MHD_X2_FIRST 17
+#define MHD_X2_LAST 21
