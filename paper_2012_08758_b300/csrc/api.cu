@@ -41,7 +41,8 @@ struct Layout {
   size_t sub_cap;  // entries reserved for the substep work split
   size_t total;
   int nk;
-  int tw, th;
+  int tw, th;    // reduction tiles (prologue, diagnostics): block shape and TMA box of rmap
+  int stw, sth;  // substep tiles: TMA box of tmap and the work split's columns
   std::vector<Tile> tiles_host;
 };
 
@@ -233,13 +234,22 @@ int validate(const mhd_params *p, std::string *why) {
   return MHD_OK;
 }
 
-// AUTO resolves to the TMA kernel; tile 0 to the default tile of the kernel
-// (the fastest measured at 256^3 on B300: FP32 32x12 with 9 stages and a CTA
-// barrier every fifth plane, FP64 32x8 with 6 stages).
+// AUTO resolves to the TMA kernel; tile 0 to the fastest variant measured on
+// B300 for the grid: FP32 grids with at least LARGE_COLUMNS columns of 64 x 8
+// points (e.g. 512^2 and up) take the paired-point kernel with 8 stages and a
+// CTA barrier every fourth plane (tile 22; 512^3: 8.0e9 against 7.6e9
+// cell-updates/s), smaller FP32 grids the 32 x 12 scalar kernel with 9 stages
+// and a barrier every fifth plane (tile 13; 256^3: 7.5e9 against 6.9e9), FP64
+// the 32 x 8 tile with 6 stages.  Runs of one batch need the same resolved
+// tile, so a batch that mixes the two classes must name a tile explicitly.
+constexpr int LARGE_COLUMNS = 256;
 mhd_params resolved(const mhd_params *p) {
   mhd_params r = *p;
   if (r.kernel == MHD_KERNEL_AUTO) r.kernel = MHD_KERNEL_TMA;
-  if (r.kernel == MHD_KERNEL_TMA && r.tile == 0) r.tile = r.dtype == MHD_F32 ? 13 : 3;
+  if (r.kernel == MHD_KERNEL_TMA && r.tile == 0) {
+    const long long cols64 = (long long)((r.nx + 63) / 64) * ((r.ny + 7) / 8);
+    r.tile = r.dtype == MHD_F32 ? (cols64 >= LARGE_COLUMNS ? 22 : 13) : 3;
+  }
   return r;
 }
 
@@ -295,7 +305,8 @@ Layout make_layout(const mhd_params *p_in) {
   L.pz = p->nz + 2 * RAD;
   L.fstride = (long long)L.px * L.py * L.pz;
   L.nk = p->f0 > 0 ? shell_vectors(p->kmin, p->kmax, nullptr) : 0;
-  substep_tile_shape(p->dtype, p->kernel, p->tile, &L.tw, &L.th);
+  substep_tile_shape(p->dtype, p->kernel, p->tile, &L.stw, &L.sth);
+  reduction_tile_shape(p->dtype, p->kernel, p->tile, &L.tw, &L.th);
   // The tile table is a function of the parameters alone (not of the device
   // it runs on), so per-tile reduction partials -- and hence every reduced
   // value -- come out in the same order on every GPU and in every batch.
@@ -321,7 +332,7 @@ Layout make_layout(const mhd_params *p_in) {
   L.scratch = take(sizeof(double) * 16);
   L.run = take(sizeof(RunDesc));
   L.tiles = take(sizeof(Tile) * L.tiles_host.size());
-  const size_t ncols = (size_t)((p->nx + L.tw - 1) / L.tw) * ((p->ny + L.th - 1) / L.th);
+  const size_t ncols = (size_t)((p->nx + L.stw - 1) / L.stw) * ((p->ny + L.sth - 1) / L.sth);
   L.sub_cap = ncols + 3 * (size_t)GMAX;
   L.sub_tiles = take(sizeof(Tile) * L.sub_cap);
   L.total = o;
@@ -586,7 +597,8 @@ int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t worksp
   if (p->kernel == MHD_KERNEL_TMA) {
     std::string why;
     for (int b = 0; b < 2; ++b)
-      if (encode_state_map(&R.tmap[b], R.q[b], L.esz, L.px, L.py, L.pz, L.tw, L.th, &why)) {
+      if (encode_state_map(&R.tmap[b], R.q[b], L.esz, L.px, L.py, L.pz, L.stw, L.sth, &why) ||
+          encode_state_map(&R.rmap[b], R.q[b], L.esz, L.px, L.py, L.pz, L.tw, L.th, &why)) {
         fail(ctx, MHD_ECUDA, "%s", why.c_str());
         return cleanup(MHD_ECUDA);
       }
@@ -597,7 +609,7 @@ int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t worksp
   if (substep_max_grid(p->dtype, p->kernel, p->tile, &bps) != 0 || bps < 1) bps = 1;
   ctx->grid = std::min(ctx->ntiles, bps * num_sms());
   std::vector<SubCol> cols;
-  add_columns(&cols, 0, p->nx, p->ny, p->nz, L.tw, L.th);
+  add_columns(&cols, 0, p->nx, p->ny, p->nz, L.stw, L.sth);
   int sub_grid = 1;
   std::vector<Tile> sub_tiles = split_columns(cols, std::min(bps * num_sms(), GMAX), &sub_grid);
   if (sub_tiles.size() <= L.sub_cap) {
@@ -902,7 +914,7 @@ int mhd_substep_plan(const mhd_params *p, int grid_ctas, int *tiles, int max_til
   if (grid_ctas < 1 || !ntiles || !grid) return fail(nullptr, MHD_EINVAL, "grid_ctas < 1 or NULL output");
   const Layout L = make_layout(p);
   std::vector<SubCol> cols;
-  add_columns(&cols, 0, p->nx, p->ny, p->nz, L.tw, L.th);
+  add_columns(&cols, 0, p->nx, p->ny, p->nz, L.stw, L.sth);
   const std::vector<Tile> t = split_columns(cols, std::min(grid_ctas, GMAX), grid);
   *ntiles = (int)t.size();
   for (size_t i = 0; tiles && i < t.size() && (int)i < max_tiles; ++i) {
@@ -1083,7 +1095,9 @@ int mhd_batch_create(mhd_ctx *const *runs, int nruns, mhd_batch **out) {
     if (!r) return fail(nullptr, MHD_EINVAL, "runs[%d] is NULL", i);
     if (r->p.dtype != r0->p.dtype || r->stream != r0->stream || r->p.kernel != r0->p.kernel ||
         r->p.tile != r0->p.tile)
-      return fail(nullptr, MHD_EINVAL, "runs of a batch must share dtype, stream, kernel and tile");
+      return fail(nullptr, MHD_EINVAL,
+                  "runs of a batch must share dtype, stream, kernel and tile (tile 0 resolves by grid size: "
+                  "name a tile to batch large and small grids together)");
     for (int j = 0; j < i; ++j)
       if (runs[j] == r) return fail(nullptr, MHD_EINVAL, "run %d appears twice", i);
     cells_total += (double)r->p.nx * r->p.ny * r->p.nz;
@@ -1125,7 +1139,7 @@ int mhd_batch_create(mhd_ctx *const *runs, int nruns, mhd_batch **out) {
   b->grid = std::min(b->ntiles, bps * num_sms());
   std::vector<SubCol> cols;
   for (int i = 0; i < nruns; ++i)
-    add_columns(&cols, i, runs[i]->p.nx, runs[i]->p.ny, runs[i]->p.nz, runs[i]->L.tw, runs[i]->L.th);
+    add_columns(&cols, i, runs[i]->p.nx, runs[i]->p.ny, runs[i]->p.nz, runs[i]->L.stw, runs[i]->L.sth);
   std::vector<Tile> sub_tiles = split_columns(cols, std::min(bps * num_sms(), GMAX), &b->sub_grid);
   b->nsub = (int)sub_tiles.size();
   b->d_runs = nullptr;
@@ -1413,13 +1427,13 @@ int mhd_slabs_create(const mhd_params *p_in, int nslabs, int overlap, void *stre
     }
     slot0 += c->ntiles;
     const int nzk = S->nzs[k];
-    add_columns(&c_all, k, p.nx, p.ny, nzk, c->L.tw, c->L.th);
+    add_columns(&c_all, k, p.nx, p.ny, nzk, c->L.stw, c->L.sth);
     if (nzk >= 2 * 2 * RAD) {  // outer: the three planes at each face; inner: the rest
-      add_columns(&c_outer, k, p.nx, p.ny, RAD, c->L.tw, c->L.th, 0);
-      add_columns(&c_outer, k, p.nx, p.ny, RAD, c->L.tw, c->L.th, nzk - RAD);
-      add_columns(&c_inner, k, p.nx, p.ny, nzk - 2 * RAD, c->L.tw, c->L.th, RAD);
+      add_columns(&c_outer, k, p.nx, p.ny, RAD, c->L.stw, c->L.sth, 0);
+      add_columns(&c_outer, k, p.nx, p.ny, RAD, c->L.stw, c->L.sth, nzk - RAD);
+      add_columns(&c_inner, k, p.nx, p.ny, nzk - 2 * RAD, c->L.stw, c->L.sth, RAD);
     } else {  // too thin to split: all of it is outer
-      add_columns(&c_outer, k, p.nx, p.ny, nzk, c->L.tw, c->L.th, 0);
+      add_columns(&c_outer, k, p.nx, p.ny, nzk, c->L.stw, c->L.sth, 0);
     }
   }
   int bps = 1;

@@ -263,6 +263,17 @@ int substep_tile_shape(int dtype, int kernel, int tile, int *tx, int *ty) {
   return 0;
 }
 
+// The paired-point variants (64-point substep tiles) reduce over 32 x 12
+// tiles, with the prologue of the 32 x 12 scalar variant.
+int reduction_tile_shape(int dtype, int kernel, int tile, int *tx, int *ty) {
+  if (kernel == 2 && dtype == 0 && x2_rows(tile) > 0) {
+    *tx = 32;
+    *ty = 12;
+    return 0;
+  }
+  return substep_tile_shape(dtype, kernel, tile, tx, ty);
+}
+
 int substep_max_grid(int dtype, int kernel, int tile, int *blocks_per_sm) {
   if (kernel == 2) return tma_occupancy(dtype, tile, blocks_per_sm);
   int n = 0;

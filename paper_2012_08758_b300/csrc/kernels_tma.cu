@@ -751,7 +751,7 @@ __global__ void __launch_bounds__(TXW * TY, TXW == 32 ? 2 : 1)
       mbar_fence_init();
     }
     __syncthreads();
-    const CUtensorMap *map = &R.tmap[step & 1];
+    const CUtensorMap *map = &R.rmap[step & 1];
     const int npl = (tile.z1 - tile.z0) + 2 * RAD;
     auto issue = [&](int p) {
       const int sl = p % NS;
@@ -984,19 +984,10 @@ int tma_tile_shape(int dtype, int tile, int *tx, int *ty) {
 }
 
 int tma_prepare(int dtype, int tile) {
-#define X(ID, TY, NS, BR)                                                                                       \
-  if (dtype == 0 && tile == ID) {                                                                              \
-    int e = x2_prepare(tile);                                                                                  \
-    if (!e)                                                                                                    \
-      e = (int)cudaFuncSetAttribute(k_prologue_tma<float, TY, 0, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                    pro_smem_bytes<float, TY, 64>());                                          \
-    if (!e)                                                                                                    \
-      e = (int)cudaFuncSetAttribute(k_prologue_tma<float, TY, 1, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                    pro_smem_bytes<float, TY, 64>());                                          \
-    return e;                                                                                                  \
+  if (dtype == 0 && x2_rows(tile) > 0) {  // the substep kernel, and the prologue of tile 13 (32 x 12)
+    const int e = x2_prepare(tile);
+    return e ? e : tma_prepare(0, 13);
   }
-  MHD_X2_VARIANTS(X)
-#undef X
 #define X(ID, SC, TY, NS)                                                                            \
   if (dtype == 0 && tile == ID) {                                                                    \
     int e = (int)cudaFuncSetAttribute(k_substep_tma_f2<TY, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
@@ -1039,16 +1030,7 @@ int tma_occupancy(int dtype, int tile, int *bps) {
 int tma_launch_prologue(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int ntiles,
                         cudaStream_t s, int mode) {
   if (ntiles <= 0) return 0;
-#define X(ID, TY, NS, BR)                                                                                   \
-  if (dtype == 0 && tile == ID) {                                                                          \
-    if (mode == 1)                                                                                         \
-      k_prologue_tma<float, TY, 1, 64><<<ntiles, dim3(64, TY), pro_smem_bytes<float, TY, 64>(), s>>>(runs, tiles); \
-    else                                                                                                   \
-      k_prologue_tma<float, TY, 0, 64><<<ntiles, dim3(64, TY), pro_smem_bytes<float, TY, 64>(), s>>>(runs, tiles); \
-    return (int)cudaGetLastError();                                                                        \
-  }
-  MHD_X2_VARIANTS(X)
-#undef X
+  if (dtype == 0 && x2_rows(tile) > 0) return tma_launch_prologue(0, 13, runs, tiles, ntiles, s, mode);
 #define X(ID, SC, TY, NS) \
   if (dtype == 0 && tile == ID) return tma_launch_prologue(0, SC, runs, tiles, ntiles, s, mode);
   MHD_PACKED_VARIANTS(X)

@@ -49,6 +49,9 @@ struct StepCoeffs {
 // Everything a kernel needs to know about one run, resident in device memory.
 struct RunDesc {
   CUtensorMap tmap[2];      // TMA maps of q[0], q[1]: 4-D (x, y, z, field), box of one z-plane
+                            // of a substep tile with its halo
+  CUtensorMap rmap[2];      // the same for the reduction tiles (step prologue, B_rms sweep);
+                            // equal to tmap unless the substep tile is wider
   int nx, ny, nz;
   int px, py, pz;           // padded extents; px is the row pitch
   long long fstride;        // elements per field (px * py * pz)
@@ -124,6 +127,8 @@ int x2_occupancy(int tile, int *bps);
 int x2_launch(int tile, const RunDesc *runs, const Tile *tiles, int ntiles, int substep, int grid, int iso,
               cudaStream_t s);
 int substep_tile_shape(int dtype, int kernel, int tile, int *tx, int *ty);
+// block shape of the reduction kernels and the step prologue for this variant
+int reduction_tile_shape(int dtype, int kernel, int tile, int *tx, int *ty);
 int substep_max_grid(int dtype, int kernel, int tile, int *blocks_per_sm);
 int launch_halo(int dtype, void *fields, int nfields, long long fstride, int nx, int ny, int nz,
                 int px, int py, cudaStream_t s);

@@ -8,6 +8,7 @@
   X(18, 8, 7, 3)           \
   X(19, 4, 5, 1)           \
   X(20, 6, 6, 2)           \
-  X(21, 8, 5, 1)
+  X(21, 8, 5, 1)           \
+  X(22, 8, 8, 4)
 #define MHD_X2_FIRST 17
-#define MHD_X2_LAST 21
+#define MHD_X2_LAST 22
