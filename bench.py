@@ -76,7 +76,8 @@ def kernel_source_hash():
     figure of the committed ncu capture is void once any of them changes)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2012_08758_b300", "csrc")
-    for name in ("kernels_tma.cu", "physics.cuh", "step_device.cuh", "mhd_internal.h"):
+    for name in ("kernels_tma.cu", "kernels_x2.cu", "tma_util.cuh", "x2_variants.h", "physics.cuh",
+                 "step_device.cuh", "mhd_internal.h"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
@@ -212,11 +213,13 @@ def dist_setup():
     return env()
 
 
-def step_config(n, dtype, world):
+def step_config(n, dtype, world, nz=None):
     """config of the step line (shared by both arms)."""
+    nz = nz or n
     px = (n + 7 + 7) // 8 * 8
-    nbytes = 21 * px * (n + 6) * (n + 6) * (4 if dtype == "f32" else 8)
-    return {"workload": workload_name(n, dtype), "grid": n, "replicas": world,
+    nbytes = 21 * px * (n + 6) * (nz + 6) * (4 if dtype == "f32" else 8)
+    name = workload_name(n, dtype) if nz == n else workload_name(n, dtype).replace(f"{n}^3", f"{n}^2 x {nz}", 1)
+    return {"workload": name, "grid": n, "nz": nz, "replicas": world,
             "parallelism": f"replicas x{world} (independent runs, no collective)",
             "l2": "inputs larger than L2 (21 padded arrays, %.2f GB)" % (nbytes / 1e9)}
 
@@ -272,15 +275,18 @@ def run_ours(args):
     from paper_2012_08758_b300.run import Run
 
     n, dtype = args.n, args.dtype
-    cells = n ** 3
+    nz = args.nz or n  # --nz: an n^2 x nz box (smaller captures of the same x-y structure)
+    cells = n * n * nz
     wl = workload(n)
-    run = Run(n=n, device=dev, dtype=B.MHD_F32 if dtype == "f32" else B.MHD_F64, kernel=args.kernel,
-              tile=args.tile, **dict(wl, seed=wl["seed"] + rank))
+    if nz != n:  # keep the grid spacing isotropic: box 2 pi x 2 pi x 2 pi nz / n
+        wl = dict(wl, lz=2 * math.pi * nz / n)
+    run = Run(nx=n, ny=n, nz=nz, device=dev, dtype=B.MHD_F32 if dtype == "f32" else B.MHD_F64,
+              kernel=args.kernel, tile=args.tile, **dict(wl, seed=wl["seed"] + rank))
     seed_key = replica_seed(0, rank)
     run.set_seed_field(seed_key, SEED_AMP)  # the paper's initial condition, on the device
     # host copy of the initial state (pinned), for the end-to-end leg
     hdt = torch.float32 if dtype == "f32" else torch.float64
-    host_in = torch.empty((7, n, n, n), dtype=hdt).pin_memory().numpy()
+    host_in = torch.empty((7, nz, n, n), dtype=hdt).pin_memory().numpy()
     B.mhd_get_state(run.ctx, host_in)
     run.step(args.warmup)
     run.sync()
@@ -304,7 +310,7 @@ def run_ours(args):
     bpc = BYTES_PER_CELL[dtype]
     achieved = bpc * cells * args.steps / (sub_ms / 1e3) / 1e9
     peak, peak_src = measured_peaks()
-    traffic = ncu_traffic(n, dtype)
+    traffic = ncu_traffic(n, dtype) if nz == n else None
     step_gbs = bpc * cells * args.steps / (total_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "kernel": "k_substep (fused RHS + RK3-2N), 3 launches per step",
@@ -318,7 +324,7 @@ def run_ours(args):
                                   "substep3": stage_ms[3] / args.steps}}
 
     # --- end to end through the public API with host buffers ---
-    host_out = torch.empty((7, n, n, n), dtype=hdt).pin_memory().numpy()
+    host_out = torch.empty((7, nz, n, n), dtype=hdt).pin_memory().numpy()
     e2e_steps = args.steps
     barrier()
     t0 = time.perf_counter()
@@ -341,7 +347,7 @@ def run_ours(args):
     # --- FP64 beside FP32 on the same workload (few steps: ALU-bound) ---
     fp64 = None
     if dtype == "f32" and not args.skip_fp64:
-        run64 = Run(n=n, device=dev, dtype=B.MHD_F64, **dict(wl, seed=wl["seed"] + rank))
+        run64 = Run(nx=n, ny=n, nz=nz, device=dev, dtype=B.MHD_F64, **dict(wl, seed=wl["seed"] + rank))
         run64.set_seed_field(seed_key, SEED_AMP)
         run64.step(1)
         run64.sync()
@@ -351,7 +357,7 @@ def run_ours(args):
         run64.close()
         # per-quantity FP32 error against FP64 after the same 1 + k64 steps
         # from the same initial state (the at-scale configuration's check)
-        run32 = Run(n=n, device=dev, dtype=B.MHD_F32, **dict(wl, seed=wl["seed"] + rank))
+        run32 = Run(nx=n, ny=n, nz=nz, device=dev, dtype=B.MHD_F32, **dict(wl, seed=wl["seed"] + rank))
         run32.set_seed_field(seed_key, SEED_AMP)
         run32.step(1 + k64)
         d32 = run32.diagnostics()
@@ -394,7 +400,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-                "config": step_config(n, dtype, world),
+                "config": step_config(n, dtype, world, nz),
                 "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "fp64": fp64,
                 "batch": batch, "serving": serve,
                 "gpu_launches": 4 * args.steps, "clocks": clk.summary()}
@@ -792,6 +798,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--nz", type=int, default=0, help="z planes of the step workload (default: n)")
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--workload", choices=["step", "batch", "serve", "fp32vs64", "paper", "spectrum", "tables",
                                            "c2", "cpu", "slabs"],

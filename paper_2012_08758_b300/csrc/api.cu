@@ -160,7 +160,10 @@ std::vector<Tile> split_columns(const std::vector<SubCol> &cols, int G, int *gri
   for (size_t k = q * G; k < full.size(); ++k) rest.push_back(full[k]);
   std::sort(rest.begin(), rest.end());
   // the rest, end to end: CTA g takes a contiguous share budget[g] that
-  // tops its load up to the common total (equal shares when q == 0)
+  // tops its load up to the common total (equal shares when q == 0).  (A
+  // z-aligned split of the rest -- piece h of every remaining column on the
+  // same planes -- measured 1.27x algorithmic DRAM traffic instead of ~1.5x
+  // but 4-5% slower steps: it cannot even out the heavier face columns.)
   double R = 0;
   for (size_t i : rest) R += cols[i].w * cols[i].nz;
   const int Gr = rest.empty() ? 0 : (int)std::max(1.0, std::min((double)G, std::floor(R / MIN_SHARE)));
@@ -236,8 +239,8 @@ int validate(const mhd_params *p, std::string *why) {
 
 // AUTO resolves to the TMA kernel; tile 0 to the fastest variant measured on
 // B300 for the grid: FP32 grids with at least LARGE_COLUMNS columns of 64 x 8
-// points (e.g. 512^2 and up) take the paired-point kernel with 8 stages and a
-// CTA barrier every fourth plane (tile 22; 512^3: 8.0e9 against 7.6e9
+// points (e.g. 512^2 and up) take the paired-point kernel with 7 stages and a
+// CTA barrier every third plane (tile 18; 512^3: 8.2e9 against 7.6e9
 // cell-updates/s), smaller FP32 grids the 32 x 12 scalar kernel with 9 stages
 // and a barrier every fifth plane (tile 13; 256^3: 7.5e9 against 6.9e9), FP64
 // the 32 x 8 tile with 6 stages.  Runs of one batch need the same resolved
@@ -248,7 +251,7 @@ mhd_params resolved(const mhd_params *p) {
   if (r.kernel == MHD_KERNEL_AUTO) r.kernel = MHD_KERNEL_TMA;
   if (r.kernel == MHD_KERNEL_TMA && r.tile == 0) {
     const long long cols64 = (long long)((r.nx + 63) / 64) * ((r.ny + 7) / 8);
-    r.tile = r.dtype == MHD_F32 ? (cols64 >= LARGE_COLUMNS ? 22 : 13) : 3;
+    r.tile = r.dtype == MHD_F32 ? (cols64 >= LARGE_COLUMNS ? 18 : 13) : 3;
   }
   return r;
 }

@@ -401,74 +401,105 @@ __global__ void __launch_bounds__(32 * TY, 1)
           PairDerivs d;
           float2 zd1, zd2, zd3, ze1, ze2, ze3;
 
+          // Each field group is finished -- its differences passed on to the
+          // rings of the planes below and its centres pushed into the pencils --
+          // as soon as its derivatives are formed, so that its rows need no
+          // registers afterwards.
           // vector potential: B = curl A, lap A, j
-          const XRow xAx = xrow(so + 4 * FIELD), xAy = xrow(so + 5 * FIELD), xAz = xrow(so + 6 * FIELD);
-          const YRow yAx = yrow<SX>(so + 4 * FIELD), yAy = yrow<SX>(so + 5 * FIELD), yAz = yrow<SX>(so + 6 * FIELD);
-          float2 Axz_, Ayz_, Azz;
-          zrow(4, zd1, zd2, zd3, ze1, ze2, ze3);
-          const float2 dzAx = d1p(c, 2, zd1, zd2, zd3);
-          Axz_ = d2p(c, 2, xAx.c, ze1, ze2, ze3);
-          zrow(5, zd1, zd2, zd3, ze1, ze2, ze3);
-          const float2 dzAy = d1p(c, 2, zd1, zd2, zd3);
-          Ayz_ = d2p(c, 2, xAy.c, ze1, ze2, ze3);
-          zrow(6, zd1, zd2, zd3, ze1, ze2, ze3);
-          Azz = d2p(c, 2, xAz.c, ze1, ze2, ze3);
-          d.B[0] = sub2(d1p(c, 1, yAz.d1, yAz.d2, yAz.d3), dzAy);
-          d.B[1] = sub2(dzAx, d1p(c, 0, xAz.d1, xAz.d2, xAz.d3));
-          d.B[2] = sub2(d1p(c, 0, xAy.d1, xAy.d2, xAy.d3), d1p(c, 1, yAx.d1, yAx.d2, yAx.d3));
-          const float2 Axx = d2p(c, 0, xAx.c, xAx.e1, xAx.e2, xAx.e3), Axy_ = d2p(c, 1, xAx.c, yAx.e1, yAx.e2, yAx.e3);
-          const float2 Ayx = d2p(c, 0, xAy.c, xAy.e1, xAy.e2, xAy.e3), Ayy = d2p(c, 1, xAy.c, yAy.e1, yAy.e2, yAy.e3);
-          const float2 Azx = d2p(c, 0, xAz.c, xAz.e1, xAz.e2, xAz.e3), Azy = d2p(c, 1, xAz.c, yAz.e1, yAz.e2, yAz.e3);
-          d.lapA[0] = add2(add2(Axx, Axy_), Axz_);
-          d.lapA[1] = add2(add2(Ayx, Ayy), Ayz_);
-          d.lapA[2] = add2(add2(Azx, Azy), Azz);
-          d.jc[0] = sub2(sub2(add2(dxy_pair<SX>(so + 5 * FIELD, c), add2(fxz(6), aX2[0])), Axy_), Axz_);
-          d.jc[1] = sub2(sub2(add2(dxy_pair<SX>(so + 4 * FIELD, c), add2(fyz(6), aY2[0])), Ayx), Ayz_);
-          d.jc[2] = sub2(sub2(add2(add2(fxz(4), fyz(5)), aZ2[0]), Azx), Azy);
+          {
+            const XRow xAx = xrow(so + 4 * FIELD), xAy = xrow(so + 5 * FIELD), xAz = xrow(so + 6 * FIELD);
+            const YRow yAx = yrow<SX>(so + 4 * FIELD), yAy = yrow<SX>(so + 5 * FIELD), yAz = yrow<SX>(so + 6 * FIELD);
+            zrow(4, zd1, zd2, zd3, ze1, ze2, ze3);
+            const float2 dzAx = d1p(c, 2, zd1, zd2, zd3);
+            const float2 Axz_ = d2p(c, 2, xAx.c, ze1, ze2, ze3);
+            zrow(5, zd1, zd2, zd3, ze1, ze2, ze3);
+            const float2 dzAy = d1p(c, 2, zd1, zd2, zd3);
+            const float2 Ayz_ = d2p(c, 2, xAy.c, ze1, ze2, ze3);
+            zrow(6, zd1, zd2, zd3, ze1, ze2, ze3);
+            const float2 Azz = d2p(c, 2, xAz.c, ze1, ze2, ze3);
+            d.B[0] = sub2(d1p(c, 1, yAz.d1, yAz.d2, yAz.d3), dzAy);
+            d.B[1] = sub2(dzAx, d1p(c, 0, xAz.d1, xAz.d2, xAz.d3));
+            d.B[2] = sub2(d1p(c, 0, xAy.d1, xAy.d2, xAy.d3), d1p(c, 1, yAx.d1, yAx.d2, yAx.d3));
+            const float2 Axx = d2p(c, 0, xAx.c, xAx.e1, xAx.e2, xAx.e3), Axy_ = d2p(c, 1, xAx.c, yAx.e1, yAx.e2, yAx.e3);
+            const float2 Ayx = d2p(c, 0, xAy.c, xAy.e1, xAy.e2, xAy.e3), Ayy = d2p(c, 1, xAy.c, yAy.e1, yAy.e2, yAy.e3);
+            const float2 Azx = d2p(c, 0, xAz.c, xAz.e1, xAz.e2, xAz.e3), Azy = d2p(c, 1, xAz.c, yAz.e1, yAz.e2, yAz.e3);
+            d.lapA[0] = add2(add2(Axx, Axy_), Axz_);
+            d.lapA[1] = add2(add2(Ayx, Ayy), Ayz_);
+            d.lapA[2] = add2(add2(Azx, Azy), Azz);
+            d.jc[0] = sub2(sub2(add2(dxy_pair<SX>(so + 5 * FIELD, c), add2(fxz(6), aX2[0])), Axy_), Axz_);
+            d.jc[1] = sub2(sub2(add2(dxy_pair<SX>(so + 4 * FIELD, c), add2(fyz(6), aY2[0])), Ayx), Ayz_);
+            d.jc[2] = sub2(sub2(add2(add2(fxz(4), fyz(5)), aZ2[0]), Azx), Azy);
+            pass1(aX2, 1, xAz.d1, xAz.d2, xAz.d3);
+            pass1(aY2, 2, yAz.d1, yAz.d2, yAz.d3);
+            pass2(aZ2, xAx.d1, xAx.d2, xAx.d3, yAy.d1, yAy.d2, yAy.d3);
+            const float2 cen[3] = {xAx.c, xAy.c, xAz.c};
+#pragma unroll
+            for (int f = 4; f < NF; ++f) {
+              pz[f][0] = pz[f][1];
+              pz[f][1] = pz[f][2];
+              pz[f][2] = cen[f - 4];
+            }
+          }
 
           // velocity: grad u, lap u, grad div u
-          const XRow xux = xrow(so + 1 * FIELD), xuy = xrow(so + 2 * FIELD), xuz = xrow(so + 3 * FIELD);
-          const YRow yux = yrow<SX>(so + 1 * FIELD), yuy = yrow<SX>(so + 2 * FIELD), yuz = yrow<SX>(so + 3 * FIELD);
-          d.u[0] = xux.c;
-          d.u[1] = xuy.c;
-          d.u[2] = xuz.c;
-          float2 uz2[3];
+          {
+            const XRow xux = xrow(so + 1 * FIELD), xuy = xrow(so + 2 * FIELD), xuz = xrow(so + 3 * FIELD);
+            const YRow yux = yrow<SX>(so + 1 * FIELD), yuy = yrow<SX>(so + 2 * FIELD), yuz = yrow<SX>(so + 3 * FIELD);
+            d.u[0] = xux.c;
+            d.u[1] = xuy.c;
+            d.u[2] = xuz.c;
+            float2 uz2[3];
 #pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            const XRow &xr = a == 0 ? xux : a == 1 ? xuy : xuz;
-            const YRow &yr = a == 0 ? yux : a == 1 ? yuy : yuz;
-            zrow(1 + a, zd1, zd2, zd3, ze1, ze2, ze3);
-            d.G[a][0] = d1p(c, 0, xr.d1, xr.d2, xr.d3);
-            d.G[a][1] = d1p(c, 1, yr.d1, yr.d2, yr.d3);
-            d.G[a][2] = d1p(c, 2, zd1, zd2, zd3);
-            const float2 xx = d2p(c, 0, xr.c, xr.e1, xr.e2, xr.e3), yy = d2p(c, 1, xr.c, yr.e1, yr.e2, yr.e3),
-                         zz = d2p(c, 2, xr.c, ze1, ze2, ze3);
-            d.lapu[a] = add2(add2(xx, yy), zz);
-            uz2[a] = a == 0 ? xx : a == 1 ? yy : zz;  // the d_a d_a u_a term of grad div u
+            for (int a = 0; a < 3; ++a) {
+              const XRow &xr = a == 0 ? xux : a == 1 ? xuy : xuz;
+              const YRow &yr = a == 0 ? yux : a == 1 ? yuy : yuz;
+              zrow(1 + a, zd1, zd2, zd3, ze1, ze2, ze3);
+              d.G[a][0] = d1p(c, 0, xr.d1, xr.d2, xr.d3);
+              d.G[a][1] = d1p(c, 1, yr.d1, yr.d2, yr.d3);
+              d.G[a][2] = d1p(c, 2, zd1, zd2, zd3);
+              const float2 xx = d2p(c, 0, xr.c, xr.e1, xr.e2, xr.e3), yy = d2p(c, 1, xr.c, yr.e1, yr.e2, yr.e3),
+                           zz = d2p(c, 2, xr.c, ze1, ze2, ze3);
+              d.lapu[a] = add2(add2(xx, yy), zz);
+              uz2[a] = a == 0 ? xx : a == 1 ? yy : zz;  // the d_a d_a u_a term of grad div u
+            }
+            d.gdu[0] = add2(add2(uz2[0], dxy_pair<SX>(so + 2 * FIELD, c)), add2(fxz(3), aX1[0]));
+            d.gdu[1] = add2(add2(dxy_pair<SX>(so + 1 * FIELD, c), uz2[1]), add2(fyz(3), aY1[0]));
+            d.gdu[2] = add2(add2(add2(fxz(1), fyz(2)), aZ1[0]), uz2[2]);
+            pass1(aX1, 1, xuz.d1, xuz.d2, xuz.d3);
+            pass1(aY1, 2, yuz.d1, yuz.d2, yuz.d3);
+            pass2(aZ1, xux.d1, xux.d2, xux.d3, yuy.d1, yuy.d2, yuy.d3);
+#pragma unroll
+            for (int f = 1; f < 4; ++f) {
+              pz[f][0] = pz[f][1];
+              pz[f][1] = pz[f][2];
+              pz[f][2] = d.u[f - 1];
+            }
           }
-          d.gdu[0] = add2(add2(uz2[0], dxy_pair<SX>(so + 2 * FIELD, c)), add2(fxz(3), aX1[0]));
-          d.gdu[1] = add2(add2(dxy_pair<SX>(so + 1 * FIELD, c), uz2[1]), add2(fyz(3), aY1[0]));
-          d.gdu[2] = add2(add2(add2(fxz(1), fyz(2)), aZ1[0]), uz2[2]);
 
           // density: grad ln rho and the upwinding term
-          const XRow xl = xrow(so);
-          const YRow yl = yrow<SX>(so);
-          zrow(0, zd1, zd2, zd3, ze1, ze2, ze3);
-          d.lnr = xl.c;
-          d.g[0] = d1p(c, 0, xl.d1, xl.d2, xl.d3);
-          d.g[1] = d1p(c, 1, yl.d1, yl.d2, yl.d3);
-          d.g[2] = d1p(c, 2, zd1, zd2, zd3);
-          d.up = bc(0.f);
-          if (c.upwind) {
-            // sixth difference (f-3 + f3) - 6 (f-2 + f2) + 15 (f-1 + f1) - 20 f0 per axis
-            const float2 m20 = mul2(bc(-20.f), xl.c);
-            auto d6 = [&](float2 e1, float2 e2, float2 e3) {
-              return add2(fma2(bc(-6.f), e2, e3), fma2(bc(15.f), e1, m20));
-            };
-            auto absu = [&](float2 u) { return pk(fabsf(u.x), fabsf(u.y)); };
-            d.up = fma2(mul2(c.w6(2), absu(d.u[2])), d6(ze1, ze2, ze3),
-                        fma2(mul2(c.w6(1), absu(d.u[1])), d6(yl.e1, yl.e2, yl.e3),
-                             mul2(mul2(c.w6(0), absu(d.u[0])), d6(xl.e1, xl.e2, xl.e3))));
+          {
+            const XRow xl = xrow(so);
+            const YRow yl = yrow<SX>(so);
+            zrow(0, zd1, zd2, zd3, ze1, ze2, ze3);
+            d.lnr = xl.c;
+            d.g[0] = d1p(c, 0, xl.d1, xl.d2, xl.d3);
+            d.g[1] = d1p(c, 1, yl.d1, yl.d2, yl.d3);
+            d.g[2] = d1p(c, 2, zd1, zd2, zd3);
+            d.up = bc(0.f);
+            if (c.upwind) {
+              // sixth difference (f-3 + f3) - 6 (f-2 + f2) + 15 (f-1 + f1) - 20 f0 per axis
+              const float2 m20 = mul2(bc(-20.f), xl.c);
+              auto d6 = [&](float2 e1, float2 e2, float2 e3) {
+                return add2(fma2(bc(-6.f), e2, e3), fma2(bc(15.f), e1, m20));
+              };
+              auto absu = [&](float2 u) { return pk(fabsf(u.x), fabsf(u.y)); };
+              d.up = fma2(mul2(c.w6(2), absu(d.u[2])), d6(ze1, ze2, ze3),
+                          fma2(mul2(c.w6(1), absu(d.u[1])), d6(yl.e1, yl.e2, yl.e3),
+                               mul2(mul2(c.w6(0), absu(d.u[0])), d6(xl.e1, xl.e2, xl.e3))));
+            }
+            pz[0][0] = pz[0][1];
+            pz[0][1] = pz[0][2];
+            pz[0][2] = xl.c;
           }
 
           // forcing of the step at the pair (Eqs. 4-6)
@@ -486,7 +517,9 @@ __global__ void __launch_bounds__(32 * TY, 1)
           rhs_pair(d, c, fr, r);
 
           // RK3-2N update: w <- alpha w + dt RHS, q <- q + beta w
-          const float2 qc[NF] = {xl.c, xux.c, xuy.c, xuz.c, xAx.c, xAy.c, xAz.c};
+          float2 qc[NF];  // centres of the output plane (just pushed into the pencils)
+#pragma unroll
+          for (int f = 0; f < NF; ++f) qc[f] = pz[f][2];
           float2 wv[NF], qn[NF];
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
@@ -525,19 +558,6 @@ __global__ void __launch_bounds__(32 * TY, 1)
             }
           }
 
-          // the output plane leaves the centre: its differences and centres enter the registers
-          pass1(aX1, 1, xuz.d1, xuz.d2, xuz.d3);
-          pass1(aY1, 2, yuz.d1, yuz.d2, yuz.d3);
-          pass2(aZ1, xux.d1, xux.d2, xux.d3, yuy.d1, yuy.d2, yuy.d3);
-          pass1(aX2, 1, xAz.d1, xAz.d2, xAz.d3);
-          pass1(aY2, 2, yAz.d1, yAz.d2, yAz.d3);
-          pass2(aZ2, xAx.d1, xAx.d2, xAx.d3, yAy.d1, yAy.d2, yAy.d3);
-#pragma unroll
-          for (int f = 0; f < NF; ++f) {
-            pz[f][0] = pz[f][1];
-            pz[f][1] = pz[f][2];
-            pz[f][2] = qc[f];
-          }
         }
       }
       if (outp) {

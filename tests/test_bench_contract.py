@@ -48,7 +48,7 @@ def test_ncu_records_are_used_only_for_the_sources_they_were_taken_from():
     sys.path.insert(0, ROOT)
     import bench
     h = bench.kernel_source_hash()
-    for name, get in (("substep_traffic.json", lambda: bench.ncu_traffic(256, "f32")),
+    for name, get in (("substep_traffic.json", lambda: bench.ncu_traffic(512, "f32")),
                       ("substep_flops.json", lambda: bench.ncu_flops("f32"))):
         with open(os.path.join(ROOT, "profiles", name)) as f:
             rec = json.load(f)
