@@ -1,7 +1,8 @@
 // Tile variants of the paired-point substep kernel (kernels_x2.cu), FP32:
 // id -> (TY rows of 64 points, TMA stages, planes between CTA barriers).
 // Each thread computes two neighbouring x-points; a CTA of 32 x TY threads
-// covers a 64 x TY column.  Prefetch distance NS - 3 - BAR >= 1 planes.
+// covers a 64 x TY column.  Prefetch distance NS - 3 - BAR >= 1 planes
+// (tiles 23, 24: two and three planes ahead).
 #pragma once
 #define MHD_X2_VARIANTS(X) \
   X(17, 8, 6, 2)           \
@@ -9,6 +10,8 @@
   X(19, 4, 5, 1)           \
   X(20, 6, 6, 2)           \
   X(21, 8, 5, 1)           \
-  X(22, 8, 8, 4)
+  X(22, 8, 8, 4)           \
+  X(23, 8, 8, 3)           \
+  X(24, 8, 8, 2)
 #define MHD_X2_FIRST 17
-#define MHD_X2_LAST 22
+#define MHD_X2_LAST 24

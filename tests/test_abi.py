@@ -68,9 +68,9 @@ def test_workspace_bytes_scale_with_grid(B):
     assert 1.9 < dbl / big < 2.01 and big > small
 
 
-@pytest.mark.parametrize("dtype,tiles", [(0, range(0, 23)), (1, range(0, 5))])
+@pytest.mark.parametrize("dtype,tiles", [(0, range(0, 25)), (1, range(0, 5))])
 def test_every_tile_variant_is_accepted(B, dtype, tiles):
-    """FP32 TMA tiles 1-22 (shapes, stage counts, barrier spacings, packed
+    """FP32 TMA tiles 1-24 (shapes, stage counts, barrier spacings, packed
     pairs, paired points) and FP64 tiles 1-4, and 0 for the default, are
     valid parameters."""
     for t in tiles:
@@ -82,7 +82,7 @@ def test_every_tile_variant_is_accepted(B, dtype, tiles):
     (dict(f0=0.1, kmin=0.0), "shell"), (dict(f0=0.1, kmin=0.2, kmax=0.5), "no integer"),
     (dict(f0=0.1, sigma=1.5), "sigma"), (dict(dtype=7), "dtype"), (dict(forcing_mode=3), "forcing_mode"), (dict(upwind=2), "upwind"),
     (dict(cfl=0.0), "cfl"), (dict(kernel=99), "kernel"),
-    (dict(kernel=2, tile=23), "tile"), (dict(kernel=2, tile=6, dtype=1), "tile"), (dict(kernel=1, tile=3), "tile"),
+    (dict(kernel=2, tile=25), "tile"), (dict(kernel=2, tile=6, dtype=1), "tile"), (dict(kernel=1, tile=3), "tile"),
 ])
 def test_invalid_parameters_are_rejected(B, bad, msg):
     with pytest.raises(B.MhdError) as e:

@@ -52,7 +52,7 @@ SHAPES = [(32, 32, 32), (37, 23, 11), (40, 8, 20), (12, 9, 1), (16, 1, 1), (1, 1
 
 
 KERNELS = [(2, 0), (1, 0)]  # (kernel, tile): TMA default tile, plane ring
-TMA_TILES = [(2, t) for t in range(1, 23)]
+TMA_TILES = [(2, t) for t in range(1, 25)]
 
 
 @pytest.mark.parametrize("kernel,tile", KERNELS)
