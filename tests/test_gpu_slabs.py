@@ -20,6 +20,8 @@ CASES = [
     ((20, 16, 12), 3, True, dict(f0=0.05, sigma=1.0, seed=4)),                  # 4-plane slabs: no inner split
     ((28, 24, 30), 2, True, dict(lx=4.0, ly=3.0, lz=3.5, f0=0.03, seed=5, forcing_mode=1)),
     ((16, 16, 16), 1, True, dict(f0=0.02, seed=6, dt_fixed=2e-3)),              # one slab: self-exchange
+    ((70, 20, 24), 2, True, dict(f0=0.05, sigma=1.0, seed=7, kernel=2, tile=18)),  # paired-point kernel
+    ((128, 16, 27), 3, False, dict(f0=0.05, sigma=0.3, seed=8, kernel=2, tile=22, upwind=1)),
 ]
 
 
@@ -32,6 +34,8 @@ def _state(shape, seed):
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("shape,nslabs,overlap,extra", CASES)
 def test_slabs_equal_the_undecomposed_run(shape, nslabs, overlap, extra, dtype):
+    if dtype == "f64" and extra.get("tile", 0) > 4:
+        pytest.skip("FP32 tile")
     from paper_2012_08758_b300 import binding as B
     from paper_2012_08758_b300.run import Run
     from paper_2012_08758_b300.slabs import Slabs, slab_extents
