@@ -31,16 +31,34 @@ def stale() -> bool:
     return any(os.path.getmtime(f) > t for f in _inputs())
 
 
+COMPILE_FLAGS = [f for f in NVCC_FLAGS if f != "-shared"]
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every .cu under csrc/ into one shared library (atomic replace)."""
+    """Compile every .cu under csrc/ (one nvcc per file, in parallel) and link
+    them into one shared library (atomic replace)."""
     if not force and not stale():
         return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = ["nvcc", *NVCC_FLAGS, "-I", INCLUDE, "-o", tmp, *sources(), *LIBS]
-    if verbose:
-        print(" ".join(cmd))
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+    from concurrent.futures import ThreadPoolExecutor
+    tag = f".tmp{os.getpid()}"
+    objs = [os.path.join(CSRC, os.path.basename(src)[:-3] + tag + ".o") for src in sources()]
+    cmds = [["nvcc", *COMPILE_FLAGS, "-I", INCLUDE, "-c", src, "-o", obj] for src, obj in zip(sources(), objs)]
+    link = ["nvcc", "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", LIB + tag, *objs, *LIBS]
+    try:
+        with ThreadPoolExecutor(max_workers=min(len(cmds), os.cpu_count() or 1)) as ex:
+            for cmd in cmds:
+                if verbose:
+                    print(" ".join(cmd))
+            for f in [ex.submit(subprocess.check_call, cmd) for cmd in cmds]:
+                f.result()
+        if verbose:
+            print(" ".join(link))
+        subprocess.check_call(link)
+        os.replace(LIB + tag, LIB)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 

@@ -209,9 +209,13 @@ __device__ __forceinline__ float2 dxy_pair(const float *b, const PairCoefs<ISO> 
 
 }  // namespace
 
-template <int TY, int NS, int BAR, bool ISO>
+// SUB: the RK substep (0, 1, 2), a compile-time constant so that each
+// instantiation carries only its own w traffic (none read at 0, none written
+// at 2) and its own RK coefficients.
+template <int TY, int NS, int BAR, bool ISO, int SUB>
 __global__ void __launch_bounds__(32 * TY, 1)
-    k_substep_x2(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles, int ntiles, int substep) {
+    k_substep_x2(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles, int ntiles) {
+  constexpr int substep = SUB;
   using SH = TmaShape<float, TY, 64>;
   constexpr int SX = SH::SX, FIELD = SH::FIELD;
   // Prefetch distance: the stage of plane q is last read when q is the output
@@ -339,8 +343,6 @@ __global__ void __launch_bounds__(32 * TY, 1)
       const int o = p - RAD;       // centre plane (lead index), interior plane z0 + o - 3
       const bool outp = o >= RAD;  // an interior plane of this tile: computed and stored
       float2 wc[NF];
-#pragma unroll
-      for (int f = 0; f < NF; ++f) wc[f] = bc(0.f);
       if (need_w && outp) {
         const float *wp = w + cidx;
 #pragma unroll
@@ -524,7 +526,7 @@ __global__ void __launch_bounds__(32 * TY, 1)
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
             wv[f] = mul2(dt, r[f]);
-            if (substep > 0) wv[f] = fma2(alpha, wc[f], wv[f]);
+            if constexpr (SUB > 0) wv[f] = fma2(alpha, wc[f], wv[f]);
             qn[f] = fma2(beta, wv[f], qc[f]);
           }
           if (force_at_end)
@@ -538,7 +540,7 @@ __global__ void __launch_bounds__(32 * TY, 1)
               float *wp = w + cidx, *qp = qout + cidx;
 #pragma unroll
               for (int f = 0; f < NF; ++f, wp += fs, qp += fs) {
-                if (substep < 2) __stcs(reinterpret_cast<float2 *>(wp), wv[f]);
+                if constexpr (SUB < 2) __stcs(reinterpret_cast<float2 *>(wp), wv[f]);
                 __stcs(reinterpret_cast<float2 *>(qp), qn[f]);
               }
             } else {
@@ -547,7 +549,7 @@ __global__ void __launch_bounds__(32 * TY, 1)
               for (int f = 0; f < NF; ++f) {
                 q0[f] = qn[f].x;
                 q1[f] = qn[f].y;
-                if (substep < 2) {
+                if constexpr (SUB < 2) {
                   __stcs(w + cidx + f * fs, wv[f].x);
                   if (act1) __stcs(w + cidx + 1 + f * fs, wv[f].y);
                 }
@@ -621,43 +623,59 @@ int x2_rows(int tile) {
 }
 
 int x2_prepare(int tile) {
-#define X(ID, TY, NS, BR)                                                                                   \
-  if (tile == ID) {                                                                                         \
-    int e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, true>,                                        \
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, x2_smem_bytes<TY, NS>()); \
-    if (!e)                                                                                                 \
-      e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, false>,                                         \
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, x2_smem_bytes<TY, NS>());   \
-    return e;                                                                                               \
+  int e = (int)cudaErrorInvalidValue;
+#define X(ID, TY, NS, BR)                                                                                  \
+  if (tile == ID) {                                                                                        \
+    const int sm = x2_smem_bytes<TY, NS>();                                                                \
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;                               \
+    e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, true, 0>, a, sm);                               \
+    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, true, 1>, a, sm);                       \
+    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, true, 2>, a, sm);                       \
+    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, false, 0>, a, sm);                      \
+    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, false, 1>, a, sm);                      \
+    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, false, 2>, a, sm);                      \
   }
   MHD_X2_VARIANTS(X)
 #undef X
-  return (int)cudaErrorInvalidValue;
+  return e;
 }
 
 int x2_occupancy(int tile, int *bps) {
-#define X(ID, TY, NS, BR)                                                                                  \
-  if (tile == ID)                                                                                          \
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_substep_x2<TY, NS, BR, true>, 32 * TY, \
+#define X(ID, TY, NS, BR)                                                                                      \
+  if (tile == ID)                                                                                              \
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_substep_x2<TY, NS, BR, true, 1>, 32 * TY, \
                                                               x2_smem_bytes<TY, NS>());
   MHD_X2_VARIANTS(X)
 #undef X
   return (int)cudaErrorInvalidValue;
 }
 
+namespace {
+template <int TY, int NS, int BR, bool ISO>
+void x2_go(const RunDesc *runs, const Tile *tiles, int ntiles, int substep, int grid, cudaStream_t s) {
+  const dim3 block(32, TY);
+  const int sm = x2_smem_bytes<TY, NS>();
+  if (substep == 0)
+    k_substep_x2<TY, NS, BR, ISO, 0><<<grid, block, sm, s>>>(runs, tiles, ntiles);
+  else if (substep == 1)
+    k_substep_x2<TY, NS, BR, ISO, 1><<<grid, block, sm, s>>>(runs, tiles, ntiles);
+  else
+    k_substep_x2<TY, NS, BR, ISO, 2><<<grid, block, sm, s>>>(runs, tiles, ntiles);
+}
+}  // namespace
+
 int x2_launch(int tile, const RunDesc *runs, const Tile *tiles, int ntiles, int substep, int grid, int iso,
               cudaStream_t s) {
   if (grid <= 0 || grid > ntiles) grid = ntiles;
   if (grid == 0) return 0;
-#define X(ID, TY, NS, BR)                                                                                       \
-  if (tile == ID) {                                                                                             \
-    if (iso)                                                                                                    \
-      k_substep_x2<TY, NS, BR, true><<<grid, dim3(32, TY), x2_smem_bytes<TY, NS>(), s>>>(runs, tiles, ntiles,   \
-                                                                                          substep);             \
-    else                                                                                                        \
-      k_substep_x2<TY, NS, BR, false><<<grid, dim3(32, TY), x2_smem_bytes<TY, NS>(), s>>>(runs, tiles, ntiles,  \
-                                                                                           substep);            \
-    return (int)cudaGetLastError();                                                                             \
+  if (substep < 0 || substep > 2) return (int)cudaErrorInvalidValue;
+#define X(ID, TY, NS, BR)                                                  \
+  if (tile == ID) {                                                        \
+    if (iso)                                                               \
+      x2_go<TY, NS, BR, true>(runs, tiles, ntiles, substep, grid, s);      \
+    else                                                                   \
+      x2_go<TY, NS, BR, false>(runs, tiles, ntiles, substep, grid, s);     \
+    return (int)cudaGetLastError();                                        \
   }
   MHD_X2_VARIANTS(X)
 #undef X
