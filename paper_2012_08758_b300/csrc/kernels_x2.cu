@@ -45,6 +45,14 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+// Streaming 64-bit global load as a volatile asm statement: the w samples of
+// the output plane keep their place before the wait for the lead plane, so
+// that the latency of the read overlaps the plane's stencil work.
+__device__ __forceinline__ float2 ldcs2_pinned(const float *p) {
+  float2 v;
+  asm volatile("ld.global.cs.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p) : "memory");
+  return v;
+}
 
 // Stencil weights of the run as packed pairs (both lanes equal).
 template <bool ISO>
@@ -255,7 +263,14 @@ __global__ void __launch_bounds__(32 * TY, 1)
     const int x = tile.x0 + 2 * tx, y = tile.y0 + ty;
     const bool act0 = x < nx && y < ny, act1 = x + 1 < nx && y < ny;
     const bool yedge = y < RAD || y >= ny - RAD;
-    const bool edge0 = yedge || x < RAD || x >= nx - RAD, edge1 = yedge || x + 1 < RAD || x + 1 >= nx - RAD;
+    const bool xn0 = x < RAD || x >= nx - RAD, xn1 = x + 1 < RAD || x + 1 >= nx - RAD;
+    const bool edge0 = yedge || xn0, edge1 = yedge || xn1;
+    // Every point within RAD of a face has exactly one image per non-empty
+    // subset of its non-zero shifts (x +- nx, y +- ny, z +- nz) when each
+    // periodic axis has at least 2 RAD + 1 points: the y and z shifts are
+    // common to the pair, so those images are stored as pairs too, and only
+    // the x images are stored per point.
+    const bool shift_images = nx >= 2 * RAD + 1 && ny >= 2 * RAD + 1 && (nz >= 2 * RAD + 1 || !zper);
     const int npl = (tile.z1 - tile.z0) + 2 * RAD;  // lead planes z0-3 .. z1+2
 
     const bool forcing = K.forcing != 0;
@@ -346,7 +361,7 @@ __global__ void __launch_bounds__(32 * TY, 1)
       if (need_w && outp) {
         const float *wp = w + cidx;
 #pragma unroll
-        for (int f = 0; f < NF; ++f, wp += fs) wc[f] = __ldcs(reinterpret_cast<const float2 *>(wp));
+        for (int f = 0; f < NF; ++f, wp += fs) wc[f] = ldcs2_pinned(wp);
       }
       const bool ok = mbar_wait(&bars[slot], phase);
       if (o >= 0 && ok) {
@@ -542,6 +557,41 @@ __global__ void __launch_bounds__(32 * TY, 1)
               for (int f = 0; f < NF; ++f, wp += fs, qp += fs) {
                 if constexpr (SUB < 2) __stcs(reinterpret_cast<float2 *>(wp), wv[f]);
                 __stcs(reinterpret_cast<float2 *>(qp), qn[f]);
+              }
+            } else if (act1 && shift_images) {
+              float *wp = w + cidx, *qp = qout + cidx;
+#pragma unroll
+              for (int f = 0; f < NF; ++f, wp += fs, qp += fs) {
+                if constexpr (SUB < 2) __stcs(reinterpret_cast<float2 *>(wp), wv[f]);
+                __stcs(reinterpret_cast<float2 *>(qp), qn[f]);
+              }
+              {
+                // images: the y / z shifts of the pair, then the x images per point
+                const long long dy = !yedge ? 0 : (y < RAD ? (long long)ny * px : -(long long)ny * px);
+                const long long dz = !(zper && zn) ? 0 : (z < RAD ? (long long)nz * wplane : -(long long)nz * wplane);
+                auto put2 = [&](long long o) {
+                  float *p = qout + o;
+#pragma unroll
+                  for (int f = 0; f < NF; ++f, p += fs) __stcs(reinterpret_cast<float2 *>(p), qn[f]);
+                };
+                auto put1 = [&](long long o, int e) {
+                  float *p = qout + o;
+#pragma unroll
+                  for (int f = 0; f < NF; ++f, p += fs) __stcs(p, e == 0 ? qn[f].x : qn[f].y);
+                };
+                if (dy != 0) put2(cidx + dy);
+                if (dz != 0) put2(cidx + dz);
+                if (dy != 0 && dz != 0) put2(cidx + dy + dz);
+#pragma unroll
+                for (int e = 0; e < 2; ++e)
+                  if (e == 0 ? xn0 : xn1) {
+                    const int xe = x + e;
+                    const long long b = cidx + e + (xe < RAD ? nx : -nx);
+                    put1(b, e);
+                    if (dy != 0) put1(b + dy, e);
+                    if (dz != 0) put1(b + dz, e);
+                    if (dy != 0 && dz != 0) put1(b + dy + dz, e);
+                  }
               }
             } else {
               float q0[NF], q1[NF];
