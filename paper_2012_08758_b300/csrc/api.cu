@@ -130,16 +130,27 @@ struct SubCol {
 
 // Columns of planes zb .. zb + nz - 1 of one run (zb > 0: the inner or outer
 // z-range of a slab of a decomposed domain).
+//
+// The paired-point kernel (64-wide tiles) has its own face weights, fitted
+// the same way at 384^3 - 1024^2 x 256 (x face 1.15-1.25 by substep, y face
+// 1.02-1.05), and its columns are listed in bands of two tile rows -- x
+// across the band, the band's two rows adjacent -- which spreads the x-face
+// columns of the whole-column waves more evenly over the CTAs than a plain
+// row-major list (512^3: 2.3% shorter substeps with both changes).
 void add_columns(std::vector<SubCol> *cols, int run, int nx, int ny, int nz, int tw, int th, int zb = 0) {
-  for (int y0 = 0; y0 < ny; y0 += th)
-    for (int x0 = 0; x0 < nx; x0 += tw) {
-      const double act = (double)std::min(tw, nx - x0) * std::min(th, ny - y0) / ((double)tw * th);
-      const bool xface = x0 < RAD || x0 + tw > nx - RAD, yface = y0 < RAD || y0 + th > ny - RAD;
-      double w = act >= 1.0 ? 1.0 : 0.565 + 0.435 * act;
-      if (xface) w *= 1.10;
-      if (yface) w *= 1.05;
-      cols->push_back(SubCol{run, x0, y0, nz, w, zb});
-    }
+  const bool paired = tw == 64;
+  const double wx = paired ? 1.18 : 1.10, wy = paired ? 1.03 : 1.05;
+  const int band = paired ? 2 * th : th;
+  for (int yb = 0; yb < ny; yb += band)
+    for (int x0 = 0; x0 < nx; x0 += tw)
+      for (int y0 = yb; y0 < std::min(ny, yb + band); y0 += th) {
+        const double act = (double)std::min(tw, nx - x0) * std::min(th, ny - y0) / ((double)tw * th);
+        const bool xface = x0 < RAD || x0 + tw > nx - RAD, yface = y0 < RAD || y0 + th > ny - RAD;
+        double w = act >= 1.0 ? 1.0 : 0.565 + 0.435 * act;
+        if (xface) w *= wx;
+        if (yface) w *= wy;
+        cols->push_back(SubCol{run, x0, y0, nz, w, zb});
+      }
 }
 
 std::vector<Tile> split_columns(const std::vector<SubCol> &cols, int G, int *grid_out) {
