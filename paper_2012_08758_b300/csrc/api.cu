@@ -250,9 +250,10 @@ int validate(const mhd_params *p, std::string *why) {
 
 // AUTO resolves to the TMA kernel; tile 0 to the fastest variant measured on
 // B300 for the grid: FP32 grids with at least LARGE_COLUMNS columns of 64 x 8
-// points (e.g. 512^2 and up) take the paired-point kernel with 7 stages and a
-// CTA barrier every third plane (tile 18; 512^3: 8.2e9 against 7.6e9
-// cell-updates/s), smaller FP32 grids the 32 x 12 scalar kernel with 9 stages
+// points (e.g. 512^2 and up) take the warp-specialised paired-point kernel
+// with 7 stages (tile 25; 512^3: 9.28e9 against 8.66e9 cell-updates/s for the
+// barrier-synchronised tile 18 and 7.6e9 for the scalar kernel), smaller
+// FP32 grids the 32 x 12 scalar kernel with 9 stages
 // and a barrier every fifth plane (tile 13; 256^3: 7.5e9 against 6.9e9), FP64
 // the 32 x 8 tile with 6 stages.  Runs of one batch need the same resolved
 // tile, so a batch that mixes the two classes must name a tile explicitly.
@@ -262,7 +263,7 @@ mhd_params resolved(const mhd_params *p) {
   if (r.kernel == MHD_KERNEL_AUTO) r.kernel = MHD_KERNEL_TMA;
   if (r.kernel == MHD_KERNEL_TMA && r.tile == 0) {
     const long long cols64 = (long long)((r.nx + 63) / 64) * ((r.ny + 7) / 8);
-    r.tile = r.dtype == MHD_F32 ? (cols64 >= LARGE_COLUMNS ? 18 : 13) : 3;
+    r.tile = r.dtype == MHD_F32 ? (cols64 >= LARGE_COLUMNS ? 25 : 13) : 3;
   }
   return r;
 }

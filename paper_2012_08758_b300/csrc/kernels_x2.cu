@@ -217,11 +217,62 @@ __device__ __forceinline__ float2 dxy_pair(const float *b, const PairCoefs<ISO> 
 
 }  // namespace
 
+// Warp-specialised variants (WS): a fifth warpgroup of the CTA only issues
+// the TMA copies; each stage has a "full" mbarrier (the copy's bytes) and an
+// "empty" one (one arrival per compute warp once the stage's plane has left
+// its last use, three planes after it led), so the compute warps never meet
+// at a CTA barrier.  The producer warpgroup gives its registers to the
+// compute warpgroups (setmaxnreg): at launch 32 x (TY + 4) threads hold
+// X2_WS_LAUNCH_REGS each; 4 x 32 producer threads keep X2_WS_PRODUCER_REGS
+// and the TY warps of compute threads may use X2_WS_COMPUTE_REGS, with
+// (TY + 4) * 32 * LAUNCH = TY * 32 * COMPUTE + 128 * PRODUCER for TY = 8.
+constexpr int X2_WS_LAUNCH_REGS = 168, X2_WS_PRODUCER_REGS = 40, X2_WS_COMPUTE_REGS = 232;
+static_assert(12 * 32 * X2_WS_LAUNCH_REGS == 8 * 32 * X2_WS_COMPUTE_REGS + 4 * 32 * X2_WS_PRODUCER_REGS,
+              "register split of the warp-specialised variants");
+
+namespace {
+// The producer: every plane of every tile of this CTA, in the compute warps'
+// order, into stage g mod NS once the plane g - NS has been released.  On a
+// wait that gives up it records status bit 1 and raises the CTA's abort flag;
+// before returning it waits (bounded) for every copy it issued.
+template <int TY, int NS, int SUB>
+__device__ __forceinline__ void x2_produce(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles,
+                                           int ntiles, unsigned char *smem, uint64_t *full, uint64_t *empty,
+                                           volatile int *abort) {
+  using SH = TmaShape<float, TY, 64>;
+  unsigned long long g = 0;
+  int fail_run = -1;
+  for (int t = blockIdx.x; t < ntiles && fail_run < 0; t += gridDim.x) {
+    const Tile tile = tiles[t];
+    if (tile.z1 <= tile.z0) continue;
+    const RunDesc &R = runs[tile.run];
+    const CUtensorMap *map = &R.tmap[(R.coeffs->parity + SUB) & 1];
+    const int npl = (tile.z1 - tile.z0) + 2 * RAD;
+    for (int p = 0; p < npl; ++p, ++g) {
+      const int sl = (int)(g % NS);
+      if ((g >= NS && !mbar_wait(&empty[sl], (uint32_t)(((g / NS) - 1) & 1ull))) || *abort) {
+        fail_run = tile.run;
+        break;
+      }
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&full[sl], (uint32_t)(NF * SH::FIELD * sizeof(float)));
+      tma_load_4d(smem + sl * SH::STAGE_BYTES, map, &full[sl], tile.x0, tile.y0, tile.z0 + p, 0);
+    }
+  }
+  if (fail_run >= 0) {
+    atomicOr(&runs[fail_run].clock->status, 2);
+    *abort = 1;
+  }
+  for (unsigned long long q = g > (unsigned long long)NS ? g - NS : 0; q < g; ++q)
+    mbar_wait(&full[q % NS], (uint32_t)((q / NS) & 1ull));
+}
+}  // namespace
+
 // SUB: the RK substep (0, 1, 2), a compile-time constant so that each
 // instantiation carries only its own w traffic (none read at 0, none written
 // at 2) and its own RK coefficients.
-template <int TY, int NS, int BAR, bool ISO, int SUB>
-__global__ void __launch_bounds__(32 * TY, 1)
+template <int TY, int NS, int BAR, bool ISO, int SUB, bool WS>
+__global__ void __launch_bounds__(32 * TY + (WS ? 128 : 0), 1)
     k_substep_x2(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles, int ntiles) {
   constexpr int substep = SUB;
   using SH = TmaShape<float, TY, 64>;
@@ -229,16 +280,29 @@ __global__ void __launch_bounds__(32 * TY, 1)
   // Prefetch distance: the stage of plane q is last read when q is the output
   // plane (lead plane q+3) and refilled by plane q+NS, issued P planes ahead;
   // warps drift apart by up to BAR planes between CTA barriers.
-  constexpr int P = NS - 3 - BAR;
-  static_assert(P >= 1, "need at least one plane of prefetch");
+  constexpr int P = WS ? NS : NS - 3 - BAR;  // WS: the producer runs ahead by itself
+  static_assert(WS ? NS >= 5 : P >= 1, "need at least one plane of prefetch");
+  static_assert(!WS || TY == 8, "the register split of the warp-specialised variants is for 8 compute warps");
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * SH::STAGE_BYTES);
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  __shared__ int ws_abort;
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+    if constexpr (WS)
+      for (int s = 0; s < NS; ++s) mbar_init(&bars[NS + s], TY);
+    if constexpr (WS) ws_abort = 0;
     mbar_fence_init();
   }
   __syncthreads();
+  if constexpr (WS) {
+    if (ty >= TY) {
+      asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(X2_WS_PRODUCER_REGS));
+      if (ty == TY && tx == 0) x2_produce<TY, NS, SUB>(runs, tiles, ntiles, smem, bars, bars + NS, &ws_abort);
+      return;
+    }
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(X2_WS_COMPUTE_REGS));
+  }
 
   unsigned long long G = 0;  // planes issued by this CTA before the current tile
   bool failed = false, waits_ok = true;
@@ -301,7 +365,7 @@ __global__ void __launch_bounds__(32 * TY, 1)
       mbar_arrive_expect_tx(bar, (uint32_t)(NF * FIELD * sizeof(float)));
       tma_load_4d(smem + sl * SH::STAGE_BYTES, map, bar, tile.x0, tile.y0, tile.z0 + p, 0);
     };
-    if (tid == 0) {
+    if (!WS && tid == 0) {
       fence_proxy_async_smem();
       const int first = npl < P ? npl : P;
       for (int p = 0; p < first; ++p) issue(p, (slot + p) % NS);
@@ -348,7 +412,7 @@ __global__ void __launch_bounds__(32 * TY, 1)
     auto ydiff = [&](const float *b, int s) { return sub2(ld2(b + s * SX), ld2(b - s * SX)); };
 
     for (int p = 0; p < npl && !failed; ++p) {
-      if (tid == 0 && p + P < npl) {
+      if (!WS && tid == 0 && p + P < npl) {
         fence_proxy_async_smem();
         int sl = slot + P;
         if (sl >= NS) sl -= NS;
@@ -623,7 +687,24 @@ __global__ void __launch_bounds__(32 * TY, 1)
         slot = 0;
         phase ^= 1u;
       }
-      if constexpr (BAR == 1) {
+      if constexpr (WS) {
+        // release the stage of plane p - 3 after its last use; a wait that
+        // gave up stops every compute warp of the CTA at its next plane
+        if (p >= RAD) {
+          int rs = slot - 1 - RAD;  // slot was advanced past plane p just above
+          if (rs < 0) rs += NS;
+          __syncwarp();
+          if (tx == 0) mbar_arrive(&bars[NS + rs]);
+        }
+        if (!ok) {
+          ws_abort = 1;
+          atomicOr(&R.clock->status, 2);
+        }
+        if (*(volatile int *)&ws_abort) {
+          failed = true;
+          break;
+        }
+      } else if constexpr (BAR == 1) {
         if (__syncthreads_or(!ok)) {
           failed = true;
           fail_run = tile.run;
@@ -643,10 +724,19 @@ __global__ void __launch_bounds__(32 * TY, 1)
         }
       }
     }
+    if constexpr (WS) {
+      if (!failed) {
+        // the last three planes of the tile had no later plane to release them
+        for (int q = npl - RAD; q < npl; ++q) {
+          __syncwarp();
+          if (tx == 0) mbar_arrive(&bars[NS + (int)((G + q) % NS)]);
+        }
+      }
+    }
     if (!failed) G += npl;
   }
 
-  if (failed && tid == 0) {
+  if (!WS && failed && tid == 0) {
     // record the time-out, then wait (bounded) for the copies still in flight
     atomicOr(&runs[fail_run].clock->status, 2);
     for (int p = fail_p; p < issued_hi; ++p) {
@@ -657,15 +747,15 @@ __global__ void __launch_bounds__(32 * TY, 1)
 }
 
 namespace {
-template <int TY, int NS>
+template <int TY, int NS, bool WS>
 constexpr int x2_smem_bytes() {
-  return NS * TmaShape<float, TY, 64>::STAGE_BYTES + NS * 8;
+  return NS * TmaShape<float, TY, 64>::STAGE_BYTES + (WS ? 2 : 1) * NS * 8;
 }
 }  // namespace
 
 // Tile rows of a paired-point variant (0 if `tile` is not one).
 int x2_rows(int tile) {
-#define X(ID, TY, NS, BR) \
+#define X(ID, TY, NS, BR, WS) \
   if (tile == ID) return TY;
   MHD_X2_VARIANTS(X)
 #undef X
@@ -674,16 +764,16 @@ int x2_rows(int tile) {
 
 int x2_prepare(int tile) {
   int e = (int)cudaErrorInvalidValue;
-#define X(ID, TY, NS, BR)                                                                                  \
+#define X(ID, TY, NS, BR, WS)                                                                              \
   if (tile == ID) {                                                                                        \
-    const int sm = x2_smem_bytes<TY, NS>();                                                                \
+    const int sm = x2_smem_bytes<TY, NS, WS>();                                                            \
     const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;                               \
-    e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, true, 0>, a, sm);                               \
-    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, true, 1>, a, sm);                       \
-    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, true, 2>, a, sm);                       \
-    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, false, 0>, a, sm);                      \
-    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, false, 1>, a, sm);                      \
-    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, false, 2>, a, sm);                      \
+    e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, true, 0, WS>, a, sm);                           \
+    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, true, 1, WS>, a, sm);                   \
+    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, true, 2, WS>, a, sm);                   \
+    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, false, 0, WS>, a, sm);                  \
+    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, false, 1, WS>, a, sm);                  \
+    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, false, 2, WS>, a, sm);                  \
   }
   MHD_X2_VARIANTS(X)
 #undef X
@@ -691,26 +781,27 @@ int x2_prepare(int tile) {
 }
 
 int x2_occupancy(int tile, int *bps) {
-#define X(ID, TY, NS, BR)                                                                                      \
-  if (tile == ID)                                                                                              \
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_substep_x2<TY, NS, BR, true, 1>, 32 * TY, \
-                                                              x2_smem_bytes<TY, NS>());
+#define X(ID, TY, NS, BR, WS)                                                                                \
+  if (tile == ID)                                                                                            \
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_substep_x2<TY, NS, BR, true, 1, WS>,    \
+                                                              32 * TY + (WS ? 128 : 0),                      \
+                                                              x2_smem_bytes<TY, NS, WS>());
   MHD_X2_VARIANTS(X)
 #undef X
   return (int)cudaErrorInvalidValue;
 }
 
 namespace {
-template <int TY, int NS, int BR, bool ISO>
+template <int TY, int NS, int BR, bool ISO, bool WS>
 void x2_go(const RunDesc *runs, const Tile *tiles, int ntiles, int substep, int grid, cudaStream_t s) {
-  const dim3 block(32, TY);
-  const int sm = x2_smem_bytes<TY, NS>();
+  const dim3 block(32, TY + (WS ? 4 : 0));
+  const int sm = x2_smem_bytes<TY, NS, WS>();
   if (substep == 0)
-    k_substep_x2<TY, NS, BR, ISO, 0><<<grid, block, sm, s>>>(runs, tiles, ntiles);
+    k_substep_x2<TY, NS, BR, ISO, 0, WS><<<grid, block, sm, s>>>(runs, tiles, ntiles);
   else if (substep == 1)
-    k_substep_x2<TY, NS, BR, ISO, 1><<<grid, block, sm, s>>>(runs, tiles, ntiles);
+    k_substep_x2<TY, NS, BR, ISO, 1, WS><<<grid, block, sm, s>>>(runs, tiles, ntiles);
   else
-    k_substep_x2<TY, NS, BR, ISO, 2><<<grid, block, sm, s>>>(runs, tiles, ntiles);
+    k_substep_x2<TY, NS, BR, ISO, 2, WS><<<grid, block, sm, s>>>(runs, tiles, ntiles);
 }
 }  // namespace
 
@@ -719,12 +810,12 @@ int x2_launch(int tile, const RunDesc *runs, const Tile *tiles, int ntiles, int 
   if (grid <= 0 || grid > ntiles) grid = ntiles;
   if (grid == 0) return 0;
   if (substep < 0 || substep > 2) return (int)cudaErrorInvalidValue;
-#define X(ID, TY, NS, BR)                                                  \
+#define X(ID, TY, NS, BR, WS)                                              \
   if (tile == ID) {                                                        \
     if (iso)                                                               \
-      x2_go<TY, NS, BR, true>(runs, tiles, ntiles, substep, grid, s);      \
+      x2_go<TY, NS, BR, true, WS>(runs, tiles, ntiles, substep, grid, s);  \
     else                                                                   \
-      x2_go<TY, NS, BR, false>(runs, tiles, ntiles, substep, grid, s);     \
+      x2_go<TY, NS, BR, false, WS>(runs, tiles, ntiles, substep, grid, s); \
     return (int)cudaGetLastError();                                        \
   }
   MHD_X2_VARIANTS(X)

@@ -1,17 +1,22 @@
 // Tile variants of the paired-point substep kernel (kernels_x2.cu), FP32:
-// id -> (TY rows of 64 points, TMA stages, planes between CTA barriers).
-// Each thread computes two neighbouring x-points; a CTA of 32 x TY threads
-// covers a 64 x TY column.  Prefetch distance NS - 3 - BAR >= 1 planes
-// (tiles 23, 24: two and three planes ahead).
+// id -> (TY rows of 64 points, TMA stages, planes between CTA barriers,
+// warp-specialised).  Each thread computes two neighbouring x-points; a CTA
+// of 32 x TY compute threads covers a 64 x TY column.  Prefetch distance
+// NS - 3 - BAR >= 1 planes (tiles 23, 24: two and three planes ahead).
+// Tiles 25-27: a producer warpgroup issues the copies against per-stage
+// "empty" mbarriers, no CTA barrier; up to NS - 4 planes ahead.
 #pragma once
 #define MHD_X2_VARIANTS(X) \
-  X(17, 8, 6, 2)           \
-  X(18, 8, 7, 3)           \
-  X(19, 4, 5, 1)           \
-  X(20, 6, 6, 2)           \
-  X(21, 8, 5, 1)           \
-  X(22, 8, 8, 4)           \
-  X(23, 8, 8, 3)           \
-  X(24, 8, 8, 2)
+  X(17, 8, 6, 2, 0)           \
+  X(18, 8, 7, 3, 0)           \
+  X(19, 4, 5, 1, 0)           \
+  X(20, 6, 6, 2, 0)           \
+  X(21, 8, 5, 1, 0)           \
+  X(22, 8, 8, 4, 0)           \
+  X(23, 8, 8, 3, 0)           \
+  X(24, 8, 8, 2, 0)           \
+  X(25, 8, 7, 0, 1)           \
+  X(26, 8, 6, 0, 1)           \
+  X(27, 8, 8, 0, 1)
 #define MHD_X2_FIRST 17
-#define MHD_X2_LAST 24
+#define MHD_X2_LAST 27

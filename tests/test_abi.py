@@ -68,9 +68,9 @@ def test_workspace_bytes_scale_with_grid(B):
     assert 1.9 < dbl / big < 2.01 and big > small
 
 
-@pytest.mark.parametrize("dtype,tiles", [(0, range(0, 25)), (1, range(0, 5))])
+@pytest.mark.parametrize("dtype,tiles", [(0, range(0, 28)), (1, range(0, 5))])
 def test_every_tile_variant_is_accepted(B, dtype, tiles):
-    """FP32 TMA tiles 1-24 (shapes, stage counts, barrier spacings, packed
+    """FP32 TMA tiles 1-27 (shapes, stage counts, barrier spacings, packed
     pairs, paired points) and FP64 tiles 1-4, and 0 for the default, are
     valid parameters."""
     for t in tiles:
@@ -82,7 +82,7 @@ def test_every_tile_variant_is_accepted(B, dtype, tiles):
     (dict(f0=0.1, kmin=0.0), "shell"), (dict(f0=0.1, kmin=0.2, kmax=0.5), "no integer"),
     (dict(f0=0.1, sigma=1.5), "sigma"), (dict(dtype=7), "dtype"), (dict(forcing_mode=3), "forcing_mode"), (dict(upwind=2), "upwind"),
     (dict(cfl=0.0), "cfl"), (dict(kernel=99), "kernel"),
-    (dict(kernel=2, tile=25), "tile"), (dict(kernel=2, tile=6, dtype=1), "tile"), (dict(kernel=1, tile=3), "tile"),
+    (dict(kernel=2, tile=28), "tile"), (dict(kernel=2, tile=6, dtype=1), "tile"), (dict(kernel=1, tile=3), "tile"),
 ])
 def test_invalid_parameters_are_rejected(B, bad, msg):
     with pytest.raises(B.MhdError) as e:
@@ -116,7 +116,7 @@ def test_seed_field_rejects_null_context(B):
 @pytest.mark.parametrize("shape,grid", [((256, 256, 256), 148), ((512, 512, 512), 148), ((64, 64, 64), 148),
                                         ((37, 23, 11), 148), ((1, 1, 1), 148), ((45, 37, 29), 444),
                                         ((256, 96, 40), 296), ((300, 200, 100), 148), ((256, 240, 128), 148)])
-@pytest.mark.parametrize("tile", [0, 2, 4, 5, 9, 16, 17, 19, 20])
+@pytest.mark.parametrize("tile", [0, 2, 4, 5, 9, 16, 17, 19, 20, 25])
 def test_substep_plan_covers_every_point_once(B, shape, grid, tile):
     """The work split of the fused substep: every (x-y tile, z) of the grid
     exactly once, table rectangular over the CTAs it uses, whole columns
@@ -125,11 +125,11 @@ def test_substep_plan_covers_every_point_once(B, shape, grid, tile):
     p = B.mhd_default_params(nx=nx, ny=ny, nz=nz, kernel=B.MHD_KERNEL_TMA, tile=tile)
     tiles, g = B.mhd_substep_plan(p, grid)
     assert 1 <= g <= grid and len(tiles) % g == 0
-    # tile 0: the paired-point tile 18 (64 x 8) for grids of >= 256 such
-    # columns, else the 32 x 12 tile 13
-    res = tile if tile else (18 if ((nx + 63) // 64) * ((ny + 7) // 8) >= 256 else 13)
+    # tile 0: the warp-specialised paired-point tile 25 (64 x 8) for grids of
+    # >= 256 such columns, else the 32 x 12 tile 13
+    res = tile if tile else (25 if ((nx + 63) // 64) * ((ny + 7) // 8) >= 256 else 13)
     tw = 64 if res >= 17 else 32
-    th = {2: 4, 4: 12, 5: 12, 9: 6, 13: 12, 16: 12, 17: 8, 18: 8, 19: 4, 20: 6, 22: 8}[res]
+    th = {2: 4, 4: 12, 5: 12, 9: 6, 13: 12, 16: 12, 17: 8, 18: 8, 19: 4, 20: 6, 22: 8, 25: 8}[res]
     seen = {}
     for x0, y0, z0, z1, run in tiles:
         assert run == 0

@@ -52,7 +52,7 @@ SHAPES = [(32, 32, 32), (37, 23, 11), (40, 8, 20), (12, 9, 1), (16, 1, 1), (1, 1
 
 
 KERNELS = [(2, 0), (1, 0)]  # (kernel, tile): TMA default tile, plane ring
-TMA_TILES = [(2, t) for t in range(1, 25)]
+TMA_TILES = [(2, t) for t in range(1, 28)]
 
 
 @pytest.mark.parametrize("kernel,tile", KERNELS)
@@ -215,7 +215,7 @@ def test_tma_tiles_give_the_same_bits(shape):
 # --------------------------------------------------------------------------
 # Paired-point FP32 kernel (two x-points per thread, 64-wide tiles)
 # --------------------------------------------------------------------------
-X2_TILES = [17, 19, 20]
+X2_TILES = [17, 19, 20, 25]
 
 
 @pytest.mark.parametrize("tile", X2_TILES)
@@ -266,7 +266,7 @@ def test_paired_kernel_steps_match_oracle(tile):
 # --------------------------------------------------------------------------
 # Upwinding of the continuity equation (upwind = 1)
 # --------------------------------------------------------------------------
-UPWIND_KERNELS = [(2, 0), (1, 0), (2, 1), (2, 7), (2, 17)]
+UPWIND_KERNELS = [(2, 0), (1, 0), (2, 1), (2, 7), (2, 17), (2, 25)]
 
 
 @pytest.mark.parametrize("kernel,tile", UPWIND_KERNELS)
@@ -559,7 +559,7 @@ def test_checkpoint_resume_is_bit_for_bit(dtype, tmp_path):
     b.close()
 
 
-@pytest.mark.parametrize("kernel,tile", [(2, 0), (1, 0), (2, 2), (2, 9), (2, 17)])
+@pytest.mark.parametrize("kernel,tile", [(2, 0), (1, 0), (2, 2), (2, 9), (2, 17), (2, 25)])
 @pytest.mark.parametrize("shape,dtype", [((32, 32, 32), "f32"), ((37, 23, 11), "f64"), ((12, 9, 1), "f32"),
                                          ((16, 1, 1), "f64"), ((40, 8, 20), "f32")])
 def test_padding_canaries_survive_every_entry_point(shape, dtype, kernel, tile):

@@ -22,6 +22,7 @@ CASES = [
     ((16, 16, 16), 1, True, dict(f0=0.02, seed=6, dt_fixed=2e-3)),              # one slab: self-exchange
     ((70, 20, 24), 2, True, dict(f0=0.05, sigma=1.0, seed=7, kernel=2, tile=18)),  # paired-point kernel
     ((128, 16, 27), 3, False, dict(f0=0.05, sigma=0.3, seed=8, kernel=2, tile=22, upwind=1)),
+    ((70, 20, 24), 4, True, dict(f0=0.05, sigma=1.0, seed=9, kernel=2, tile=25)),  # warp-specialised
 ]
 
 
