@@ -357,6 +357,10 @@ __global__ void __launch_bounds__(32 * TY + (WS ? 128 : 0), 1)
     const int kz = K.kmod[2];
     const Cplx<float> ephi = {float(K.cphi), float(K.sphi)};
     const Cplx<float> *rz = static_cast<const Cplx<float> *>(R.roots[2]);
+    // warp-specialised variants: e^{i k_z z} of the next output plane is
+    // requested one plane ahead (measured: the barrier variants run slower so)
+    Cplx<float> ez_next = {1.f, 0.f};
+    if (WS && forcing) ez_next = rz[mz];
 
     int slot = (int)(G % NS);
     uint32_t phase = (uint32_t)((G / NS) & 1ull);
@@ -586,7 +590,7 @@ __global__ void __launch_bounds__(32 * TY + (WS ? 128 : 0), 1)
           // forcing of the step at the pair (Eqs. 4-6)
           float2 fz[3] = {bc(0.f), bc(0.f), bc(0.f)};
           if (forcing) {
-            const Cplx<float> ez = cmul(rz[mz], ephi);  // e^{i (k_z z + phi)}
+            const Cplx<float> ez = cmul(WS ? ez_next : rz[mz], ephi);  // e^{i (k_z z + phi)}
             const float2 er = fma2(exr, bc(ez.re), mul2(exi, bc(-ez.im)));
             const float2 ei = fma2(exr, bc(ez.im), mul2(exi, bc(ez.re)));
 #pragma unroll
@@ -681,6 +685,7 @@ __global__ void __launch_bounds__(32 * TY + (WS ? 128 : 0), 1)
         if (forcing) {
           mz += kz;
           if (mz >= nzg) mz -= nzg;
+          if constexpr (WS) ez_next = rz[mz];
         }
       }
       if (++slot == NS) {
