@@ -24,6 +24,7 @@
 // error in the run's clock (status bit 1), waits (bounded) for the copies it
 // issued and returns without writing further results.
 #include <cuda.h>
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -772,9 +773,13 @@ __global__ void __launch_bounds__(TXW * TY, TXW == 32 ? 2 : 1)
     const int cxy = (ty + RAD) * SX + tx + 4;
     // pencils of A_x, A_y over planes p-6 .. p; delay line of the lead-plane
     // values (d_y A_z, d_x A_z, d_x A_y, d_y A_x, |u|, 1/rho) of planes p-3 .. p
-    T ax[7], ay[7], dl[4][6];
+    // rings indexed by the plane: A_x, A_y of planes p-7 .. p in slot p & 7,
+    // the lead-plane values of planes p-3 .. p in slot p & 3; the plane loop
+    // is unrolled by 8 so that every ring index is a constant and no value
+    // moves between registers as the sweep advances
+    T ax[8], ay[8], dl[4][6];
 #pragma unroll
-    for (int k = 0; k < 7; ++k) ax[k] = ay[k] = T(0);
+    for (int k = 0; k < 8; ++k) ax[k] = ay[k] = T(0);
 #pragma unroll
     for (int k = 0; k < 4; ++k)
 #pragma unroll
@@ -785,7 +790,9 @@ __global__ void __launch_bounds__(TXW * TY, TXW == 32 ? 2 : 1)
     bool bad = false;
     bool failed = false;
     int p = 0;
-    for (; p < npl; ++p) {
+    // one plane of the sweep at phase PH = p mod 8; false once a wait gave up
+    auto plane = [&](auto PH) -> bool {
+      constexpr int K = decltype(PH)::value;
       if (tid == 0 && p + P < npl) {
         fence_proxy_async_smem();
         issue(p + P);  // into the stage of plane p-1, released at the end of the last iteration
@@ -802,43 +809,57 @@ __global__ void __launch_bounds__(TXW * TY, TXW == 32 ? 2 : 1)
         const T *r = o + f * FIELD;
         return d1_vals(r[SX], r[-SX], r[2 * SX], r[-2 * SX], r[3 * SX], r[-3 * SX], w[1]);
       };
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        ax[k] = ax[k + 1];
-        ay[k] = ay[k + 1];
-      }
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int v = 0; v < 6; ++v) dl[k][v] = dl[k + 1][v];
-      ax[6] = o[4 * FIELD];
-      ay[6] = o[5 * FIELD];
+      ax[K] = o[4 * FIELD];
+      ay[K] = o[5 * FIELD];
+      T *d = dl[K & 3];
       if (active) {
         const T ux = o[FIELD], uy = o[2 * FIELD], uz = o[3 * FIELD];
-        dl[3][0] = dy(6);
-        dl[3][1] = dx(6);
-        dl[3][2] = dx(5);
-        dl[3][3] = dy(4);
-        dl[3][4] = sqrt(ux * ux + uy * uy + uz * uz);
-        dl[3][5] = exp(-o[0]);
+        d[0] = dy(6);
+        d[1] = dx(6);
+        d[2] = dx(5);
+        d[3] = dy(4);
+        d[4] = sqrt(ux * ux + uy * uy + uz * uz);
+        d[5] = exp(-o[0]);
       }
       if (p >= 2 * RAD && ok && active) {  // output plane p-3
-        const T dzAx = d1_vals(ax[4], ax[2], ax[5], ax[1], ax[6], ax[0], w[2]);
-        const T dzAy = d1_vals(ay[4], ay[2], ay[5], ay[1], ay[6], ay[0], w[2]);
-        const T Bx = dl[0][0] - dzAy;
-        const T By = dzAx - dl[0][1];
-        const T Bz = dl[0][2] - dl[0][3];
+        constexpr int c = (K + 5) & 7;     // slot of plane p-3
+        const T dzAx = d1_vals(ax[(c + 1) & 7], ax[(c + 7) & 7], ax[(c + 2) & 7], ax[(c + 6) & 7], ax[(c + 3) & 7],
+                               ax[(c + 5) & 7], w[2]);
+        const T dzAy = d1_vals(ay[(c + 1) & 7], ay[(c + 7) & 7], ay[(c + 2) & 7], ay[(c + 6) & 7], ay[(c + 3) & 7],
+                               ay[(c + 5) & 7], w[2]);
+        const T *e = dl[(K + 1) & 3];  // lead-plane values of plane p-3
+        const T Bx = e[0] - dzAy;
+        const T By = dzAx - e[1];
+        const T Bz = e[2] - e[3];
         const T b2 = norm2_rn(Bx, By, Bz);
-        const T v = dl[0][4] + sqrt(cs2 + b2 * dl[0][5]);
+        const T v = e[4] + sqrt(cs2 + b2 * e[5]);
         bad |= isnan(v);
         vm = fmax(vm, v);
         if constexpr (MODE == 1) sb2 += (double)b2;
       }
-      if (__syncthreads_or(!ok)) {
-        failed = true;
-        break;
-      }
+      return !__syncthreads_or(!ok);
+    };
+    using I0 = std::integral_constant<int, 0>;
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    using I3 = std::integral_constant<int, 3>;
+    using I4 = std::integral_constant<int, 4>;
+    using I5 = std::integral_constant<int, 5>;
+    using I6 = std::integral_constant<int, 6>;
+    using I7 = std::integral_constant<int, 7>;
+    // npl is the same for every thread of the CTA, so the guards are uniform
+    while (p < npl) {
+      if (!plane(I0{})) break;
+      if (++p == npl || !plane(I1{})) break;
+      if (++p == npl || !plane(I2{})) break;
+      if (++p == npl || !plane(I3{})) break;
+      if (++p == npl || !plane(I4{})) break;
+      if (++p == npl || !plane(I5{})) break;
+      if (++p == npl || !plane(I6{})) break;
+      if (++p == npl || !plane(I7{})) break;
+      ++p;
     }
+    failed = p < npl;
     vmax = bad ? __longlong_as_double(0x7ff8000000000000ll) : (double)vm;
     if (failed) {
       if (tid == 0) {
