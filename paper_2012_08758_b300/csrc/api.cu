@@ -251,8 +251,10 @@ int validate(const mhd_params *p, std::string *why) {
 // AUTO resolves to the TMA kernel; tile 0 to the fastest variant measured on
 // B300 for the grid: FP32 grids with at least LARGE_COLUMNS columns of 64 x 8
 // points (e.g. 512^2 and up) take the warp-specialised paired-point kernel
-// with 7 stages (tile 25; 512^3: 9.28e9 against 8.66e9 cell-updates/s for the
-// barrier-synchronised tile 18 and 7.6e9 for the scalar kernel), smaller
+// with 6 stages of q and 3 of w, both copied by its producer warpgroup
+// (tile 26; 512^3: 1.03e10 cell-updates/s, against 9.99e9 for tile 25, which
+// reads w from global memory, 8.66e9 for the barrier-synchronised tile 18 and
+// 7.6e9 for the scalar kernel), smaller
 // FP32 grids the 32 x 12 scalar kernel with 9 stages
 // and a barrier every fifth plane (tile 13; 256^3: 7.5e9 against 6.9e9), FP64
 // the 32 x 8 tile with 6 stages.  Runs of one batch need the same resolved
@@ -263,7 +265,7 @@ mhd_params resolved(const mhd_params *p) {
   if (r.kernel == MHD_KERNEL_AUTO) r.kernel = MHD_KERNEL_TMA;
   if (r.kernel == MHD_KERNEL_TMA && r.tile == 0) {
     const long long cols64 = (long long)((r.nx + 63) / 64) * ((r.ny + 7) / 8);
-    r.tile = r.dtype == MHD_F32 ? (cols64 >= LARGE_COLUMNS ? 25 : 13) : 3;
+    r.tile = r.dtype == MHD_F32 ? (cols64 >= LARGE_COLUMNS ? 26 : 13) : 3;
   }
   return r;
 }
@@ -288,8 +290,20 @@ EncodeTiledFn encode_fn() {
 
 // 4-D map of one state buffer: (x: px, y: py, z: pz, field: 7), box = one
 // z-plane of a (tw+8) x (th+6) tile of all seven fields.
+// Padded 4-D field array (x, y, z, field) with a box of bx x by points of one
+// z-plane, all fields.
+int encode_box_map(CUtensorMap *m, void *base, size_t esz, int px, int py, int pz, int bx, int by,
+                   std::string *why);
+
+// The substep / reduction tile of tw x th points with its halo (4 points
+// left and right so that rows stay 16-byte aligned, RAD above and below).
 int encode_state_map(CUtensorMap *m, void *base, size_t esz, int px, int py, int pz, int tw, int th,
                      std::string *why) {
+  return encode_box_map(m, base, esz, px, py, pz, tw + 8, th + 2 * RAD, why);
+}
+
+int encode_box_map(CUtensorMap *m, void *base, size_t esz, int px, int py, int pz, int bx, int by,
+                   std::string *why) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) {
     *why = "cuTensorMapEncodeTiled is not available from the driver";
@@ -298,7 +312,7 @@ int encode_state_map(CUtensorMap *m, void *base, size_t esz, int px, int py, int
   const cuuint64_t dims[4] = {(cuuint64_t)px, (cuuint64_t)py, (cuuint64_t)pz, (cuuint64_t)NF};
   const cuuint64_t strides[3] = {(cuuint64_t)px * esz, (cuuint64_t)px * py * esz,
                                  (cuuint64_t)px * py * pz * esz};
-  const cuuint32_t box[4] = {(cuuint32_t)(tw + 8), (cuuint32_t)(th + 2 * RAD), 1u, (cuuint32_t)NF};
+  const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1u, (cuuint32_t)NF};
   const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
   CUresult r = fn(m, esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, base,
                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -613,7 +627,8 @@ int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t worksp
     std::string why;
     for (int b = 0; b < 2; ++b)
       if (encode_state_map(&R.tmap[b], R.q[b], L.esz, L.px, L.py, L.pz, L.stw, L.sth, &why) ||
-          encode_state_map(&R.rmap[b], R.q[b], L.esz, L.px, L.py, L.pz, L.tw, L.th, &why)) {
+          encode_state_map(&R.rmap[b], R.q[b], L.esz, L.px, L.py, L.pz, L.tw, L.th, &why) ||
+          (b == 0 && encode_box_map(&R.wmap, R.w, L.esz, L.px, L.py, L.pz, L.stw, L.sth, &why))) {
         fail(ctx, MHD_ECUDA, "%s", why.c_str());
         return cleanup(MHD_ECUDA);
       }

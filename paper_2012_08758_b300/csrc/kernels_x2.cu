@@ -230,17 +230,43 @@ constexpr int X2_WS_LAUNCH_REGS = 168, X2_WS_PRODUCER_REGS = 40, X2_WS_COMPUTE_R
 static_assert(12 * 32 * X2_WS_LAUNCH_REGS == 8 * 32 * X2_WS_COMPUTE_REGS + 4 * 32 * X2_WS_PRODUCER_REGS,
               "register split of the warp-specialised variants");
 
+// Shared memory of a variant: NS TMA stages of q; for the warp-specialised
+// variants, where it fits, a ring of NS - 3 stages of w (the interior points
+// of one z-plane of the tile, all fields; substeps 2 and 3 read w through it
+// instead of from global memory); then the mbarriers (full / empty per
+// stage of each ring).
+template <int TY>
+__host__ __device__ constexpr int x2_wstage_bytes() {
+  return NF * TY * 64 * (int)sizeof(float);
+}
+template <int TY, int NS>
+__host__ __device__ constexpr bool x2_w_by_tma() {
+  return NS * TmaShape<float, TY, 64>::STAGE_BYTES + (NS - 3) * x2_wstage_bytes<TY>() + (4 * NS - 6) * 8 <=
+         232448;  // the opt-in limit of dynamic shared memory per block
+}
+template <int TY, int NS, bool WS>
+__host__ __device__ constexpr int x2_smem_bytes() {
+  return !WS ? NS * TmaShape<float, TY, 64>::STAGE_BYTES + NS * 8
+             : x2_w_by_tma<TY, NS>()
+                   ? NS * TmaShape<float, TY, 64>::STAGE_BYTES + (NS - 3) * x2_wstage_bytes<TY>() + (4 * NS - 6) * 8
+                   : NS * TmaShape<float, TY, 64>::STAGE_BYTES + 2 * NS * 8;
+}
+
 namespace {
 // The producer: every plane of every tile of this CTA, in the compute warps'
 // order, into stage g mod NS once the plane g - NS has been released.  On a
 // wait that gives up it records status bit 1 and raises the CTA's abort flag;
-// before returning it waits (bounded) for every copy it issued.
-template <int TY, int NS, int SUB>
+// before returning it waits (bounded) for every copy it issued.  WT: after
+// lead plane p (p >= 6) it also copies w of output plane p - 3 into the w
+// ring, slot gw mod NW, once w plane gw - NW has been released.
+template <int TY, int NS, int SUB, bool WT>
 __device__ __forceinline__ void x2_produce(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles,
                                            int ntiles, unsigned char *smem, uint64_t *full, uint64_t *empty,
+                                           unsigned char *wst, uint64_t *wfull, uint64_t *wempty,
                                            volatile int *abort) {
   using SH = TmaShape<float, TY, 64>;
-  unsigned long long g = 0;
+  constexpr int NW = NS - 3;
+  unsigned long long g = 0, gw = 0;
   int fail_run = -1;
   for (int t = blockIdx.x; t < ntiles && fail_run < 0; t += gridDim.x) {
     const Tile tile = tiles[t];
@@ -257,6 +283,20 @@ __device__ __forceinline__ void x2_produce(const RunDesc *__restrict__ runs, con
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(&full[sl], (uint32_t)(NF * SH::FIELD * sizeof(float)));
       tma_load_4d(smem + sl * SH::STAGE_BYTES, map, &full[sl], tile.x0, tile.y0, tile.z0 + p, 0);
+      if constexpr (WT) {
+        if (p >= 2 * RAD) {  // w of output plane o = p - 3: padded z = z0 + o
+          const int ws = (int)(gw % NW);
+          if ((gw >= NW && !mbar_wait(&wempty[ws], (uint32_t)(((gw / NW) - 1) & 1ull))) || *abort) {
+            fail_run = tile.run;
+            ++g;
+            break;
+          }
+          mbar_arrive_expect_tx(&wfull[ws], (uint32_t)x2_wstage_bytes<TY>());
+          tma_load_4d(wst + ws * x2_wstage_bytes<TY>(), &R.wmap, &wfull[ws], tile.x0 + OX, tile.y0 + OY,
+                      tile.z0 + p - RAD, 0);
+          ++gw;
+        }
+      }
     }
   }
   if (fail_run >= 0) {
@@ -265,6 +305,9 @@ __device__ __forceinline__ void x2_produce(const RunDesc *__restrict__ runs, con
   }
   for (unsigned long long q = g > (unsigned long long)NS ? g - NS : 0; q < g; ++q)
     mbar_wait(&full[q % NS], (uint32_t)((q / NS) & 1ull));
+  if constexpr (WT)
+    for (unsigned long long q = gw > (unsigned long long)NW ? gw - NW : 0; q < gw; ++q)
+      mbar_wait(&wfull[q % NW], (uint32_t)((q / NW) & 1ull));
 }
 }  // namespace
 
@@ -284,13 +327,25 @@ __global__ void __launch_bounds__(32 * TY + (WS ? 128 : 0), 1)
   static_assert(WS ? NS >= 5 : P >= 1, "need at least one plane of prefetch");
   static_assert(!WS || TY == 8, "the register split of the warp-specialised variants is for 8 compute warps");
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * SH::STAGE_BYTES);
+  // WTL: the layout holds the w ring (every substep of such a variant); WT:
+  // this substep reads w through it
+  constexpr bool WTL = WS && x2_w_by_tma<TY, NS>();
+  constexpr bool WT = WTL && SUB > 0;
+  constexpr int NW = WTL ? NS - 3 : 1;
+  unsigned char *wst = smem + NS * SH::STAGE_BYTES;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(wst + (WTL ? NW * x2_wstage_bytes<TY>() : 0));
+  uint64_t *wfull = bars + 2 * NS, *wempty = bars + 2 * NS + NW;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
   __shared__ int ws_abort;
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
     if constexpr (WS)
       for (int s = 0; s < NS; ++s) mbar_init(&bars[NS + s], TY);
+    if constexpr (WTL)
+      for (int s = 0; s < NW; ++s) {
+        mbar_init(&wfull[s], 1);
+        mbar_init(&wempty[s], TY);
+      }
     if constexpr (WS) ws_abort = 0;
     mbar_fence_init();
   }
@@ -298,13 +353,15 @@ __global__ void __launch_bounds__(32 * TY + (WS ? 128 : 0), 1)
   if constexpr (WS) {
     if (ty >= TY) {
       asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(X2_WS_PRODUCER_REGS));
-      if (ty == TY && tx == 0) x2_produce<TY, NS, SUB>(runs, tiles, ntiles, smem, bars, bars + NS, &ws_abort);
+      if (ty == TY && tx == 0)
+        x2_produce<TY, NS, SUB, WT>(runs, tiles, ntiles, smem, bars, bars + NS, wst, wfull, wempty, &ws_abort);
       return;
     }
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(X2_WS_COMPUTE_REGS));
   }
 
   unsigned long long G = 0;  // planes issued by this CTA before the current tile
+  unsigned long long gwc = 0;  // WT: output planes whose w this warp has taken from the ring
   bool failed = false, waits_ok = true;
   int fail_run = -1, fail_p = 0, issued_hi = 0;
 
@@ -426,7 +483,7 @@ __global__ void __launch_bounds__(32 * TY + (WS ? 128 : 0), 1)
       const int o = p - RAD;       // centre plane (lead index), interior plane z0 + o - 3
       const bool outp = o >= RAD;  // an interior plane of this tile: computed and stored
       float2 wc[NF];
-      if (need_w && outp) {
+      if (!WT && need_w && outp) {
         const float *wp = w + cidx;
 #pragma unroll
         for (int f = 0; f < NF; ++f, wp += fs) wc[f] = ldcs2_pinned(wp);
@@ -606,6 +663,20 @@ __global__ void __launch_bounds__(32 * TY + (WS ? 128 : 0), 1)
 #pragma unroll
           for (int f = 0; f < NF; ++f) qc[f] = pz[f][2];
           float2 wv[NF], qn[NF];
+          if constexpr (WT) {
+            // w of this output plane from the ring, then the slot goes back
+            const int ws = (int)(gwc % NW);
+            if (!mbar_wait(&wfull[ws], (uint32_t)((gwc / NW) & 1ull))) {
+              ws_abort = 1;
+              atomicOr(&R.clock->status, 2);
+            }
+            const float *wr = reinterpret_cast<const float *>(wst + ws * x2_wstage_bytes<TY>()) + ty * 64 + 2 * tx;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) wc[f] = ld2(wr + f * TY * 64);
+            __syncwarp();
+            if (tx == 0) mbar_arrive(&wempty[ws]);
+            ++gwc;
+          }
 #pragma unroll
           for (int f = 0; f < NF; ++f) {
             wv[f] = mul2(dt, r[f]);
@@ -751,12 +822,6 @@ __global__ void __launch_bounds__(32 * TY + (WS ? 128 : 0), 1)
   }
 }
 
-namespace {
-template <int TY, int NS, bool WS>
-constexpr int x2_smem_bytes() {
-  return NS * TmaShape<float, TY, 64>::STAGE_BYTES + (WS ? 2 : 1) * NS * 8;
-}
-}  // namespace
 
 // Tile rows of a paired-point variant (0 if `tile` is not one).
 int x2_rows(int tile) {

@@ -52,6 +52,8 @@ struct RunDesc {
                             // of a substep tile with its halo
   CUtensorMap rmap[2];      // the same for the reduction tiles (step prologue, B_rms sweep);
                             // equal to tmap unless the substep tile is wider
+  CUtensorMap wmap;         // TMA map of w: box of the substep tile's interior points of one
+                            // z-plane, all fields (warp-specialised paired kernel)
   int nx, ny, nz;
   int px, py, pz;           // padded extents; px is the row pitch
   long long fstride;        // elements per field (px * py * pz)

@@ -4,7 +4,9 @@
 // of 32 x TY compute threads covers a 64 x TY column.  Prefetch distance
 // NS - 3 - BAR >= 1 planes (tiles 23, 24: two and three planes ahead).
 // Tiles 25-27: a producer warpgroup issues the copies against per-stage
-// "empty" mbarriers, no CTA barrier; up to NS - 4 planes ahead.
+// "empty" mbarriers, no CTA barrier; up to NS - 4 planes ahead.  Tile 26
+// (6 stages) also has room for a ring of 3 stages of w, which its producer
+// fills one output plane at a time (the large-grid default).
 #pragma once
 #define MHD_X2_VARIANTS(X) \
   X(17, 8, 6, 2, 0)           \

@@ -215,7 +215,7 @@ def test_tma_tiles_give_the_same_bits(shape):
 # --------------------------------------------------------------------------
 # Paired-point FP32 kernel (two x-points per thread, 64-wide tiles)
 # --------------------------------------------------------------------------
-X2_TILES = [17, 19, 20, 25]
+X2_TILES = [17, 19, 20, 25, 26]
 
 
 @pytest.mark.parametrize("tile", X2_TILES)
@@ -266,7 +266,7 @@ def test_paired_kernel_steps_match_oracle(tile):
 # --------------------------------------------------------------------------
 # Upwinding of the continuity equation (upwind = 1)
 # --------------------------------------------------------------------------
-UPWIND_KERNELS = [(2, 0), (1, 0), (2, 1), (2, 7), (2, 17), (2, 25)]
+UPWIND_KERNELS = [(2, 0), (1, 0), (2, 1), (2, 7), (2, 17), (2, 25), (2, 26)]
 
 
 @pytest.mark.parametrize("kernel,tile", UPWIND_KERNELS)
