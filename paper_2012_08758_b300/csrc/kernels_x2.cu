@@ -231,25 +231,29 @@ static_assert(12 * 32 * X2_WS_LAUNCH_REGS == 8 * 32 * X2_WS_COMPUTE_REGS + 4 * 3
               "register split of the warp-specialised variants");
 
 // Shared memory of a variant: NS TMA stages of q; for the warp-specialised
-// variants, where it fits, a ring of NS - 3 stages of w (the interior points
-// of one z-plane of the tile, all fields; substeps 2 and 3 read w through it
-// instead of from global memory); then the mbarriers (full / empty per
-// stage of each ring).
+// variants, where it fits, a ring of NW <= NS - 3 stages of w (the interior
+// points of one z-plane of the tile, all fields; substeps 2 and 3 read w
+// through it instead of from global memory); then the mbarriers (full /
+// empty per stage of each ring).
 template <int TY>
 __host__ __device__ constexpr int x2_wstage_bytes() {
   return NF * TY * 64 * (int)sizeof(float);
 }
+template <int TY, int NS, int NW>
+__host__ __device__ constexpr int x2_ws_bytes() {
+  return NS * TmaShape<float, TY, 64>::STAGE_BYTES + NW * x2_wstage_bytes<TY>() + (2 * NS + 2 * NW) * 8;
+}
+// the largest w ring that fits the opt-in limit of dynamic shared memory per
+// block (232448 bytes), 0 if none
 template <int TY, int NS>
-__host__ __device__ constexpr bool x2_w_by_tma() {
-  return NS * TmaShape<float, TY, 64>::STAGE_BYTES + (NS - 3) * x2_wstage_bytes<TY>() + (4 * NS - 6) * 8 <=
-         232448;  // the opt-in limit of dynamic shared memory per block
+__host__ __device__ constexpr int x2_wring() {
+  return x2_ws_bytes<TY, NS, NS - 3>() <= 232448   ? NS - 3
+         : x2_ws_bytes<TY, NS, 2>() <= 232448      ? 2
+         : 0;
 }
 template <int TY, int NS, bool WS>
 __host__ __device__ constexpr int x2_smem_bytes() {
-  return !WS ? NS * TmaShape<float, TY, 64>::STAGE_BYTES + NS * 8
-             : x2_w_by_tma<TY, NS>()
-                   ? NS * TmaShape<float, TY, 64>::STAGE_BYTES + (NS - 3) * x2_wstage_bytes<TY>() + (4 * NS - 6) * 8
-                   : NS * TmaShape<float, TY, 64>::STAGE_BYTES + 2 * NS * 8;
+  return !WS ? NS * TmaShape<float, TY, 64>::STAGE_BYTES + NS * 8 : x2_ws_bytes<TY, NS, x2_wring<TY, NS>()>();
 }
 
 namespace {
@@ -257,15 +261,17 @@ namespace {
 // order, into stage g mod NS once the plane g - NS has been released.  On a
 // wait that gives up it records status bit 1 and raises the CTA's abort flag;
 // before returning it waits (bounded) for every copy it issued.  WT: after
-// lead plane p (p >= 6) it also copies w of output plane p - 3 into the w
-// ring, slot gw mod NW, once w plane gw - NW has been released.
+// lead plane p it also copies w of output plane p - 3 - D into the w ring,
+// slot gw mod NW, once w plane gw - NW has been released (D = NS - 3 - NW
+// keeps at most NW w planes in flight; the last D of a tile follow its last
+// lead plane).
 template <int TY, int NS, int SUB, bool WT>
 __device__ __forceinline__ void x2_produce(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles,
                                            int ntiles, unsigned char *smem, uint64_t *full, uint64_t *empty,
                                            unsigned char *wst, uint64_t *wfull, uint64_t *wempty,
                                            volatile int *abort) {
   using SH = TmaShape<float, TY, 64>;
-  constexpr int NW = NS - 3;
+  constexpr int NW = x2_wring<TY, NS>() > 0 ? x2_wring<TY, NS>() : 1, D = NS - 3 - NW;
   unsigned long long g = 0, gw = 0;
   int fail_run = -1;
   for (int t = blockIdx.x; t < ntiles && fail_run < 0; t += gridDim.x) {
@@ -274,6 +280,15 @@ __device__ __forceinline__ void x2_produce(const RunDesc *__restrict__ runs, con
     const RunDesc &R = runs[tile.run];
     const CUtensorMap *map = &R.tmap[(R.coeffs->parity + SUB) & 1];
     const int npl = (tile.z1 - tile.z0) + 2 * RAD;
+    // w of output plane o (lead index, padded z = z0 + o) into the ring
+    auto issue_w = [&](int o) {
+      const int ws = (int)(gw % NW);
+      if ((gw >= NW && !mbar_wait(&wempty[ws], (uint32_t)(((gw / NW) - 1) & 1ull))) || *abort) return false;
+      mbar_arrive_expect_tx(&wfull[ws], (uint32_t)x2_wstage_bytes<TY>());
+      tma_load_4d(wst + ws * x2_wstage_bytes<TY>(), &R.wmap, &wfull[ws], tile.x0 + OX, tile.y0 + OY, tile.z0 + o, 0);
+      ++gw;
+      return true;
+    };
     for (int p = 0; p < npl; ++p, ++g) {
       const int sl = (int)(g % NS);
       if ((g >= NS && !mbar_wait(&empty[sl], (uint32_t)(((g / NS) - 1) & 1ull))) || *abort) {
@@ -284,19 +299,17 @@ __device__ __forceinline__ void x2_produce(const RunDesc *__restrict__ runs, con
       mbar_arrive_expect_tx(&full[sl], (uint32_t)(NF * SH::FIELD * sizeof(float)));
       tma_load_4d(smem + sl * SH::STAGE_BYTES, map, &full[sl], tile.x0, tile.y0, tile.z0 + p, 0);
       if constexpr (WT) {
-        if (p >= 2 * RAD) {  // w of output plane o = p - 3: padded z = z0 + o
-          const int ws = (int)(gw % NW);
-          if ((gw >= NW && !mbar_wait(&wempty[ws], (uint32_t)(((gw / NW) - 1) & 1ull))) || *abort) {
-            fail_run = tile.run;
-            ++g;
-            break;
-          }
-          mbar_arrive_expect_tx(&wfull[ws], (uint32_t)x2_wstage_bytes<TY>());
-          tma_load_4d(wst + ws * x2_wstage_bytes<TY>(), &R.wmap, &wfull[ws], tile.x0 + OX, tile.y0 + OY,
-                      tile.z0 + p - RAD, 0);
-          ++gw;
+        if (p >= 2 * RAD + D && !issue_w(p - RAD - D)) {
+          fail_run = tile.run;
+          ++g;
+          break;
         }
       }
+    }
+    if constexpr (WT) {
+      // the w of the tile's last D output planes
+      for (int o = npl - RAD - D; fail_run < 0 && o < npl - RAD; ++o)
+        if (o >= RAD && !issue_w(o)) fail_run = tile.run;
     }
   }
   if (fail_run >= 0) {
@@ -329,9 +342,9 @@ __global__ void __launch_bounds__(32 * TY + (WS ? 128 : 0), 1)
   extern __shared__ __align__(128) unsigned char smem[];
   // WTL: the layout holds the w ring (every substep of such a variant); WT:
   // this substep reads w through it
-  constexpr bool WTL = WS && x2_w_by_tma<TY, NS>();
+  constexpr bool WTL = WS && x2_wring<TY, NS>() > 0;
   constexpr bool WT = WTL && SUB > 0;
-  constexpr int NW = WTL ? NS - 3 : 1;
+  constexpr int NW = WTL ? x2_wring<TY, NS>() : 1;
   unsigned char *wst = smem + NS * SH::STAGE_BYTES;
   uint64_t *bars = reinterpret_cast<uint64_t *>(wst + (WTL ? NW * x2_wstage_bytes<TY>() : 0));
   uint64_t *wfull = bars + 2 * NS, *wempty = bars + 2 * NS + NW;

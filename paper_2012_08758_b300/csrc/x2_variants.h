@@ -4,9 +4,10 @@
 // of 32 x TY compute threads covers a 64 x TY column.  Prefetch distance
 // NS - 3 - BAR >= 1 planes (tiles 23, 24: two and three planes ahead).
 // Tiles 25-27: a producer warpgroup issues the copies against per-stage
-// "empty" mbarriers, no CTA barrier; up to NS - 4 planes ahead.  Tile 26
-// (6 stages) also has room for a ring of 3 stages of w, which its producer
-// fills one output plane at a time (the large-grid default).
+// "empty" mbarriers, no CTA barrier; up to NS - 4 planes ahead.  Tiles 26
+// (6 stages) and 25 (7) also have room for a ring of 3 / 2 stages of w, which
+// the producer fills one output plane at a time (tile 26 is the large-grid
+// default; the two measure alike).
 #pragma once
 #define MHD_X2_VARIANTS(X) \
   X(17, 8, 6, 2, 0)           \
