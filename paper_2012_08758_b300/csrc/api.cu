@@ -249,24 +249,16 @@ int validate(const mhd_params *p, std::string *why) {
 }
 
 // AUTO resolves to the TMA kernel; tile 0 to the fastest variant measured on
-// B300 for the grid: FP32 grids with at least LARGE_COLUMNS columns of 64 x 8
-// points (e.g. 512^2 and up) take the warp-specialised paired-point kernel
-// with 6 stages of q and 3 of w, both copied by its producer warpgroup
-// (tile 26; 512^3: 1.03e10 cell-updates/s, against 9.99e9 for tile 25, which
-// reads w from global memory, 8.66e9 for the barrier-synchronised tile 18 and
-// 7.6e9 for the scalar kernel), smaller
-// FP32 grids the 32 x 12 scalar kernel with 9 stages
-// and a barrier every fifth plane (tile 13; 256^3: 7.5e9 against 6.9e9), FP64
-// the 32 x 8 tile with 6 stages.  Runs of one batch need the same resolved
-// tile, so a batch that mixes the two classes must name a tile explicitly.
-constexpr int LARGE_COLUMNS = 256;
+// B300: FP32 grids take the warp-specialised paired-point kernel with 6
+// stages of q and 3 of w, both copied by its producer warpgroup (tile 26;
+// 512^3: 1.03e10 cell-updates/s against 8.66e9 for the barrier-synchronised
+// paired tile 18 and 7.6e9 for the 32 x 12 scalar kernel; 32^3 - 192^3 6-51%
+// faster than the scalar kernel, 256^3 within 1%), FP64 the 32 x 8 scalar
+// tile with 6 stages.
 mhd_params resolved(const mhd_params *p) {
   mhd_params r = *p;
   if (r.kernel == MHD_KERNEL_AUTO) r.kernel = MHD_KERNEL_TMA;
-  if (r.kernel == MHD_KERNEL_TMA && r.tile == 0) {
-    const long long cols64 = (long long)((r.nx + 63) / 64) * ((r.ny + 7) / 8);
-    r.tile = r.dtype == MHD_F32 ? (cols64 >= LARGE_COLUMNS ? 26 : 13) : 3;
-  }
+  if (r.kernel == MHD_KERNEL_TMA && r.tile == 0) r.tile = r.dtype == MHD_F32 ? 26 : 3;
   return r;
 }
 
@@ -1126,8 +1118,7 @@ int mhd_batch_create(mhd_ctx *const *runs, int nruns, mhd_batch **out) {
     if (r->p.dtype != r0->p.dtype || r->stream != r0->stream || r->p.kernel != r0->p.kernel ||
         r->p.tile != r0->p.tile)
       return fail(nullptr, MHD_EINVAL,
-                  "runs of a batch must share dtype, stream, kernel and tile (tile 0 resolves by grid size: "
-                  "name a tile to batch large and small grids together)");
+                  "runs of a batch must share dtype, stream, kernel and tile");
     for (int j = 0; j < i; ++j)
       if (runs[j] == r) return fail(nullptr, MHD_EINVAL, "run %d appears twice", i);
     cells_total += (double)r->p.nx * r->p.ny * r->p.nz;

@@ -125,9 +125,8 @@ def test_substep_plan_covers_every_point_once(B, shape, grid, tile):
     p = B.mhd_default_params(nx=nx, ny=ny, nz=nz, kernel=B.MHD_KERNEL_TMA, tile=tile)
     tiles, g = B.mhd_substep_plan(p, grid)
     assert 1 <= g <= grid and len(tiles) % g == 0
-    # tile 0: the warp-specialised paired-point tile 26 (64 x 8) for grids of
-    # >= 256 such columns, else the 32 x 12 tile 13
-    res = tile if tile else (26 if ((nx + 63) // 64) * ((ny + 7) // 8) >= 256 else 13)
+    # tile 0: the warp-specialised paired-point tile 26 (64 x 8 columns)
+    res = tile if tile else 26
     tw = 64 if res >= 17 else 32
     th = {2: 4, 4: 12, 5: 12, 9: 6, 13: 12, 16: 12, 17: 8, 18: 8, 19: 4, 20: 6, 22: 8, 25: 8, 26: 8}[res]
     seen = {}
