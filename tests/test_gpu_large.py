@@ -121,3 +121,59 @@ def test_largest_grid_1024_cubed_sampled_rhs_and_invariants():
     assert d["divb_max"] < 1e-4 * d["bmax"] * n / (2 * math.pi)
     assert B.mhd_padding_check(run.ctx) == 0
     run.close()
+
+
+def _product_state(n, seed, amp=0.2):
+    """Each field a sum of two products g(x) h(y) k(z) of random 1-D waves:
+    built by broadcasting (cheap at 512^3), with non-zero mixed derivatives."""
+    rng = np.random.default_rng(seed)
+    c = np.arange(n) * (2 * math.pi / n)
+    q = np.zeros((7, n, n, n), dtype=np.float32)
+    for f in range(7):
+        for _ in range(2):
+            kx, ky, kz = rng.integers(1, 6, size=3)
+            px, py, pz = rng.uniform(0, 2 * math.pi, size=3)
+            a = amp * rng.standard_normal()
+            gx = np.cos(kx * c + px).astype(np.float32)
+            gy = np.cos(ky * c + py).astype(np.float32)
+            gz = np.cos(kz * c + pz).astype(np.float32)
+            q[f] += np.float32(a) * gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
+    return q
+
+
+@pytest.mark.gpu
+def test_bench_grid_512_cubed_step_sampled_against_oracle_windows():
+    """The 512^3 FP32 grid in the benchmark's launch configuration (default
+    tile and work split over every SM): one full step (three substeps),
+    then 24 sampled points -- corners, faces, random -- against the FP64
+    oracle stepping a 25^3 periodic window of the initial state around each
+    point with the same dt.  One step reaches 3 substeps x 3 points = 9
+    points along each axis, so the window's centre (12 from its edges) sees
+    exactly the large grid's values.  Forcing off (its phase is tied to the
+    global coordinates), viscosity and resistivity on."""
+    n, w, r = 512, 25, 12
+    phys = dict(cs=1.0, nu=5e-3, eta=5e-3, f0=0.0, dt_fixed=2e-3)
+    q0 = _product_state(n, seed=21)
+    run = make_run(nx=n, ny=n, nz=n, dtype="f32", **phys)
+    run.set_state(q0)
+    run.step(1)
+    got, t, step = run.get_state(dtype=np.float32)
+    run.close()
+    assert step == 1 and t == pytest.approx(2e-3, rel=1e-12)
+    rng = np.random.default_rng(5)
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1), (0, n - 1, 5), (n - 2, 3, n - 1), (255, 1, 510), (2, 300, 0)]
+    pts += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(18)]
+    h = 2 * math.pi / n
+    p = oracle_params(nx=w, ny=w, nz=w, lx=w * h, ly=w * h, lz=w * h, **phys)
+    scale = np.abs(q0.reshape(7, -1)).max(axis=1).astype(np.float64)
+    d = np.arange(-r, r + 1)
+    worst = 0.0
+    for (i, j, k) in pts:
+        win = q0[:, np.take(np.arange(n), k + d, mode="wrap")][:, :, np.take(np.arange(n), j + d, mode="wrap")][
+            :, :, :, np.take(np.arange(n), i + d, mode="wrap")]
+        qw = np.ascontiguousarray(win, dtype=np.float64)
+        O.run(p, qw, 1)
+        err = np.abs(got[:, k, j, i].astype(np.float64) - qw[:, r, r, r]) / scale
+        worst = max(worst, float(err.max()))
+        assert err.max() < 2e-5, ((i, j, k), err)
+    assert worst > 0.0
