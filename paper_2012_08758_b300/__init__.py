@@ -12,7 +12,7 @@ import of any binding name fails loudly if it is missing.
 from __future__ import annotations
 
 _BINDING_NAMES = {
-    "MhdError", "MhdParams", "lib", "mhd_default_params", "mhd_workspace_bytes", "mhd_create",
+    "MhdError", "MhdParams", "lib", "mhd_default_params", "mhd_resolve_params", "mhd_workspace_bytes", "mhd_create",
     "mhd_destroy", "mhd_set_state", "mhd_get_state", "mhd_step", "mhd_step_timed", "mhd_reduce", "mhd_diagnostics",
     "mhd_time", "mhd_sync", "mhd_forcing_draw", "mhd_eval_rhs", "mhd_eval_rhs_at", "mhd_last_error",
     "mhd_batch_create", "mhd_batch_step", "mhd_batch_destroy", "MHD_F32", "MHD_F64",

@@ -26,7 +26,7 @@ CANDIDATES = {
                 (B.MHD_KERNEL_TMA, 11), (B.MHD_KERNEL_TMA, 12), (B.MHD_KERNEL_TMA, 13), (B.MHD_KERNEL_TMA, 14),
                 (B.MHD_KERNEL_TMA, 15), (B.MHD_KERNEL_TMA, 16), (B.MHD_KERNEL_TMA, 17), (B.MHD_KERNEL_TMA, 18),
                 (B.MHD_KERNEL_TMA, 19), (B.MHD_KERNEL_TMA, 20), (B.MHD_KERNEL_TMA, 21), (B.MHD_KERNEL_TMA, 22), (B.MHD_KERNEL_TMA, 23), (B.MHD_KERNEL_TMA, 24),
-                (B.MHD_KERNEL_TMA, 25), (B.MHD_KERNEL_TMA, 26), (B.MHD_KERNEL_TMA, 27),
+                (B.MHD_KERNEL_TMA, 25), (B.MHD_KERNEL_TMA, 26), (B.MHD_KERNEL_TMA, 27), (B.MHD_KERNEL_TMA, 28),
                 (B.MHD_KERNEL_SMEM, 0)],
     B.MHD_F64: [(B.MHD_KERNEL_TMA, 1), (B.MHD_KERNEL_TMA, 2), (B.MHD_KERNEL_TMA, 3), (B.MHD_KERNEL_TMA, 4),
                 (B.MHD_KERNEL_SMEM, 0)],

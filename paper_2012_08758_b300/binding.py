@@ -58,6 +58,7 @@ def lib():
         dp = C.POINTER(C.c_double)
         sig = {
             "mhd_default_params": (None, [pp]),
+            "mhd_resolve_params": (C.c_int, [pp, pp]),
             "mhd_workspace_bytes": (C.c_int, [pp, C.POINTER(sz)]),
             "mhd_create": (C.c_int, [pp, vp, vp, sz, C.POINTER(vp)]),
             "mhd_destroy": (None, [vp]),
@@ -117,6 +118,13 @@ def mhd_default_params(**overrides) -> MhdParams:
             raise AttributeError(f"mhd_params has no field {k}")
         setattr(p, k, v)
     return p
+
+
+def mhd_resolve_params(p: MhdParams) -> MhdParams:
+    """p with the automatic kernel and tile choices made."""
+    out = MhdParams()
+    _check(lib().mhd_resolve_params(C.byref(p), C.byref(out)))
+    return out
 
 
 def mhd_workspace_bytes(p: MhdParams) -> int:

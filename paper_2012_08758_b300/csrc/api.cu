@@ -43,6 +43,7 @@ struct Layout {
   int nk;
   int tw, th;    // reduction tiles (prologue, diagnostics): block shape and TMA box of rmap
   int stw, sth;  // substep tiles: TMA box of tmap and the work split's columns
+  int wpairs;    // w's fields 0-5 in the interleaved layout of x2_w_pairs
   std::vector<Tile> tiles_host;
 };
 
@@ -273,7 +274,14 @@ int validate(const mhd_params *p, std::string *why) {
 mhd_params resolved(const mhd_params *p) {
   mhd_params r = *p;
   if (r.kernel == MHD_KERNEL_AUTO) r.kernel = MHD_KERNEL_TMA;
-  if (r.kernel == MHD_KERNEL_TMA && r.tile == 0) r.tile = r.dtype == MHD_F32 ? 26 : 3;
+  // FP32: the warp-specialised paired-point kernel; its interleaved-w form
+  // (tile 28) where the grid has more than two waves of 64 x 8 columns (the
+  // third substep reads that layout more slowly, which the 16-byte w stores
+  // of the first two outweigh only there, as measured at 256^3 - 1024^2 x 256)
+  if (r.kernel == MHD_KERNEL_TMA && r.tile == 0) {
+    const long long cols = (long long)((r.nx + 63) / 64) * ((r.ny + 7) / 8);
+    r.tile = r.dtype != MHD_F32 ? 3 : cols > 2LL * num_sms() ? 28 : 26;
+  }
   return r;
 }
 
@@ -309,17 +317,18 @@ int encode_state_map(CUtensorMap *m, void *base, size_t esz, int px, int py, int
   return encode_box_map(m, base, esz, px, py, pz, tw + 8, th + 2 * RAD, why);
 }
 
-int encode_box_map(CUtensorMap *m, void *base, size_t esz, int px, int py, int pz, int bx, int by,
-                   std::string *why) {
+// 4-D array (x: dx values, y: py, z: pz, then nf arrays fs values apart),
+// rows dx values apart; box bx x by x 1 x nf.
+int encode_map4(CUtensorMap *m, void *base, size_t esz, long long dx, int py, int pz, int nf, long long fs,
+                int bx, int by, std::string *why) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) {
     *why = "cuTensorMapEncodeTiled is not available from the driver";
     return MHD_ECUDA;
   }
-  const cuuint64_t dims[4] = {(cuuint64_t)px, (cuuint64_t)py, (cuuint64_t)pz, (cuuint64_t)NF};
-  const cuuint64_t strides[3] = {(cuuint64_t)px * esz, (cuuint64_t)px * py * esz,
-                                 (cuuint64_t)px * py * pz * esz};
-  const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1u, (cuuint32_t)NF};
+  const cuuint64_t dims[4] = {(cuuint64_t)dx, (cuuint64_t)py, (cuuint64_t)pz, (cuuint64_t)nf};
+  const cuuint64_t strides[3] = {(cuuint64_t)dx * esz, (cuuint64_t)dx * py * esz, (cuuint64_t)fs * esz};
+  const cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1u, (cuuint32_t)nf};
   const cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
   CUresult r = fn(m, esz == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, base,
                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -329,6 +338,23 @@ int encode_box_map(CUtensorMap *m, void *base, size_t esz, int px, int py, int p
     return MHD_ECUDA;
   }
   return MHD_OK;
+}
+
+int encode_box_map(CUtensorMap *m, void *base, size_t esz, int px, int py, int pz, int bx, int by,
+                   std::string *why) {
+  return encode_map4(m, base, esz, px, py, pz, NF, (long long)px * py * pz, bx, by, why);
+}
+
+// The w maps of the interleaved layout: fields 0-5 as three arrays (2 px
+// values per row, 2 fstride apart; box 2 tw x th), and field 6 (box tw x th).
+// Encoded for every FP32 run, so that a batch may step it with either layout.
+int encode_w_pair_maps(RunDesc *R, const Layout &L, std::string *why) {
+  char *w = static_cast<char *>(R->w);
+  if (int e = encode_map4(&R->wpmap[0], w, L.esz, 2LL * L.px, L.py, L.pz, 3, 2 * L.fstride, 2 * L.stw, L.sth,
+                          why))
+    return e;
+  return encode_map4(&R->wpmap[1], w + (size_t)6 * L.fstride * L.esz, L.esz, L.px, L.py, L.pz, 1, L.fstride,
+                     L.stw, L.sth, why);
 }
 
 Layout make_layout(const mhd_params *p_in) {
@@ -342,6 +368,7 @@ Layout make_layout(const mhd_params *p_in) {
   L.fstride = (long long)L.px * L.py * L.pz;
   L.nk = p->f0 > 0 ? shell_vectors(p->kmin, p->kmax, nullptr) : 0;
   substep_tile_shape(p->dtype, p->kernel, p->tile, &L.stw, &L.sth);
+  L.wpairs = p->dtype == MHD_F32 && p->kernel == MHD_KERNEL_TMA && x2_w_pairs(p->tile);
   reduction_tile_shape(p->dtype, p->kernel, p->tile, &L.tw, &L.th);
   // The tile table is a function of the parameters alone (not of the device
   // it runs on), so per-tile reduction partials -- and hence every reduced
@@ -397,6 +424,7 @@ struct mhd_ctx {
   Tile *d_sub;  // substep work split (split_columns) and its grid
   int nsub, sub_grid;
   int iso;   // equal grid spacings on all axes
+  bool tile_auto;  // the tile was chosen by resolved() (mhd_params.tile == 0)
   std::string err;
   cufftHandle fft = 0;  // spectrum plan, made by the first mhd_spectrum call
   bool fft_made = false;
@@ -508,7 +536,7 @@ int download_fields(mhd_ctx *ctx, const char *dev, int host_dtype, char *host, s
       c3.kind = cudaMemcpyDeviceToHost;
       CK(ctx, cudaMemcpy3DAsync(&c3, s));
     } else {
-      CK(ctx, launch_get_field(ctx->p.dtype, host_dtype, field, R.w, R.nx, R.ny, R.nz, R.px, R.py, s));
+      CK(ctx, launch_get_field(ctx->p.dtype, host_dtype, field, R.w, R.nx, R.ny, R.nz, R.px, R.py, 0, s));
       CK(ctx, cudaMemcpyAsync(out, R.w, hb, cudaMemcpyDeviceToHost, s));
     }
   }
@@ -541,6 +569,14 @@ void mhd_default_params(mhd_params *p) {
   p->tile = 0;
 }
 
+int mhd_resolve_params(const mhd_params *p, mhd_params *out) {
+  std::string why;
+  if (validate(p, &why)) return fail(nullptr, MHD_EINVAL, "%s", why.c_str());
+  if (!out) return fail(nullptr, MHD_EINVAL, "out is NULL");
+  *out = resolved(p);
+  return MHD_OK;
+}
+
 int mhd_workspace_bytes(const mhd_params *p, size_t *bytes) {
   std::string why;
   if (validate(p, &why)) return fail(nullptr, MHD_EINVAL, "%s", why.c_str());
@@ -557,6 +593,7 @@ int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t worksp
   if (validate(p, &why)) return fail(nullptr, MHD_EINVAL, "%s", why.c_str());
   mhd_ctx *ctx = new mhd_ctx();
   ctx->p = resolved(p);
+  ctx->tile_auto = p->tile == 0;
   p = &ctx->p;
   ctx->stream = static_cast<cudaStream_t>(stream);
   ctx->L = make_layout(p);
@@ -635,7 +672,8 @@ int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t worksp
     for (int b = 0; b < 2; ++b)
       if (encode_state_map(&R.tmap[b], R.q[b], L.esz, L.px, L.py, L.pz, L.stw, L.sth, &why) ||
           encode_state_map(&R.rmap[b], R.q[b], L.esz, L.px, L.py, L.pz, L.tw, L.th, &why) ||
-          (b == 0 && encode_box_map(&R.wmap, R.w, L.esz, L.px, L.py, L.pz, L.stw, L.sth, &why))) {
+          (b == 0 && encode_box_map(&R.wmap, R.w, L.esz, L.px, L.py, L.pz, L.stw, L.sth, &why)) ||
+          (b == 0 && L.esz == 4 && encode_w_pair_maps(&R, L, &why))) {
         fail(ctx, MHD_ECUDA, "%s", why.c_str());
         return cleanup(MHD_ECUDA);
       }
@@ -1059,10 +1097,13 @@ int mhd_eval_rhs(mhd_ctx *ctx, int64_t step, double dt_forcing, void *host_rhs, 
                          ctx->nsub, 0, ctx->sub_grid, ctx->iso, s));
   const size_t npts = (size_t)R.nx * R.ny * R.nz, hb = npts * host_esz(host_dtype);
   void *staging = R.q[par ^ 1];
+  const bool pairs = ctx->L.wpairs;
   for (int f = 0; f < NF; ++f) {
-    CK(ctx, launch_get_field(ctx->p.dtype, host_dtype,
-                             static_cast<const char *>(R.w) + (size_t)f * R.fstride * ctx->L.esz,
-                             staging, R.nx, R.ny, R.nz, R.px, R.py, s));
+    // field f of w: interleaved array f / 2 from its value 2 (f % 2) on, or field f
+    const bool pf = pairs && f < 6;
+    const size_t at = pf ? (size_t)(f >> 1) * 2 * R.fstride + 2 * (f & 1) : (size_t)f * R.fstride;
+    CK(ctx, launch_get_field(ctx->p.dtype, host_dtype, static_cast<const char *>(R.w) + at * ctx->L.esz,
+                             staging, R.nx, R.ny, R.nz, R.px, R.py, pf ? 1 : 0, s));
     CK(ctx, cudaMemcpyAsync(static_cast<char *>(host_rhs) + f * hb, staging, hb,
                             cudaMemcpyDeviceToHost, s));
   }
@@ -1104,7 +1145,7 @@ int mhd_eval_rhs_at(mhd_ctx *ctx, int64_t step, double dt_forcing, int npts, con
   int *d_ijk = reinterpret_cast<int *>(staging);
   double *d_out = reinterpret_cast<double *>(staging + ijk_bytes);
   CK(ctx, cudaMemcpyAsync(d_ijk, ijk, (size_t)3 * npts * sizeof(int), cudaMemcpyHostToDevice, s));
-  CK(ctx, launch_gather_points(ctx->p.dtype, R.w, R.fstride, R.px, R.py, d_ijk, npts, d_out, s));
+  CK(ctx, launch_gather_points(ctx->p.dtype, R.w, R.fstride, R.px, R.py, d_ijk, npts, d_out, ctx->L.wpairs, s));
   CK(ctx, cudaMemcpyAsync(host_out, d_out, (size_t)NF * npts * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(ctx, cudaMemsetAsync(staging, 0xFF, (size_t)NF * R.fstride * ctx->L.esz, s));
   CK(ctx, cudaStreamSynchronize(s));
@@ -1127,11 +1168,22 @@ int mhd_batch_create(mhd_ctx *const *runs, int nruns, mhd_batch **out) {
   std::vector<RunDesc> descs;
   std::vector<Tile> tiles;
   double cells_total = 0;
+  // Runs whose FP32 paired-point tile was chosen automatically (26 or 28,
+  // the two w layouts of one kernel) are stepped with the choice for the
+  // batch's combined columns: w is dead between steps and every such run
+  // carries the tensor maps of both layouts.
+  bool auto_x2 = true;
+  long long cols_total = 0;
   for (int i = 0; i < nruns; ++i) {
     mhd_ctx *r = runs[i];
     if (!r) return fail(nullptr, MHD_EINVAL, "runs[%d] is NULL", i);
+    auto_x2 = auto_x2 && r->tile_auto && (r->p.tile == 26 || r->p.tile == 28);
+    cols_total += (long long)((r->p.nx + 63) / 64) * ((r->p.ny + 7) / 8);
+  }
+  for (int i = 0; i < nruns; ++i) {
+    mhd_ctx *r = runs[i];
     if (r->p.dtype != r0->p.dtype || r->stream != r0->stream || r->p.kernel != r0->p.kernel ||
-        r->p.tile != r0->p.tile)
+        (r->p.tile != r0->p.tile && !auto_x2))
       return fail(nullptr, MHD_EINVAL,
                   "runs of a batch must share dtype, stream, kernel and tile");
     for (int j = 0; j < i; ++j)
@@ -1164,7 +1216,7 @@ int mhd_batch_create(mhd_ctx *const *runs, int nruns, mhd_batch **out) {
   b->stream = r0->stream;
   b->dtype = r0->p.dtype;
   b->kernel = r0->p.kernel;
-  b->tile = r0->p.tile;
+  b->tile = auto_x2 ? (cols_total > 2LL * num_sms() ? 28 : 26) : r0->p.tile;
   b->tw = r0->L.tw;
   b->th = r0->L.th;
   b->ntiles = (int)tiles.size();

@@ -359,31 +359,37 @@ __global__ void k_set_field(const H *src, T *dst, int nx, int ny, int nz, int px
 
 template <typename T>
 __global__ void k_gather_points(const T *q, long long fstride, int px, int py, const int *ijk, int npts,
-                                double *out) {
+                                double *out, int wpairs) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= npts) return;
   const long long c = ((long long)(ijk[3 * n + 2] + OZ) * py + (ijk[3 * n + 1] + OY)) * px + (ijk[3 * n] + OX);
-  for (int f = 0; f < NF; ++f) out[(long long)NF * n + f] = (double)q[f * fstride + c];
+  for (int f = 0; f < NF; ++f) {
+    const long long at =
+        wpairs && f < 6 ? (long long)(f >> 1) * 2 * fstride + 4 * (c >> 1) + 2 * (f & 1) + (c & 1) : f * fstride + c;
+    out[(long long)NF * n + f] = (double)q[at];
+  }
 }
 
 int launch_gather_points(int dtype, const void *q, long long fstride, int px, int py, const int *ijk, int npts,
-                         double *out, cudaStream_t s) {
+                         double *out, int wpairs, cudaStream_t s) {
   const int grid = (npts + 255) / 256;
   if (dtype == 0)
-    k_gather_points<float><<<grid, 256, 0, s>>>(static_cast<const float *>(q), fstride, px, py, ijk, npts, out);
+    k_gather_points<float><<<grid, 256, 0, s>>>(static_cast<const float *>(q), fstride, px, py, ijk, npts, out,
+                                                 wpairs);
   else
     k_gather_points<double><<<grid, 256, 0, s>>>(static_cast<const double *>(q), fstride, px, py, ijk, npts,
-                                                  out);
+                                                  out, wpairs);
   return (int)cudaGetLastError();
 }
 
 template <typename T, typename H>
-__global__ void k_get_field(const T *src, H *dst, int nx, int ny, int nz, int px, int py) {
+__global__ void k_get_field(const T *src, H *dst, int nx, int ny, int nz, int px, int py, int pairs) {
   const long long total = (long long)nx * ny * nz;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / ((long long)nx * ny));
-    dst[e] = H(src[((long long)(k + OZ) * py + (j + OY)) * px + (i + OX)]);
+    const long long c = ((long long)(k + OZ) * py + (j + OY)) * px + (i + OX);
+    dst[e] = H(src[pairs ? 4 * (c >> 1) + (c & 1) : c]);
   }
 }
 
@@ -482,16 +488,20 @@ int launch_padding_check(int dtype, const void *q, int nf, long long fstride, in
 }
 
 int launch_get_field(int dtype, int host_dtype, const void *src_field, void *dst, int nx, int ny,
-                     int nz, int px, int py, cudaStream_t s) {
+                     int nz, int px, int py, int pairs, cudaStream_t s) {
   const int g = conv_grid((long long)nx * ny * nz);
   if (dtype == 0 && host_dtype == 0)
-    k_get_field<float, float><<<g, 256, 0, s>>>((const float *)src_field, (float *)dst, nx, ny, nz, px, py);
+    k_get_field<float, float><<<g, 256, 0, s>>>((const float *)src_field, (float *)dst, nx, ny, nz, px, py,
+                                                pairs);
   else if (dtype == 0)
-    k_get_field<float, double><<<g, 256, 0, s>>>((const float *)src_field, (double *)dst, nx, ny, nz, px, py);
+    k_get_field<float, double><<<g, 256, 0, s>>>((const float *)src_field, (double *)dst, nx, ny, nz, px, py,
+                                                 pairs);
   else if (host_dtype == 0)
-    k_get_field<double, float><<<g, 256, 0, s>>>((const double *)src_field, (float *)dst, nx, ny, nz, px, py);
+    k_get_field<double, float><<<g, 256, 0, s>>>((const double *)src_field, (float *)dst, nx, ny, nz, px, py,
+                                                 pairs);
   else
-    k_get_field<double, double><<<g, 256, 0, s>>>((const double *)src_field, (double *)dst, nx, ny, nz, px, py);
+    k_get_field<double, double><<<g, 256, 0, s>>>((const double *)src_field, (double *)dst, nx, ny, nz, px, py,
+                                                  pairs);
   return (int)cudaGetLastError();
 }
 

@@ -235,9 +235,22 @@ static_assert(12 * 32 * X2_WS_LAUNCH_REGS == 8 * 32 * X2_WS_COMPUTE_REGS + 4 * 3
 // points of one z-plane of the tile, all fields; substeps 2 and 3 read w
 // through it instead of from global memory); then the mbarriers (full /
 // empty per stage of each ring).
+//
+// A w stage holds the seven fields' TY x 64 values.  Variants with the WP
+// layout instead keep w's fields 0-5 as three interleaved arrays, m = 0..2,
+// each 2 fstride values from 2 m fstride on: the points (2j, 2j+1) of fields
+// 2m and 2m+1 are the four values 4j .. 4j+3 (field 2m at both points, then
+// field 2m+1), field 6 as usual; a thread writes and reads its two points of
+// a field pair as one 16-byte access, and a w stage holds the three arrays'
+// TY x 128 values, then field 6's TY x 64.  (The second substep updates w in
+// place, so every substep of a run uses the one layout.)
 template <int TY>
 __host__ __device__ constexpr int x2_wstage_bytes() {
   return NF * TY * 64 * (int)sizeof(float);
+}
+template <int TY>
+__host__ __device__ constexpr int x2_wpair_bytes() {
+  return 3 * TY * 128 * (int)sizeof(float);
 }
 template <int TY, int NS, int NW>
 __host__ __device__ constexpr int x2_ws_bytes() {
@@ -265,7 +278,7 @@ namespace {
 // slot gw mod NW, once w plane gw - NW has been released (D = NS - 3 - NW
 // keeps at most NW w planes in flight; the last D of a tile follow its last
 // lead plane).
-template <int TY, int NS, int SUB, bool WT>
+template <int TY, int NS, int SUB, bool WT, bool WP>
 __device__ __forceinline__ void x2_produce(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles,
                                            int ntiles, unsigned char *smem, uint64_t *full, uint64_t *empty,
                                            unsigned char *wst, uint64_t *wfull, uint64_t *wempty,
@@ -284,8 +297,15 @@ __device__ __forceinline__ void x2_produce(const RunDesc *__restrict__ runs, con
     auto issue_w = [&](int o) {
       const int ws = (int)(gw % NW);
       if ((gw >= NW && !mbar_wait(&wempty[ws], (uint32_t)(((gw / NW) - 1) & 1ull))) || *abort) return false;
+      unsigned char *dst = wst + ws * x2_wstage_bytes<TY>();
       mbar_arrive_expect_tx(&wfull[ws], (uint32_t)x2_wstage_bytes<TY>());
-      tma_load_4d(wst + ws * x2_wstage_bytes<TY>(), &R.wmap, &wfull[ws], tile.x0 + OX, tile.y0 + OY, tile.z0 + o, 0);
+      if constexpr (WP) {
+        tma_load_4d(dst, &R.wpmap[0], &wfull[ws], 2 * (tile.x0 + OX), tile.y0 + OY, tile.z0 + o, 0);
+        tma_load_4d(dst + x2_wpair_bytes<TY>(), &R.wpmap[1], &wfull[ws], tile.x0 + OX, tile.y0 + OY, tile.z0 + o,
+                    0);
+      } else {
+        tma_load_4d(dst, &R.wmap, &wfull[ws], tile.x0 + OX, tile.y0 + OY, tile.z0 + o, 0);
+      }
       ++gw;
       return true;
     };
@@ -327,7 +347,7 @@ __device__ __forceinline__ void x2_produce(const RunDesc *__restrict__ runs, con
 // SUB: the RK substep (0, 1, 2), a compile-time constant so that each
 // instantiation carries only its own w traffic (none read at 0, none written
 // at 2) and its own RK coefficients.
-template <int TY, int NS, int BAR, bool ISO, int SUB, bool WS>
+template <int TY, int NS, int BAR, bool ISO, int SUB, bool WS, bool WP>
 __global__ void __launch_bounds__(32 * TY + (WS ? 128 : 0), 1)
     k_substep_x2(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles, int ntiles) {
   constexpr int substep = SUB;
@@ -345,6 +365,7 @@ __global__ void __launch_bounds__(32 * TY + (WS ? 128 : 0), 1)
   constexpr bool WTL = WS && x2_wring<TY, NS>() > 0;
   constexpr bool WT = WTL && SUB > 0;
   constexpr int NW = WTL ? x2_wring<TY, NS>() : 1;
+  static_assert(!WP || WTL, "the interleaved w layout is read through the w ring");
   unsigned char *wst = smem + NS * SH::STAGE_BYTES;
   uint64_t *bars = reinterpret_cast<uint64_t *>(wst + (WTL ? NW * x2_wstage_bytes<TY>() : 0));
   uint64_t *wfull = bars + 2 * NS, *wempty = bars + 2 * NS + NW;
@@ -367,7 +388,7 @@ __global__ void __launch_bounds__(32 * TY + (WS ? 128 : 0), 1)
     if (ty >= TY) {
       asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(X2_WS_PRODUCER_REGS));
       if (ty == TY && tx == 0)
-        x2_produce<TY, NS, SUB, WT>(runs, tiles, ntiles, smem, bars, bars + NS, wst, wfull, wempty, &ws_abort);
+        x2_produce<TY, NS, SUB, WT, WP>(runs, tiles, ntiles, smem, bars, bars + NS, wst, wfull, wempty, &ws_abort);
       return;
     }
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(X2_WS_COMPUTE_REGS));
@@ -683,9 +704,19 @@ __global__ void __launch_bounds__(32 * TY + (WS ? 128 : 0), 1)
               ws_abort = 1;
               atomicOr(&R.clock->status, 2);
             }
-            const float *wr = reinterpret_cast<const float *>(wst + ws * x2_wstage_bytes<TY>()) + ty * 64 + 2 * tx;
+            const float *wr = reinterpret_cast<const float *>(wst + ws * x2_wstage_bytes<TY>());
+            if constexpr (WP) {
 #pragma unroll
-            for (int f = 0; f < NF; ++f) wc[f] = ld2(wr + f * TY * 64);
+              for (int m = 0; m < 3; ++m) {
+                const float4 v = *reinterpret_cast<const float4 *>(wr + (m * TY + ty) * 128 + 4 * tx);
+                wc[2 * m] = make_float2(v.x, v.y);
+                wc[2 * m + 1] = make_float2(v.z, v.w);
+              }
+              wc[6] = ld2(wr + 3 * TY * 128 + ty * 64 + 2 * tx);
+            } else {
+#pragma unroll
+              for (int f = 0; f < NF; ++f) wc[f] = ld2(wr + (f * TY + ty) * 64 + 2 * tx);
+            }
             __syncwarp();
             if (tx == 0) mbar_arrive(&wempty[ws]);
             ++gwc;
@@ -704,17 +735,33 @@ __global__ void __launch_bounds__(32 * TY + (WS ? 128 : 0), 1)
             const bool zn = z < RAD || z >= nz - RAD;
             const bool near0 = edge0 || zn, near1 = edge1 || zn;
             if (act1 && !near0 && !near1) {
+              if constexpr (SUB < 2 && WP) {
+                float *wb = w + 2 * cidx;
+#pragma unroll
+                for (int m = 0; m < 3; ++m)
+                  __stcs(reinterpret_cast<float4 *>(wb + 2 * m * fs),
+                         make_float4(wv[2 * m].x, wv[2 * m].y, wv[2 * m + 1].x, wv[2 * m + 1].y));
+                __stcs(reinterpret_cast<float2 *>(w + cidx + 6 * fs), wv[6]);
+              }
               float *wp = w + cidx, *qp = qout + cidx;
 #pragma unroll
               for (int f = 0; f < NF; ++f, wp += fs, qp += fs) {
-                if constexpr (SUB < 2) __stcs(reinterpret_cast<float2 *>(wp), wv[f]);
+                if constexpr (SUB < 2 && !WP) __stcs(reinterpret_cast<float2 *>(wp), wv[f]);
                 __stcs(reinterpret_cast<float2 *>(qp), qn[f]);
               }
             } else if (act1 && shift_images) {
+              if constexpr (SUB < 2 && WP) {
+                float *wb = w + 2 * cidx;
+#pragma unroll
+                for (int m = 0; m < 3; ++m)
+                  __stcs(reinterpret_cast<float4 *>(wb + 2 * m * fs),
+                         make_float4(wv[2 * m].x, wv[2 * m].y, wv[2 * m + 1].x, wv[2 * m + 1].y));
+                __stcs(reinterpret_cast<float2 *>(w + cidx + 6 * fs), wv[6]);
+              }
               float *wp = w + cidx, *qp = qout + cidx;
 #pragma unroll
               for (int f = 0; f < NF; ++f, wp += fs, qp += fs) {
-                if constexpr (SUB < 2) __stcs(reinterpret_cast<float2 *>(wp), wv[f]);
+                if constexpr (SUB < 2 && !WP) __stcs(reinterpret_cast<float2 *>(wp), wv[f]);
                 __stcs(reinterpret_cast<float2 *>(qp), qn[f]);
               }
               {
@@ -752,8 +799,13 @@ __global__ void __launch_bounds__(32 * TY + (WS ? 128 : 0), 1)
                 q0[f] = qn[f].x;
                 q1[f] = qn[f].y;
                 if constexpr (SUB < 2) {
-                  __stcs(w + cidx + f * fs, wv[f].x);
-                  if (act1) __stcs(w + cidx + 1 + f * fs, wv[f].y);
+                  // field f of padded point i: interleaved array f / 2 (WP, f < 6) or field f
+                  auto wi = [&](long long i) {
+                    return WP && f < 6 ? (long long)(f >> 1) * 2 * fs + 4 * (i >> 1) + 2 * (f & 1) + (i & 1)
+                                        : f * fs + i;
+                  };
+                  __stcs(w + wi(cidx), wv[f].x);
+                  if (act1) __stcs(w + wi(cidx + 1), wv[f].y);
                 }
               }
               store_with_images<float, true>(qout, fs, cidx, q0, near0, x, y, z, nx, ny, nz, px, py, zper);
@@ -838,8 +890,18 @@ __global__ void __launch_bounds__(32 * TY + (WS ? 128 : 0), 1)
 
 // Tile rows of a paired-point variant (0 if `tile` is not one).
 int x2_rows(int tile) {
-#define X(ID, TY, NS, BR, WS) \
+#define X(ID, TY, NS, BR, WS, WP) \
   if (tile == ID) return TY;
+  MHD_X2_VARIANTS(X)
+#undef X
+  return 0;
+}
+
+// 1 if the variant keeps w's fields 0-5 in the interleaved layout (WP), 0
+// otherwise.
+int x2_w_pairs(int tile) {
+#define X(ID, TY, NS, BR, WS, WP) \
+  if (tile == ID) return WP;
   MHD_X2_VARIANTS(X)
 #undef X
   return 0;
@@ -847,16 +909,16 @@ int x2_rows(int tile) {
 
 int x2_prepare(int tile) {
   int e = (int)cudaErrorInvalidValue;
-#define X(ID, TY, NS, BR, WS)                                                                              \
-  if (tile == ID) {                                                                                        \
-    const int sm = x2_smem_bytes<TY, NS, WS>();                                                            \
-    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;                               \
-    e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, true, 0, WS>, a, sm);                           \
-    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, true, 1, WS>, a, sm);                   \
-    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, true, 2, WS>, a, sm);                   \
-    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, false, 0, WS>, a, sm);                  \
-    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, false, 1, WS>, a, sm);                  \
-    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, false, 2, WS>, a, sm);                  \
+#define X(ID, TY, NS, BR, WS, WP)                                                             \
+  if (tile == ID) {                                                                           \
+    const int sm = x2_smem_bytes<TY, NS, WS>();                                               \
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;                  \
+    e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, true, 0, WS, WP>, a, sm);          \
+    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, true, 1, WS, WP>, a, sm);  \
+    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, true, 2, WS, WP>, a, sm);  \
+    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, false, 0, WS, WP>, a, sm); \
+    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, false, 1, WS, WP>, a, sm); \
+    if (!e) e = (int)cudaFuncSetAttribute(k_substep_x2<TY, NS, BR, false, 2, WS, WP>, a, sm); \
   }
   MHD_X2_VARIANTS(X)
 #undef X
@@ -864,10 +926,10 @@ int x2_prepare(int tile) {
 }
 
 int x2_occupancy(int tile, int *bps) {
-#define X(ID, TY, NS, BR, WS)                                                                                \
-  if (tile == ID)                                                                                            \
-    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_substep_x2<TY, NS, BR, true, 1, WS>,    \
-                                                              32 * TY + (WS ? 128 : 0),                      \
+#define X(ID, TY, NS, BR, WS, WP)                                                                             \
+  if (tile == ID)                                                                                             \
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_substep_x2<TY, NS, BR, true, 1, WS, WP>, \
+                                                              32 * TY + (WS ? 128 : 0),                       \
                                                               x2_smem_bytes<TY, NS, WS>());
   MHD_X2_VARIANTS(X)
 #undef X
@@ -875,16 +937,16 @@ int x2_occupancy(int tile, int *bps) {
 }
 
 namespace {
-template <int TY, int NS, int BR, bool ISO, bool WS>
+template <int TY, int NS, int BR, bool ISO, bool WS, bool WP>
 void x2_go(const RunDesc *runs, const Tile *tiles, int ntiles, int substep, int grid, cudaStream_t s) {
   const dim3 block(32, TY + (WS ? 4 : 0));
   const int sm = x2_smem_bytes<TY, NS, WS>();
   if (substep == 0)
-    k_substep_x2<TY, NS, BR, ISO, 0, WS><<<grid, block, sm, s>>>(runs, tiles, ntiles);
+    k_substep_x2<TY, NS, BR, ISO, 0, WS, WP><<<grid, block, sm, s>>>(runs, tiles, ntiles);
   else if (substep == 1)
-    k_substep_x2<TY, NS, BR, ISO, 1, WS><<<grid, block, sm, s>>>(runs, tiles, ntiles);
+    k_substep_x2<TY, NS, BR, ISO, 1, WS, WP><<<grid, block, sm, s>>>(runs, tiles, ntiles);
   else
-    k_substep_x2<TY, NS, BR, ISO, 2, WS><<<grid, block, sm, s>>>(runs, tiles, ntiles);
+    k_substep_x2<TY, NS, BR, ISO, 2, WS, WP><<<grid, block, sm, s>>>(runs, tiles, ntiles);
 }
 }  // namespace
 
@@ -893,13 +955,13 @@ int x2_launch(int tile, const RunDesc *runs, const Tile *tiles, int ntiles, int 
   if (grid <= 0 || grid > ntiles) grid = ntiles;
   if (grid == 0) return 0;
   if (substep < 0 || substep > 2) return (int)cudaErrorInvalidValue;
-#define X(ID, TY, NS, BR, WS)                                              \
-  if (tile == ID) {                                                        \
-    if (iso)                                                               \
-      x2_go<TY, NS, BR, true, WS>(runs, tiles, ntiles, substep, grid, s);  \
-    else                                                                   \
-      x2_go<TY, NS, BR, false, WS>(runs, tiles, ntiles, substep, grid, s); \
-    return (int)cudaGetLastError();                                        \
+#define X(ID, TY, NS, BR, WS, WP)                                              \
+  if (tile == ID) {                                                            \
+    if (iso)                                                                   \
+      x2_go<TY, NS, BR, true, WS, WP>(runs, tiles, ntiles, substep, grid, s);  \
+    else                                                                       \
+      x2_go<TY, NS, BR, false, WS, WP>(runs, tiles, ntiles, substep, grid, s); \
+    return (int)cudaGetLastError();                                            \
   }
   MHD_X2_VARIANTS(X)
 #undef X

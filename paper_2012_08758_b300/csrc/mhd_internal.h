@@ -52,8 +52,10 @@ struct RunDesc {
                             // of a substep tile with its halo
   CUtensorMap rmap[2];      // the same for the reduction tiles (step prologue, B_rms sweep);
                             // equal to tmap unless the substep tile is wider
-  CUtensorMap wmap;         // TMA map of w: box of the substep tile's interior points of one
-                            // z-plane, all fields (warp-specialised paired kernel)
+  CUtensorMap wmap;         // TMA maps of w for the paired variants with a w ring; boxes: the
+  CUtensorMap wpmap[2];     // substep tile's interior points of one z-plane.  wmap: all fields;
+                            // wpmap (variants with the layout of x2_w_pairs): fields 0-5 as
+                            // (2 px, py, pz, array), and field 6
   int nx, ny, nz;
   int px, py, pz;           // padded extents; px is the row pitch
   long long fstride;        // elements per field (px * py * pz)
@@ -124,6 +126,10 @@ int tma_launch(int dtype, int tile, const RunDesc *runs, const Tile *tiles, int 
 // Paired-point FP32 substep variants (kernels_x2.cu): x2_rows(tile) is the
 // tile's row count (0: not such a variant); tiles are 64 points wide.
 int x2_rows(int tile);
+// 1 if the variant keeps w's fields 0-5 as three interleaved arrays (field
+// 2m + c of padded point i at w[2 m fstride + 4 (i / 2) + 2 c + i % 2]), 0
+// otherwise
+int x2_w_pairs(int tile);
 int x2_prepare(int tile);
 int x2_occupancy(int tile, int *bps);
 int x2_launch(int tile, const RunDesc *runs, const Tile *tiles, int ntiles, int substep, int grid, int iso,
@@ -139,11 +145,15 @@ int launch_seed_field(int dtype, void *A, long long fstride, int nx, int ny, int
                       unsigned long long seed, double amp, cudaStream_t s);
 int launch_set_field(int dtype, int host_dtype, const void *src, void *dst_field, int nx, int ny,
                      int nz, int px, int py, cudaStream_t s);
-// out[7 n + f] = field f of the NF-field array q at padded point of ijk[3n ..]
+// out[7 n + f] = field f of the NF-field array q at padded point of ijk[3n ..];
+// wpairs: q's fields 0-5 are in the interleaved layout of x2_w_pairs
 int launch_gather_points(int dtype, const void *q, long long fstride, int px, int py, const int *ijk, int npts,
-                         double *out, cudaStream_t s);
+                         double *out, int wpairs, cudaStream_t s);
+// dense copy of a padded field whose padded point i is src_field[i], or
+// (pairs) src_field[4 (i / 2) + i % 2]: one field of x2_w_pairs' layout, with
+// src_field at its array's first value of that field
 int launch_get_field(int dtype, int host_dtype, const void *src_field, void *dst, int nx, int ny,
-                     int nz, int px, int py, cudaStream_t s);
+                     int nz, int px, int py, int pairs, cudaStream_t s);
 // B_rms of the run's current state into diag[1] (curl and sum in one pass)
 int launch_brms(int dtype, const RunDesc *run_dev, const Tile *tiles, int ntiles, int tw, int th,
                 cudaStream_t s);

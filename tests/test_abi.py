@@ -68,11 +68,11 @@ def test_workspace_bytes_scale_with_grid(B):
     assert 1.9 < dbl / big < 2.01 and big > small
 
 
-@pytest.mark.parametrize("dtype,tiles", [(0, range(0, 28)), (1, range(0, 5))])
+@pytest.mark.parametrize("dtype,tiles", [(0, range(0, 29)), (1, range(0, 5))])
 def test_every_tile_variant_is_accepted(B, dtype, tiles):
-    """FP32 TMA tiles 1-27 (shapes, stage counts, barrier spacings, packed
-    pairs, paired points) and FP64 tiles 1-4, and 0 for the default, are
-    valid parameters."""
+    """FP32 TMA tiles 1-28 (shapes, stage counts, barrier spacings, packed
+    pairs, paired points, w layouts) and FP64 tiles 1-4, and 0 for the
+    default, are valid parameters."""
     for t in tiles:
         assert B.mhd_workspace_bytes(B.mhd_default_params(nx=40, ny=24, nz=16, kernel=2, tile=t, dtype=dtype)) > 0
 
@@ -82,7 +82,7 @@ def test_every_tile_variant_is_accepted(B, dtype, tiles):
     (dict(f0=0.1, kmin=0.0), "shell"), (dict(f0=0.1, kmin=0.2, kmax=0.5), "no integer"),
     (dict(f0=0.1, sigma=1.5), "sigma"), (dict(dtype=7), "dtype"), (dict(forcing_mode=3), "forcing_mode"), (dict(upwind=2), "upwind"),
     (dict(cfl=0.0), "cfl"), (dict(kernel=99), "kernel"),
-    (dict(kernel=2, tile=28), "tile"), (dict(kernel=2, tile=6, dtype=1), "tile"), (dict(kernel=1, tile=3), "tile"),
+    (dict(kernel=2, tile=29), "tile"), (dict(kernel=2, tile=6, dtype=1), "tile"), (dict(kernel=1, tile=3), "tile"),
 ])
 def test_invalid_parameters_are_rejected(B, bad, msg):
     with pytest.raises(B.MhdError) as e:
@@ -116,7 +116,7 @@ def test_seed_field_rejects_null_context(B):
 @pytest.mark.parametrize("shape,grid", [((256, 256, 256), 148), ((512, 512, 512), 148), ((64, 64, 64), 148),
                                         ((37, 23, 11), 148), ((1, 1, 1), 148), ((45, 37, 29), 444),
                                         ((256, 96, 40), 296), ((300, 200, 100), 148), ((256, 240, 128), 148)])
-@pytest.mark.parametrize("tile", [0, 2, 4, 5, 9, 16, 17, 19, 20, 25])
+@pytest.mark.parametrize("tile", [0, 2, 4, 5, 9, 16, 17, 19, 20, 25, 28])
 def test_substep_plan_covers_every_point_once(B, shape, grid, tile):
     """The work split of the fused substep: every (x-y tile, z) of the grid
     exactly once, table rectangular over the CTAs it uses, whole columns
@@ -125,10 +125,11 @@ def test_substep_plan_covers_every_point_once(B, shape, grid, tile):
     p = B.mhd_default_params(nx=nx, ny=ny, nz=nz, kernel=B.MHD_KERNEL_TMA, tile=tile)
     tiles, g = B.mhd_substep_plan(p, grid)
     assert 1 <= g <= grid and len(tiles) % g == 0
-    # tile 0: the warp-specialised paired-point tile 26 (64 x 8 columns)
-    res = tile if tile else 26
+    # tile 0: the warp-specialised paired-point tile 26 or 28 (64 x 8 columns)
+    res = B.mhd_resolve_params(p).tile
+    assert res == tile or (tile == 0 and res in (26, 28))
     tw = 64 if res >= 17 else 32
-    th = {2: 4, 4: 12, 5: 12, 9: 6, 13: 12, 16: 12, 17: 8, 18: 8, 19: 4, 20: 6, 22: 8, 25: 8, 26: 8}[res]
+    th = {2: 4, 4: 12, 5: 12, 9: 6, 13: 12, 16: 12, 17: 8, 18: 8, 19: 4, 20: 6, 22: 8, 25: 8, 26: 8, 28: 8}[res]
     seen = {}
     for x0, y0, z0, z1, run in tiles:
         assert run == 0
@@ -165,6 +166,25 @@ def test_paired_split_uses_whole_columns_for_one_or_two_full_waves(B, shape, gri
     assert whole == (expect < grid or (nx // 64) * (ny // 8) == grid)
     if expect < grid:
         assert len(real) == (nx // 64) * (ny // 8)
+
+
+@pytest.mark.parametrize("shape,expect", [((256, 256, 256), 26), ((320, 320, 320), 26), ((384, 384, 384), 26),
+                                          ((384, 392, 64), 26), ((384, 400, 64), 28), ((448, 448, 448), 28),
+                                          ((512, 512, 512), 28), ((1024, 1024, 256), 28), ((33, 17, 9), 26)])
+def test_default_fp32_tile_follows_the_column_count(B, shape, expect):
+    """Automatic tile: FP32 takes the paired-point kernel, in its
+    interleaved-w form (tile 28) only with more than two waves of 64 x 8
+    columns over 148 SMs (384 x 392: 6 x 49 = 294 columns; 384 x 400: 300);
+    FP64 takes tile 3; an explicit tile is kept."""
+    nx, ny, nz = shape
+    r = B.mhd_resolve_params(B.mhd_default_params(nx=nx, ny=ny, nz=nz))
+    assert (r.kernel, r.tile) == (B.MHD_KERNEL_TMA, expect)
+    r = B.mhd_resolve_params(B.mhd_default_params(nx=nx, ny=ny, nz=nz, dtype=B.MHD_F64))
+    assert (r.kernel, r.tile) == (B.MHD_KERNEL_TMA, 3)
+    r = B.mhd_resolve_params(B.mhd_default_params(nx=nx, ny=ny, nz=nz, kernel=B.MHD_KERNEL_TMA, tile=26))
+    assert r.tile == 26
+    with pytest.raises(B.MhdError):
+        B.mhd_resolve_params(B.mhd_default_params(nx=0))
 
 
 def test_padding_check_rejects_null(B):

@@ -52,7 +52,7 @@ SHAPES = [(32, 32, 32), (37, 23, 11), (40, 8, 20), (12, 9, 1), (16, 1, 1), (1, 1
 
 
 KERNELS = [(2, 0), (1, 0)]  # (kernel, tile): TMA default tile, plane ring
-TMA_TILES = [(2, t) for t in range(1, 28)]
+TMA_TILES = [(2, t) for t in range(1, 29)]
 
 
 @pytest.mark.parametrize("kernel,tile", KERNELS)
@@ -215,7 +215,7 @@ def test_tma_tiles_give_the_same_bits(shape):
 # --------------------------------------------------------------------------
 # Paired-point FP32 kernel (two x-points per thread, 64-wide tiles)
 # --------------------------------------------------------------------------
-X2_TILES = [17, 19, 20, 25, 26]
+X2_TILES = [17, 19, 20, 25, 26, 28]
 
 
 @pytest.mark.parametrize("tile", X2_TILES)
@@ -263,10 +263,64 @@ def test_paired_kernel_steps_match_oracle(tile):
     assert_state_matches(got, want, "f32")
 
 
+@pytest.mark.parametrize("shape", [(128, 24, 16), (70, 22, 18), (64, 8, 1)])
+def test_interleaved_w_layout_steps_bit_for_bit_like_tile_26(shape):
+    """Tile 28 is tile 26 with w's fields 0-5 in the interleaved layout: the
+    same arithmetic in the same order, so 5 forced, upwinded steps (and the
+    RHS) agree bit for bit, ragged tiles and a single plane included."""
+    nx, ny, nz = shape
+    kw = dict(nx=nx, ny=ny, nz=nz, nu=0.01, eta=0.02, f0=0.05, sigma=1.0, kmin=1.0, kmax=2.0, seed=7,
+              upwind=1, dtype="f32", kernel=2)
+    q0 = inputs.random_modes_state(nx, ny, nz, seed=9, amp=0.2)
+    out = []
+    for tile in (26, 28):
+        run = make_run(tile=tile, **kw)
+        run.set_state(q0)
+        rhs = run.eval_rhs(step=2, dt_forcing=0.01)
+        run.step(5)
+        out.append((rhs, run.get_state()))
+        run.close()
+    (ra, (qa, ta, sa)), (rb, (qb, tb, sb)) = out
+    assert np.array_equal(ra, rb)
+    assert sa == sb == 5 and ta == tb and np.array_equal(qa, qb)
+
+
+def test_auto_tiled_batch_of_both_w_layouts_is_bitwise_identical_to_alone():
+    """A grid of more than two waves of 64 x 8 columns (512 x 512 x 4: tile
+    28 by default) batched with one of a few columns (tile 26): the batch
+    steps both with one layout, and each run matches its stepping alone."""
+    from paper_2012_08758_b300 import binding as B
+    from paper_2012_08758_b300.run import Batch
+    cfgs = [dict(nx=512, ny=512, nz=4, lz=2 * math.pi * 4 / 512, nu=4e-3, eta=4e-3, f0=0.02, sigma=1.0, seed=1),
+            dict(nx=40, ny=24, nz=16, nu=5e-3, eta=5e-3, f0=0.03, sigma=0.5, seed=2)]
+    tiles = [B.mhd_resolve_params(B.mhd_default_params(**gpu_params(dtype="f32", **c))).tile for c in cfgs]
+    assert tiles == [28, 26]
+    states = [inputs.random_modes_state(c["nx"], c["ny"], c["nz"], seed=3 + i, amp=0.2) for i, c in enumerate(cfgs)]
+    alone = []
+    for c, q in zip(cfgs, states):
+        r = make_run(dtype="f32", **c)
+        r.set_state(q)
+        r.step(3)
+        alone.append(r.get_state(dtype=np.float32))
+        r.close()
+    runs = [make_run(dtype="f32", **c) for c in cfgs]
+    for r, q in zip(runs, states):
+        r.set_state(q)
+    b = Batch(runs)
+    b.step(3)
+    for r, (ref, t, step) in zip(runs, alone):
+        got, tg, sg = r.get_state(dtype=np.float32)
+        assert sg == step == 3 and tg == t
+        assert np.array_equal(got, ref)
+    b.close()
+    for r in runs:
+        r.close()
+
+
 # --------------------------------------------------------------------------
 # Upwinding of the continuity equation (upwind = 1)
 # --------------------------------------------------------------------------
-UPWIND_KERNELS = [(2, 0), (1, 0), (2, 1), (2, 7), (2, 17), (2, 25), (2, 26)]
+UPWIND_KERNELS = [(2, 0), (1, 0), (2, 1), (2, 7), (2, 17), (2, 25), (2, 26), (2, 28)]
 
 
 @pytest.mark.parametrize("kernel,tile", UPWIND_KERNELS)
@@ -559,7 +613,7 @@ def test_checkpoint_resume_is_bit_for_bit(dtype, tmp_path):
     b.close()
 
 
-@pytest.mark.parametrize("kernel,tile", [(2, 0), (1, 0), (2, 2), (2, 9), (2, 17), (2, 25)])
+@pytest.mark.parametrize("kernel,tile", [(2, 0), (1, 0), (2, 2), (2, 9), (2, 17), (2, 25), (2, 28)])
 @pytest.mark.parametrize("shape,dtype", [((32, 32, 32), "f32"), ((37, 23, 11), "f64"), ((12, 9, 1), "f32"),
                                          ((16, 1, 1), "f64"), ((40, 8, 20), "f32")])
 def test_padding_canaries_survive_every_entry_point(shape, dtype, kernel, tile):

@@ -24,6 +24,7 @@ CASES = [
     ((128, 16, 27), 3, False, dict(f0=0.05, sigma=0.3, seed=8, kernel=2, tile=22, upwind=1)),
     ((70, 20, 24), 4, True, dict(f0=0.05, sigma=1.0, seed=9, kernel=2, tile=25)),  # warp-specialised
     ((66, 30, 21), 3, False, dict(f0=0.05, sigma=0.5, seed=10, kernel=2, tile=26)),  # w through TMA
+    ((72, 24, 18), 3, True, dict(f0=0.05, sigma=1.0, seed=11, kernel=2, tile=28)),  # interleaved w
 ]
 
 
