@@ -107,10 +107,9 @@ void mhd_default_params(mhd_params *p);
 
 /* The parameters a context created with p runs with: p with the automatic
  * choices made (kernel MHD_KERNEL_AUTO -> MHD_KERNEL_TMA; on that kernel tile
- * 0 -> FP64: 3; FP32: the warp-specialised paired-point tile, 28 -- w in
- * the interleaved layout -- on grids of more than two waves of 64 x 8
- * columns, i.e. ceil(nx/64) ceil(ny/8) > 2 x the device's SM count, else
- * 26).  Host-only.  Errors: MHD_EINVAL (invalid p, NULL out). */
+ * 0 -> FP32: 28, the warp-specialised paired-point kernel with w in the
+ * interleaved layout; FP64: 3).  Host-only.  Errors: MHD_EINVAL (invalid p,
+ * NULL out). */
 int mhd_resolve_params(const mhd_params *p, mhd_params *out);
 
 /* Device bytes a context with parameters p needs when the caller supplies

@@ -274,14 +274,8 @@ int validate(const mhd_params *p, std::string *why) {
 mhd_params resolved(const mhd_params *p) {
   mhd_params r = *p;
   if (r.kernel == MHD_KERNEL_AUTO) r.kernel = MHD_KERNEL_TMA;
-  // FP32: the warp-specialised paired-point kernel; its interleaved-w form
-  // (tile 28) where the grid has more than two waves of 64 x 8 columns (the
-  // third substep reads that layout more slowly, which the 16-byte w stores
-  // of the first two outweigh only there, as measured at 256^3 - 1024^2 x 256)
-  if (r.kernel == MHD_KERNEL_TMA && r.tile == 0) {
-    const long long cols = (long long)((r.nx + 63) / 64) * ((r.ny + 7) / 8);
-    r.tile = r.dtype != MHD_F32 ? 3 : cols > 2LL * num_sms() ? 28 : 26;
-  }
+  // FP32: the warp-specialised paired-point kernel with w interleaved
+  if (r.kernel == MHD_KERNEL_TMA && r.tile == 0) r.tile = r.dtype == MHD_F32 ? 28 : 3;
   return r;
 }
 
@@ -347,7 +341,6 @@ int encode_box_map(CUtensorMap *m, void *base, size_t esz, int px, int py, int p
 
 // The w maps of the interleaved layout: fields 0-5 as three arrays (2 px
 // values per row, 2 fstride apart; box 2 tw x th), and field 6 (box tw x th).
-// Encoded for every FP32 run, so that a batch may step it with either layout.
 int encode_w_pair_maps(RunDesc *R, const Layout &L, std::string *why) {
   char *w = static_cast<char *>(R->w);
   if (int e = encode_map4(&R->wpmap[0], w, L.esz, 2LL * L.px, L.py, L.pz, 3, 2 * L.fstride, 2 * L.stw, L.sth,
@@ -424,7 +417,6 @@ struct mhd_ctx {
   Tile *d_sub;  // substep work split (split_columns) and its grid
   int nsub, sub_grid;
   int iso;   // equal grid spacings on all axes
-  bool tile_auto;  // the tile was chosen by resolved() (mhd_params.tile == 0)
   std::string err;
   cufftHandle fft = 0;  // spectrum plan, made by the first mhd_spectrum call
   bool fft_made = false;
@@ -593,7 +585,6 @@ int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t worksp
   if (validate(p, &why)) return fail(nullptr, MHD_EINVAL, "%s", why.c_str());
   mhd_ctx *ctx = new mhd_ctx();
   ctx->p = resolved(p);
-  ctx->tile_auto = p->tile == 0;
   p = &ctx->p;
   ctx->stream = static_cast<cudaStream_t>(stream);
   ctx->L = make_layout(p);
@@ -673,7 +664,7 @@ int mhd_create(const mhd_params *p, void *stream, void *workspace, size_t worksp
       if (encode_state_map(&R.tmap[b], R.q[b], L.esz, L.px, L.py, L.pz, L.stw, L.sth, &why) ||
           encode_state_map(&R.rmap[b], R.q[b], L.esz, L.px, L.py, L.pz, L.tw, L.th, &why) ||
           (b == 0 && encode_box_map(&R.wmap, R.w, L.esz, L.px, L.py, L.pz, L.stw, L.sth, &why)) ||
-          (b == 0 && L.esz == 4 && encode_w_pair_maps(&R, L, &why))) {
+          (b == 0 && L.wpairs && encode_w_pair_maps(&R, L, &why))) {
         fail(ctx, MHD_ECUDA, "%s", why.c_str());
         return cleanup(MHD_ECUDA);
       }
@@ -1168,22 +1159,11 @@ int mhd_batch_create(mhd_ctx *const *runs, int nruns, mhd_batch **out) {
   std::vector<RunDesc> descs;
   std::vector<Tile> tiles;
   double cells_total = 0;
-  // Runs whose FP32 paired-point tile was chosen automatically (26 or 28,
-  // the two w layouts of one kernel) are stepped with the choice for the
-  // batch's combined columns: w is dead between steps and every such run
-  // carries the tensor maps of both layouts.
-  bool auto_x2 = true;
-  long long cols_total = 0;
   for (int i = 0; i < nruns; ++i) {
     mhd_ctx *r = runs[i];
     if (!r) return fail(nullptr, MHD_EINVAL, "runs[%d] is NULL", i);
-    auto_x2 = auto_x2 && r->tile_auto && (r->p.tile == 26 || r->p.tile == 28);
-    cols_total += (long long)((r->p.nx + 63) / 64) * ((r->p.ny + 7) / 8);
-  }
-  for (int i = 0; i < nruns; ++i) {
-    mhd_ctx *r = runs[i];
     if (r->p.dtype != r0->p.dtype || r->stream != r0->stream || r->p.kernel != r0->p.kernel ||
-        (r->p.tile != r0->p.tile && !auto_x2))
+        r->p.tile != r0->p.tile)
       return fail(nullptr, MHD_EINVAL,
                   "runs of a batch must share dtype, stream, kernel and tile");
     for (int j = 0; j < i; ++j)
@@ -1216,7 +1196,7 @@ int mhd_batch_create(mhd_ctx *const *runs, int nruns, mhd_batch **out) {
   b->stream = r0->stream;
   b->dtype = r0->p.dtype;
   b->kernel = r0->p.kernel;
-  b->tile = auto_x2 ? (cols_total > 2LL * num_sms() ? 28 : 26) : r0->p.tile;
+  b->tile = r0->p.tile;
   b->tw = r0->L.tw;
   b->th = r0->L.th;
   b->ntiles = (int)tiles.size();

@@ -274,17 +274,22 @@ namespace {
 // order, into stage g mod NS once the plane g - NS has been released.  On a
 // wait that gives up it records status bit 1 and raises the CTA's abort flag;
 // before returning it waits (bounded) for every copy it issued.  WT: after
-// lead plane p it also copies w of output plane p - 3 - D into the w ring,
-// slot gw mod NW, once w plane gw - NW has been released (D = NS - 3 - NW
-// keeps at most NW w planes in flight; the last D of a tile follow its last
-// lead plane).
+// lead plane p it also copies w of output plane p - WL into the w ring, slot
+// gw mod NW, once w plane gw - NW has been released; WL = NS - NW - 1, so
+// that w arrives a plane before the compute warps reach that output plane
+// (with the copy issued with the plane's own lead copy the third substep
+// waited for it) and at most NW w planes are in flight; the w of the tile's
+// last output planes follows its last lead plane.
 template <int TY, int NS, int SUB, bool WT, bool WP>
 __device__ __forceinline__ void x2_produce(const RunDesc *__restrict__ runs, const Tile *__restrict__ tiles,
                                            int ntiles, unsigned char *smem, uint64_t *full, uint64_t *empty,
                                            unsigned char *wst, uint64_t *wfull, uint64_t *wempty,
                                            volatile int *abort) {
   using SH = TmaShape<float, TY, 64>;
-  constexpr int NW = x2_wring<TY, NS>() > 0 ? x2_wring<TY, NS>() : 1, D = NS - 3 - NW;
+  constexpr int NW = x2_wring<TY, NS>() > 0 ? x2_wring<TY, NS>() : 1, WL = NS - NW - 1;
+  // the w slot the producer waits for at lead p frees once output p - WL - NW
+  // is done, which needs q planes up to p - WL - NW + RAD only: no cycle
+  static_assert(!WT || WL + NW > RAD, "the w ring must not wait on planes not yet issued");
   unsigned long long g = 0, gw = 0;
   int fail_run = -1;
   for (int t = blockIdx.x; t < ntiles && fail_run < 0; t += gridDim.x) {
@@ -319,7 +324,8 @@ __device__ __forceinline__ void x2_produce(const RunDesc *__restrict__ runs, con
       mbar_arrive_expect_tx(&full[sl], (uint32_t)(NF * SH::FIELD * sizeof(float)));
       tma_load_4d(smem + sl * SH::STAGE_BYTES, map, &full[sl], tile.x0, tile.y0, tile.z0 + p, 0);
       if constexpr (WT) {
-        if (p >= 2 * RAD + D && !issue_w(p - RAD - D)) {
+        const int ow = p - WL;
+        if (ow >= RAD && ow < npl - RAD && !issue_w(ow)) {
           fail_run = tile.run;
           ++g;
           break;
@@ -327,8 +333,8 @@ __device__ __forceinline__ void x2_produce(const RunDesc *__restrict__ runs, con
       }
     }
     if constexpr (WT) {
-      // the w of the tile's last D output planes
-      for (int o = npl - RAD - D; fail_run < 0 && o < npl - RAD; ++o)
+      // the w of the tile's last output planes
+      for (int o = npl - WL; fail_run < 0 && o < npl - RAD; ++o)
         if (o >= RAD && !issue_w(o)) fail_run = tile.run;
     }
   }

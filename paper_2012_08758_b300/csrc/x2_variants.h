@@ -9,7 +9,7 @@
 // 28 (6 stages) and 25 (7) also have room for a ring of 3 / 2 stages of w,
 // which the producer fills one output plane at a time.  Tile 28 is tile 26
 // with w's fields 0-5 in the interleaved layout (WP): 16-byte w stores and
-// ring reads; the default for grids of more than two waves of 64 x 8 columns.
+// ring reads; the FP32 default.
 #pragma once
 #define MHD_X2_VARIANTS(X) \
   X(17, 8, 6, 2, 0, 0)     \

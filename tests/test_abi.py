@@ -125,9 +125,9 @@ def test_substep_plan_covers_every_point_once(B, shape, grid, tile):
     p = B.mhd_default_params(nx=nx, ny=ny, nz=nz, kernel=B.MHD_KERNEL_TMA, tile=tile)
     tiles, g = B.mhd_substep_plan(p, grid)
     assert 1 <= g <= grid and len(tiles) % g == 0
-    # tile 0: the warp-specialised paired-point tile 26 or 28 (64 x 8 columns)
+    # tile 0: the warp-specialised paired-point tile 28 (64 x 8 columns)
     res = B.mhd_resolve_params(p).tile
-    assert res == tile or (tile == 0 and res in (26, 28))
+    assert res == (tile if tile else 28)
     tw = 64 if res >= 17 else 32
     th = {2: 4, 4: 12, 5: 12, 9: 6, 13: 12, 16: 12, 17: 8, 18: 8, 19: 4, 20: 6, 22: 8, 25: 8, 26: 8, 28: 8}[res]
     seen = {}
@@ -168,21 +168,19 @@ def test_paired_split_uses_whole_columns_for_one_or_two_full_waves(B, shape, gri
         assert len(real) == (nx // 64) * (ny // 8)
 
 
-@pytest.mark.parametrize("shape,expect", [((256, 256, 256), 26), ((320, 320, 320), 26), ((384, 384, 384), 26),
-                                          ((384, 392, 64), 26), ((384, 400, 64), 28), ((448, 448, 448), 28),
-                                          ((512, 512, 512), 28), ((1024, 1024, 256), 28), ((33, 17, 9), 26)])
-def test_default_fp32_tile_follows_the_column_count(B, shape, expect):
-    """Automatic tile: FP32 takes the paired-point kernel, in its
-    interleaved-w form (tile 28) only with more than two waves of 64 x 8
-    columns over 148 SMs (384 x 392: 6 x 49 = 294 columns; 384 x 400: 300);
-    FP64 takes tile 3; an explicit tile is kept."""
+@pytest.mark.parametrize("shape", [(256, 256, 256), (384, 384, 384), (512, 512, 512), (1024, 1024, 256), (33, 17, 9)])
+def test_default_tile_choice(B, shape):
+    """Automatic kernel and tile: FP32 takes the paired-point kernel with w
+    interleaved (tile 28), FP64 tile 3; an explicit tile is kept."""
     nx, ny, nz = shape
     r = B.mhd_resolve_params(B.mhd_default_params(nx=nx, ny=ny, nz=nz))
-    assert (r.kernel, r.tile) == (B.MHD_KERNEL_TMA, expect)
+    assert (r.kernel, r.tile) == (B.MHD_KERNEL_TMA, 28)
     r = B.mhd_resolve_params(B.mhd_default_params(nx=nx, ny=ny, nz=nz, dtype=B.MHD_F64))
     assert (r.kernel, r.tile) == (B.MHD_KERNEL_TMA, 3)
     r = B.mhd_resolve_params(B.mhd_default_params(nx=nx, ny=ny, nz=nz, kernel=B.MHD_KERNEL_TMA, tile=26))
     assert r.tile == 26
+    r = B.mhd_resolve_params(B.mhd_default_params(nx=nx, ny=ny, nz=nz, kernel=B.MHD_KERNEL_SMEM))
+    assert (r.kernel, r.tile) == (B.MHD_KERNEL_SMEM, 0)
     with pytest.raises(B.MhdError):
         B.mhd_resolve_params(B.mhd_default_params(nx=0))
 
