@@ -266,15 +266,14 @@ int validate(const mhd_params *p, std::string *why) {
 
 // AUTO resolves to the TMA kernel; tile 0 to the fastest variant measured on
 // B300: FP32 grids take the warp-specialised paired-point kernel with 6
-// stages of q and 3 of w, both copied by its producer warpgroup (tile 26;
-// 512^3: 1.03e10 cell-updates/s against 8.66e9 for the barrier-synchronised
-// paired tile 18 and 7.6e9 for the 32 x 12 scalar kernel; 32^3 - 192^3 6-51%
-// faster than the scalar kernel, 256^3 within 1%), FP64 the 32 x 8 scalar
-// tile with 6 stages.
+// stages of q and 3 of w, both copied by its producer warpgroup, and w kept
+// in interleaved field pairs (tile 28; 512^3: 1.05e10 cell-updates/s against
+// 1.02e10 with w field by field (tile 26), 8.66e9 for the barrier-synchronised
+// paired tile 18 and 7.6e9 for the 32 x 12 scalar kernel; 256^3 - 1024^3
+// 1.5-8.6% faster than tile 26), FP64 the 32 x 8 scalar tile with 6 stages.
 mhd_params resolved(const mhd_params *p) {
   mhd_params r = *p;
   if (r.kernel == MHD_KERNEL_AUTO) r.kernel = MHD_KERNEL_TMA;
-  // FP32: the warp-specialised paired-point kernel with w interleaved
   if (r.kernel == MHD_KERNEL_TMA && r.tile == 0) r.tile = r.dtype == MHD_F32 ? 28 : 3;
   return r;
 }
