@@ -185,6 +185,24 @@ def test_default_tile_choice(B, shape):
         B.mhd_resolve_params(B.mhd_default_params(nx=0))
 
 
+def test_autotuner_candidates_cover_every_accepted_variant(B):
+    """The autotuner tries every (kernel, tile) the library accepts for each
+    dtype and nothing it rejects: all TMA tiles up to the first invalid id,
+    and the plane-ring kernel."""
+    from paper_2012_08758_b300 import autotune
+    for dtype in (B.MHD_F32, B.MHD_F64):
+        valid = []
+        t = 1
+        while True:
+            try:
+                B.mhd_workspace_bytes(B.mhd_default_params(kernel=B.MHD_KERNEL_TMA, tile=t, dtype=dtype))
+            except B.MhdError:
+                break
+            valid.append((B.MHD_KERNEL_TMA, t))
+            t += 1
+        assert sorted(autotune.CANDIDATES[dtype]) == sorted(valid + [(B.MHD_KERNEL_SMEM, 0)])
+
+
 def test_padding_check_rejects_null(B):
     import ctypes as C
     n = C.c_longlong()
