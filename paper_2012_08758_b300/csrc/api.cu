@@ -127,7 +127,6 @@ struct SubCol {
   int run, x0, y0, nz;
   double w;    // work per plane relative to a full tile
   int zb = 0;  // first interior plane of the column's z-range
-  bool paired = false;  // a column of the paired-point kernel (64-wide tile)
 };
 
 // Columns of planes zb .. zb + nz - 1 of one run (zb > 0: the inner or outer
@@ -151,26 +150,15 @@ void add_columns(std::vector<SubCol> *cols, int run, int nx, int ny, int nz, int
         double w = act >= 1.0 ? 1.0 : 0.565 + 0.435 * act;
         if (xface) w *= wx;
         if (yface) w *= wy;
-        cols->push_back(SubCol{run, x0, y0, nz, w, zb, paired});
+        cols->push_back(SubCol{run, x0, y0, nz, w, zb});
       }
 }
 
+// (Leaving CTAs idle to run one or two waves of whole columns was faster
+// with the barrier-synchronised paired kernel; with the warp-specialised one
+// the split below is: 256^3 3% and 384^3 3% shorter steps.)
 std::vector<Tile> split_columns(const std::vector<SubCol> &cols, int G, int *grid_out) {
   G = std::max(1, G);
-  {
-    // Paired kernel: one or two waves of whole columns that keep at least
-    // 85% of the CTAs busy beat cutting the columns end to end (measured:
-    // 256^3 +7%, 384^3 +3%); with more waves the split that tops up every
-    // CTA's load wins (512^3: whole columns alone 16% slower), and the FP64
-    // scalar kernel loses by it (256^3 -11%).
-    int nzmax = 0;
-    for (const SubCol &c : cols) nzmax = std::max(nzmax, c.nz);
-    const int n = (int)cols.size();
-    bool equal = true;
-    for (const SubCol &c : cols) equal &= c.nz == nzmax && c.paired;
-    const int waves = (n + G - 1) / G;
-    if (equal && n > 0 && waves <= 2 && (double)n >= 0.85 * waves * G) G = (n + waves - 1) / waves;
-  }
   std::vector<std::vector<Tile>> per(G);
   // whole-column waves over the full columns of the largest length
   int nzmax = 0;

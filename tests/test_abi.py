@@ -150,22 +150,19 @@ def test_substep_plan_covers_every_point_once(B, shape, grid, tile):
         assert planes.max() <= 1.15 * planes.mean()
 
 
-@pytest.mark.parametrize("shape,grid,expect", [((256, 256, 256), 148, 128), ((384, 384, 384), 148, 144),
-                                               ((512, 512, 512), 148, 148), ((320, 320, 320), 148, 148)])
-def test_paired_split_uses_whole_columns_for_one_or_two_full_waves(B, shape, grid, expect):
-    """Paired kernel: when one or two waves of whole columns keep at least 85%
-    of the CTAs busy (256^3: 128 columns of 64 x 8; 384^3: 288 in two waves
-    of 144) every CTA sweeps whole columns only; otherwise (512^3: 512
-    columns; 320^3: 200 columns, two waves at 68%) the remainder is split."""
+@pytest.mark.parametrize("shape", [(256, 256, 256), (384, 384, 384), (512, 512, 512), (320, 320, 320)])
+def test_paired_split_keeps_every_sm_busy(B, shape):
+    """Paired kernel: the split uses all 148 CTAs even where one or two
+    waves of whole columns would fit (256^3: 128 columns of 64 x 8; 384^3:
+    288), cutting columns end to end so that every CTA gets the same load."""
     nx, ny, nz = shape
-    p = B.mhd_default_params(nx=nx, ny=ny, nz=nz, kernel=B.MHD_KERNEL_TMA, tile=26)
-    tiles, g = B.mhd_substep_plan(p, grid)
-    assert g == expect
-    real = [t for t in tiles if t[3] > t[2]]
-    whole = all(z0 == 0 and z1 == nz for _, _, z0, z1, _ in real)
-    assert whole == (expect < grid or (nx // 64) * (ny // 8) == grid)
-    if expect < grid:
-        assert len(real) == (nx // 64) * (ny // 8)
+    p = B.mhd_default_params(nx=nx, ny=ny, nz=nz, kernel=B.MHD_KERNEL_TMA, tile=28)
+    tiles, g = B.mhd_substep_plan(p, 148)
+    assert g == 148
+    planes = np.zeros(g)
+    for k, (x0, y0, z0, z1, run) in enumerate(tiles):
+        planes[k % g] += max(0, z1 - z0)
+    assert planes.min() > 0
 
 
 @pytest.mark.parametrize("shape", [(256, 256, 256), (384, 384, 384), (512, 512, 512), (1024, 1024, 256), (33, 17, 9)])
